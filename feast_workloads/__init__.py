@@ -1,0 +1,291 @@
+"""Seeded synthetic inputs for the FEAST contour-filter eigensolver.
+
+This module only builds matrices, intervals and random start blocks.  It holds
+none of the eigensolver's arithmetic, so both the CPU oracle (``oracle/``) and
+the CUDA library can be fed from it without sharing any method code.
+
+Every generator is deterministic: random numbers come from numpy's PCG64
+(``numpy.random.default_rng(seed)``).  Matrices are returned as 0-based CSR
+triples ``(indptr int32, indices int32, data float64)`` with sorted, duplicate
+free rows.  The paper's own test matrix (the 4x4 "helloworld" system of the
+FEAST v4.0 user guide, Sec. 2.3 and its IFEAST variant in Sec. 5) is the only
+matrix taken from the paper; it stands in for the missing example data sets.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+# --------------------------------------------------------------------------
+# CSR helpers
+# --------------------------------------------------------------------------
+@dataclass
+class CSR:
+    n: int
+    indptr: np.ndarray  # int32 [n+1], 0-based
+    indices: np.ndarray  # int32 [nnz]
+    data: np.ndarray  # float64 [nnz]
+
+    @property
+    def nnz(self) -> int:
+        return int(self.indptr[-1])
+
+    def to_dense(self) -> np.ndarray:
+        d = np.zeros((self.n, self.n))
+        for i in range(self.n):
+            s, e = self.indptr[i], self.indptr[i + 1]
+            d[i, self.indices[s:e]] += self.data[s:e]
+        return d
+
+
+def csr_from_coo(n: int, rows, cols, vals) -> CSR:
+    """Sort (row, col) pairs, sum duplicates and return a 0-based CSR."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    vals = np.asarray(vals, dtype=np.float64)
+    key = rows * n + cols
+    order = np.argsort(key, kind="stable")
+    key, vals = key[order], vals[order]
+    uniq, start = np.unique(key, return_index=True)
+    summed = np.add.reduceat(vals, start) if len(vals) else vals
+    r = (uniq // n).astype(np.int64)
+    c = (uniq % n).astype(np.int32)
+    indptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(indptr, r + 1, 1)
+    indptr = np.cumsum(indptr).astype(np.int32)
+    return CSR(n, indptr, c, summed.astype(np.float64))
+
+
+def csr_from_dense(d: np.ndarray) -> CSR:
+    r, c = np.nonzero(d)
+    return csr_from_coo(d.shape[0], r, c, d[r, c])
+
+
+def identity_csr(n: int) -> CSR:
+    i = np.arange(n)
+    return csr_from_coo(n, i, i, np.ones(n))
+
+
+def diagonal_csr(d: np.ndarray) -> CSR:
+    i = np.arange(len(d))
+    return csr_from_coo(len(d), i, i, d)
+
+
+# --------------------------------------------------------------------------
+# Matrices
+# --------------------------------------------------------------------------
+def laplacian_1d(n: int) -> CSR:
+    """tridiag(-1, 2, -1) of order n (Dirichlet)."""
+    i = np.arange(n)
+    rows = np.concatenate([i, i[1:], i[:-1]])
+    cols = np.concatenate([i, i[:-1], i[1:]])
+    vals = np.concatenate([np.full(n, 2.0), np.full(n - 1, -1.0), np.full(n - 1, -1.0)])
+    return csr_from_coo(n, rows, cols, vals)
+
+
+def _grid_laplacian(shape, potential) -> CSR:
+    """(2d)-point Dirichlet Laplacian on a box grid plus a diagonal potential.
+
+    Row index is lexicographic with the LAST axis fastest.
+    """
+    shape = tuple(int(s) for s in shape)
+    n = int(np.prod(shape))
+    idx = np.arange(n).reshape(shape)
+    rows = [idx.ravel()]
+    cols = [idx.ravel()]
+    vals = [np.full(n, 2.0 * len(shape)) + np.asarray(potential, dtype=np.float64).ravel()]
+    for ax in range(len(shape)):
+        lo = [slice(None)] * len(shape)
+        hi = [slice(None)] * len(shape)
+        lo[ax] = slice(0, shape[ax] - 1)
+        hi[ax] = slice(1, shape[ax])
+        a = idx[tuple(lo)].ravel()
+        b = idx[tuple(hi)].ravel()
+        rows += [a, b]
+        cols += [b, a]
+        vals += [np.full(a.size, -1.0), np.full(a.size, -1.0)]
+    return csr_from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def laplacian_2d(side: int, potential=None) -> CSR:
+    pot = np.zeros((side, side)) if potential is None else potential
+    return _grid_laplacian((side, side), pot)
+
+
+def laplacian_3d(side: int, potential=None) -> CSR:
+    pot = np.zeros((side, side, side)) if potential is None else potential
+    return _grid_laplacian((side, side, side), pot)
+
+
+def stencil27_spd(side: int, rng: np.random.Generator) -> CSR:
+    """27-point SPD stencil: off-diagonals -U[0.5,1.5] drawn once per undirected
+    edge (so the matrix is symmetric), diagonal = row-abs-sum + U[0.1,1]."""
+    shape = (side, side, side)
+    n = side ** 3
+    idx = np.arange(n).reshape(shape)
+    rows, cols = [], []
+    # each undirected edge once: offsets with the first nonzero component > 0
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                off = (dz, dy, dx)
+                first = next((o for o in off if o != 0), 0)
+                if first <= 0:
+                    continue
+                src = [slice(max(0, -o), side - max(0, o)) for o in off]
+                dst = [slice(max(0, o), side - max(0, -o)) for o in off]
+                rows.append(idx[tuple(src)].ravel())
+                cols.append(idx[tuple(dst)].ravel())
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    w = -rng.uniform(0.5, 1.5, size=r.size)
+    absum = np.zeros(n)
+    np.add.at(absum, r, -w)
+    np.add.at(absum, c, -w)
+    diag = absum + rng.uniform(0.1, 1.0, size=n)
+    i = np.arange(n)
+    return csr_from_coo(n, np.concatenate([r, c, i]), np.concatenate([c, r, i]),
+                        np.concatenate([w, w, diag]))
+
+
+def helloworld_dense() -> np.ndarray:
+    """The 4x4 real symmetric example of the FEAST v4.0 guide (Sec. 2.3),
+    eigenvalues {0, 2, 4, 4}."""
+    return np.array([[2.0, -1.0, -1.0, 0.0],
+                     [-1.0, 3.0, -1.0, -1.0],
+                     [-1.0, -1.0, 3.0, -1.0],
+                     [0.0, -1.0, -1.0, 2.0]])
+
+
+def helloworld_csr_1based():
+    """The same matrix in the guide's 1-based CSR encoding (IFEAST example,
+    Sec. 5): returns (sA, IA, JA) exactly as printed there."""
+    sA = np.array([2.0, -1.0, -1.0, -1.0, 3.0, -1.0, -1.0, -1.0, -1.0, 3.0, -1.0, -1.0, -1.0, 2.0])
+    IA = np.array([1, 4, 8, 12, 15], dtype=np.int32)
+    JA = np.array([1, 2, 3, 1, 2, 3, 4, 1, 2, 3, 4, 2, 3, 4], dtype=np.int32)
+    return sA, IA, JA
+
+
+# --------------------------------------------------------------------------
+# Start block and search-interval estimates
+# --------------------------------------------------------------------------
+def gaussian_block(n: int, m0: int, seed: int) -> np.ndarray:
+    """Y0 ~ N(0,1), shape (n, m0), Fortran (column-major) order."""
+    rng = np.random.default_rng(seed)
+    return np.asfortranarray(rng.standard_normal((n, m0)))
+
+
+def _laplacian_levels(side: int, dim: int, count: int) -> np.ndarray:
+    """Lowest `count`+ closed-form eigenvalues of the dim-D Dirichlet Laplacian
+    on a side^dim grid (sums of 2-2cos(k pi/(side+1)))."""
+    kmax = min(side, int(math.ceil((count * 2 ** dim) ** (1.0 / dim))) + 4)
+    mu = 2.0 - 2.0 * np.cos(np.arange(1, kmax + 1) * np.pi / (side + 1))
+    grids = np.meshgrid(*([mu] * dim), indexing="ij")
+    return np.sort(np.sum(grids, axis=0).ravel())
+
+
+def interval_estimate(side: int, dim: int, count: int, mean_potential: float) -> float:
+    """Upper interval end placed in a gap of the closed-form spectrum of the
+    constant-potential Laplacian (mean potential added), at the first gap after
+    `count` eigenvalues.  For a random potential the true count is close to
+    `count`, not exact; it is an input choice, not an expected value."""
+    lev = _laplacian_levels(side, dim, count + 64)
+    k = count
+    while k < len(lev) - 1 and lev[k] - lev[k - 1] < 1e-9:
+        k += 1
+    return float(mean_potential + 0.5 * (lev[k - 1] + lev[k]))
+
+
+# --------------------------------------------------------------------------
+# Workloads of the evaluation configurations
+# --------------------------------------------------------------------------
+@dataclass
+class Problem:
+    name: str
+    A: CSR
+    B: CSR | None  # None means B = I
+    emin: float
+    emax: float
+    m0: int
+    ne: int
+    ratio: int  # fpm(18): ellipse ratio in percent
+    y0_seed: int
+    notes: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return self.A.n
+
+    def y0(self) -> np.ndarray:
+        return gaussian_block(self.n, self.m0, self.y0_seed)
+
+
+def tridiag_1d(n: int = 1000, emin: float = 0.0, emax: float = 0.01, m0: int = 48,
+               ne: int = 8, ratio: int = 30, seed: int = 0) -> Problem:
+    """1D Laplacian tridiag(-1,2,-1), B = I.  At n=1000, [0,0.01] holds the 31
+    eigenvalues 2-2cos(k pi/1001), k=1..31."""
+    return Problem(f"laplace1d_n{n}", laplacian_1d(n), None, emin, emax, m0, ne, ratio, seed)
+
+
+def laplace3d_potential(side: int = 64, count: int = 100, m0: int = 150, ne: int = 8,
+                        ratio: int = 100, seed: int = 1, vmax: float = 0.5) -> Problem:
+    """7-point 3D Laplacian on side^3 plus diagonal V ~ U[0, vmax] (seeded), B = I,
+    interval [0, Emax] with Emax from the closed-form spectrum estimate."""
+    rng = np.random.default_rng(seed)
+    pot = rng.uniform(0.0, vmax, size=(side, side, side))
+    A = laplacian_3d(side, pot)
+    emax = interval_estimate(side, 3, count, 0.5 * vmax)
+    return Problem(f"laplace3d_{side}^3", A, None, 0.0, emax, m0, ne, ratio, seed,
+                   {"target_count": count})
+
+
+def laplace3d_constant(side: int, v0: float, emax: float, m0: int, ne: int = 8,
+                       ratio: int = 100, seed: int = 5) -> Problem:
+    """Constant potential v0: spectrum is v0 + closed-form 3D Laplacian levels."""
+    A = laplacian_3d(side, np.full((side, side, side), v0))
+    return Problem(f"laplace3d_const_{side}^3", A, None, 0.0, emax, m0, ne, ratio, seed)
+
+
+def stencil27_generalized(side: int = 96, count: int = 200, m0: int = 300, ne: int = 16,
+                          ratio: int = 100, seed: int = 2, emax: float | None = None) -> Problem:
+    """27-point SPD stencil with B = diag(U[1,2]); Emax must be supplied or is
+    left to the extreme-eigenvalue estimate of the caller."""
+    rng = np.random.default_rng(seed)
+    A = stencil27_spd(side, rng)
+    B = diagonal_csr(rng.uniform(1.0, 2.0, size=side ** 3))
+    return Problem(f"stencil27_{side}^3", A, B, 0.0, -1.0 if emax is None else emax,
+                   m0, ne, ratio, seed, {"target_count": count})
+
+
+def batched_laplace2d(count: int = 512, seed: int = 3, ne: int = 8, ratio: int = 100,
+                      side_lo: int = 32, side_hi: int = 256) -> list[Problem]:
+    """Independent 2D 5-point Laplacians with V ~ U[0,1]; grid side log-uniform in
+    [side_lo, side_hi]; each with k ~ U{8..64} wanted eigenvalues, M0 = ceil(1.5k).
+    Problem p draws from the PCG64 stream seeded by (seed, p)."""
+    out = []
+    for p in range(count):
+        rng = np.random.default_rng([seed, p])
+        side = int(math.floor(math.exp(rng.uniform(math.log(side_lo), math.log(side_hi)))))
+        side = max(side_lo, min(side_hi, side))
+        k = int(rng.integers(8, 65))
+        pot = rng.uniform(0.0, 1.0, size=(side, side))
+        A = laplacian_2d(side, pot)
+        emax = interval_estimate(side, 2, k, 0.5)
+        m0 = int(math.ceil(1.5 * k))
+        out.append(Problem(f"laplace2d_{p}_{side}^2", A, None, 0.0, emax, m0, ne, ratio,
+                           1000 * seed + p, {"target_count": k}))
+    return out
+
+
+def laplace3d_grad(side: int = 48, count: int = 64, m0: int = 96, ne: int = 8,
+                   ratio: int = 100, seed: int = 4) -> Problem:
+    """Differentiation workload: 7-point 3D Laplacian + V ~ U[0,0.5]."""
+    return laplace3d_potential(side, count, m0, ne, ratio, seed)
+
+
+def loss_weights(m: int, seed: int) -> np.ndarray:
+    """g_k ~ N(0,1) for the eigenvalue loss sum_k g_k lambda_k."""
+    return np.random.default_rng([seed, 7]).standard_normal(m)

@@ -1,0 +1,241 @@
+"""FP64 CPU oracle for the FEAST contour-filter eigensolver -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
+may import this package.  The product path (``paper_2002_04807_gb300``) never
+imports it and shares no code with it.
+
+The arithmetic lives in ``feast_oracle.c`` (plain C, compiled with gcc by
+:func:`build`); this module only marshals numpy arrays into it.  Each wrapper
+names the step of the method it performs; the C file cites the guide's
+sections and states the formulas.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "feast_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liboracle.so (gcc, OpenMP)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"],
+                       check=True)
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            _lib.orc_rho.restype = C.c_double
+            _lib.orc_count_below.restype = C.c_long
+    return _lib
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _csr_args(M):
+    if M is None:
+        return None, None, None
+    return _c(M.indptr, np.int32), _c(M.indices, np.int32), _c(M.data, np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+# ---------------------------------------------------------------- quadrature
+def gauss_legendre(n: int):
+    x = np.zeros(n)
+    w = np.zeros(n)
+    if lib().orc_gauss_legendre(C.c_int(n), _ptr(x), _ptr(w)):
+        raise ValueError("n must be >= 1")
+    return x, w
+
+
+def contour_gauss(ne: int, emin: float, emax: float, ratio: float):
+    """Half-contour Gauss nodes z_e and weights w_e (complex arrays)."""
+    z = np.zeros(2 * ne)
+    w = np.zeros(2 * ne)
+    lib().orc_contour_gauss(C.c_int(ne), C.c_double(emin), C.c_double(emax), C.c_double(ratio),
+                            _ptr(z), _ptr(w))
+    return z[0::2] + 1j * z[1::2], w[0::2] + 1j * w[1::2]
+
+
+def rho(ne: int, emin: float, emax: float, ratio: float, lam):
+    z = np.zeros(2 * ne)
+    w = np.zeros(2 * ne)
+    L = lib()
+    L.orc_contour_gauss(C.c_int(ne), C.c_double(emin), C.c_double(emax), C.c_double(ratio),
+                        _ptr(z), _ptr(w))
+    lam = np.atleast_1d(np.asarray(lam, dtype=np.float64))
+    return np.array([L.orc_rho(C.c_int(ne), _ptr(z), _ptr(w), C.c_double(v)) for v in lam])
+
+
+# ---------------------------------------------------------------- linear algebra
+def csr_mm(A, X):
+    X = np.asfortranarray(X, dtype=np.float64)
+    m = X.shape[1]
+    Y = np.zeros((A.n, m), order="F")
+    ip, ix, v = _csr_args(A)
+    lib().orc_csr_mm(C.c_int(A.n), _ptr(ip), _ptr(ix), _ptr(v), C.c_int(m), _ptr(X), _ptr(Y))
+    return Y
+
+
+def _cplx_block(R, n):
+    R = np.asarray(R, dtype=np.complex128).reshape(n, -1, order="F")
+    m = R.shape[1]
+    buf = np.empty(2 * n * m)
+    buf[0::2] = R.real.ravel(order="F")
+    buf[1::2] = R.imag.ravel(order="F")
+    return buf, m
+
+
+def _unblock(buf, n, m):
+    return (buf[0::2] + 1j * buf[1::2]).reshape(n, m, order="F")
+
+
+def shifted_solve(A, B, z: complex, R, method: str = "direct", tol: float = 1e-13,
+                  maxit: int = 100000):
+    """Solve (z B - A) X = R for a block of right-hand sides (B None = identity)."""
+    n = A.n
+    rhs, m = _cplx_block(R, n)
+    sol = np.zeros_like(rhs)
+    ip, ix, v = _csr_args(A)
+    bip, bix, bv = _csr_args(B)
+    if method == "direct":
+        st = lib().orc_shifted_solve_direct(C.c_int(n), _ptr(ip), _ptr(ix), _ptr(v), _ptr(bip),
+                                            _ptr(bix), _ptr(bv), C.c_double(z.real),
+                                            C.c_double(z.imag), C.c_int(m), _ptr(rhs), _ptr(sol))
+        its = None
+    else:
+        its = np.zeros(m, dtype=np.int32)
+        st = lib().orc_shifted_solve_cocg(C.c_int(n), _ptr(ip), _ptr(ix), _ptr(v), _ptr(bip),
+                                          _ptr(bix), _ptr(bv), C.c_double(z.real),
+                                          C.c_double(z.imag), C.c_int(m), _ptr(rhs), _ptr(sol),
+                                          C.c_double(tol), C.c_int(maxit), _ptr(its))
+    if st:
+        raise RuntimeError(f"shifted solve failed ({st})")
+    return _unblock(sol, n, m), its
+
+
+def jacobi_eig(a):
+    a = np.array(a, dtype=np.float64, order="F", copy=True)
+    n = a.shape[0]
+    w = np.zeros(n)
+    V = np.zeros((n, n), order="F")
+    sweeps = lib().orc_jacobi_eig(C.c_int(n), _ptr(a), _ptr(w), _ptr(V))
+    return w, V, int(sweeps)
+
+
+def reduced_gev(Aq, Bq):
+    Aq = np.asfortranarray(Aq, dtype=np.float64)
+    Bq = np.asfortranarray(Bq, dtype=np.float64)
+    m = Aq.shape[0]
+    lam = np.zeros(m)
+    V = np.zeros((m, m), order="F")
+    mk = C.c_int(0)
+    info = lib().orc_reduced_gev(C.c_int(m), _ptr(Aq), _ptr(Bq), _ptr(lam), _ptr(V), C.byref(mk))
+    k = mk.value
+    return info, lam[:k], np.asfortranarray(V[:, :k])
+
+
+def count_below(A, B, sigma: float) -> int:
+    """Number of eigenvalues of (A, B) below sigma (Sylvester inertia)."""
+    ip, ix, v = _csr_args(A)
+    bip, bix, bv = _csr_args(B)
+    r = lib().orc_count_below(C.c_int(A.n), _ptr(ip), _ptr(ix), _ptr(v), _ptr(bip), _ptr(bix),
+                              _ptr(bv), C.c_double(sigma))
+    if r < 0:
+        raise RuntimeError("zero pivot in inertia count")
+    return int(r)
+
+
+def residuals(A, B, X, lam, emin, emax):
+    X = np.asfortranarray(X, dtype=np.float64)
+    lam = _c(lam, np.float64)
+    m = X.shape[1]
+    res = np.zeros(m)
+    ip, ix, v = _csr_args(A)
+    bip, bix, bv = _csr_args(B)
+    lib().orc_residuals(C.c_int(A.n), _ptr(ip), _ptr(ix), _ptr(v), _ptr(bip), _ptr(bix), _ptr(bv),
+                        C.c_int(m), _ptr(X), _ptr(lam), C.c_double(emin), C.c_double(emax),
+                        _ptr(res))
+    return res
+
+
+# ---------------------------------------------------------------- FEAST
+def feastinit():
+    """fpm defaults of the guide's parameter table (C indexing fpm[i-1])."""
+    fpm = np.zeros(64, dtype=np.int32)
+    defaults = {1: 0, 2: 8, 3: 12, 4: 20, 5: 0, 6: 1, 8: 16, 10: 1, 14: 0, 15: 2, 16: 0, 18: 30,
+                19: 0, 40: 0, 41: 1, 42: 1, 43: 0, 45: 1, 46: 40}
+    for i, v in defaults.items():
+        fpm[i - 1] = v
+    return fpm
+
+
+def feast_scsr(A, B, emin, emax, m0, Y0=None, X0=None, ne=8, ratio=30, tol_exp=10, maxloop=20,
+               solver="direct", solve_tol=1e-13, rii=False):
+    """Plain FP64 FEAST on a real symmetric CSR problem.
+
+    Returns a dict with E (inside first, ascending), X (n x m0', column-major),
+    res, M, loop, epsout, info, m0 (kept size), per-loop trace and max-residual.
+    """
+    n = A.n
+    fpm = feastinit()
+    fpm[1] = ne
+    fpm[2] = tol_exp
+    fpm[3] = maxloop
+    fpm[17] = ratio
+    X = np.zeros((n, m0), order="F")
+    if X0 is not None:
+        fpm[4] = 1
+        X[:] = X0
+        Y = np.zeros((n, m0), order="F")
+    else:
+        Y = np.asfortranarray(Y0, dtype=np.float64)
+    E = np.zeros(m0)
+    res = np.zeros(m0)
+    M = C.c_int(0)
+    loop = C.c_int(0)
+    eps = C.c_double(0)
+    m0io = C.c_int(m0)
+    th = np.zeros(maxloop + 2)
+    mh = np.zeros(maxloop + 2)
+    it = C.c_long(0)
+    ip, ix, v = _csr_args(A)
+    bip, bix, bv = _csr_args(B)
+    info = lib().orc_feast_scsr(
+        C.c_int(n), _ptr(ip), _ptr(ix), _ptr(v), _ptr(bip), _ptr(bix), _ptr(bv), _ptr(fpm),
+        C.c_double(emin), C.c_double(emax), C.byref(m0io), _ptr(Y), _ptr(E), _ptr(X), _ptr(res),
+        C.byref(M), C.byref(loop), C.byref(eps), C.c_int(0 if solver == "direct" else 1),
+        C.c_double(solve_tol), C.c_int(1 if rii else 0), _ptr(th), _ptr(mh), C.byref(it))
+    k = m0io.value
+    return {"info": int(info), "E": E[:k].copy(), "X": np.asfortranarray(X[:, :k]),
+            "res": res[:k].copy(), "M": M.value, "loop": loop.value, "epsout": eps.value,
+            "m0": k, "trace": th[: loop.value + 1].copy(), "maxres": mh[: loop.value + 1].copy(),
+            "inner_iters": it.value}

@@ -1,0 +1,284 @@
+"""Pins of the FP64 CPU oracle against facts fixed outside it.
+
+Each test checks one oracle step against a closed form, a worked example the
+FEAST guide prints, brute force or a library routine on small inputs, so that a
+dropped term, a wrong sign, index or transposed operand fails somewhere.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.integrate
+import scipy.linalg
+
+import feast_workloads as fw
+import oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _angles(U, V):
+    """Sine of the largest principal angle between two column spaces of equal
+    dimension: ||(I - P_V) Q_U||_2 with orthonormal bases (no arccos round-off)."""
+    qu, _ = np.linalg.qr(U)
+    qv, _ = np.linalg.qr(V)
+    return float(np.linalg.norm(qu - qv @ (qv.T @ qu), 2))
+
+
+# ------------------------------------------------------------------ quadrature
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 16, 24, 56])
+def test_gauss_legendre_exact_on_polynomials(n):
+    x, w = O.gauss_legendre(n)
+    for p in range(2 * n):
+        exact = 0.0 if p % 2 else 2.0 / (p + 1)
+        assert abs(np.sum(w * x ** p) - exact) < 1e-13, p
+    xr, wr = np.polynomial.legendre.leggauss(n)
+    assert np.allclose(np.sort(x), xr, atol=1e-14) and np.allclose(w[np.argsort(x)], wr, atol=1e-14)
+
+
+@pytest.mark.parametrize("ne", [1, 3, 8, 16])
+def test_circle_filter_is_one_at_centre(ne):
+    # on a circle (ratio 1) w_e/(z_e - c) = omega_e/2, so rho(c) = sum omega_e / 2 = 1
+    assert abs(O.rho(ne, -2.0, 4.0, 1.0, 1.0)[0] - 1.0) < 1e-14
+
+
+@pytest.mark.parametrize("ratio", [0.3, 1.0])
+def test_filter_matches_contour_integral(ratio):
+    # rho(lambda) approximates (1/pi) Im int_0^pi z'(t)/(z(t)-lambda) dt, an
+    # independent adaptive quadrature of the same half-contour integral; for a
+    # rule of many nodes it is the indicator of [Emin, Emax].
+    emin, emax = 1.0, 3.0
+    c, r = 2.0, 1.0
+
+    def integral(lam):
+        f = lambda t: ((-r * math.sin(t) + 1j * ratio * r * math.cos(t))
+                       / (c + r * math.cos(t) + 1j * ratio * r * math.sin(t) - lam)).imag
+        return scipy.integrate.quad(f, 0.0, math.pi, limit=400, epsabs=1e-13)[0] / math.pi
+
+    for lam in [1.5, 2.0, 2.7, 0.0, 3.6, 10.0]:
+        ref = integral(lam)
+        ind = 1.0 if emin < lam < emax else 0.0
+        assert abs(ref - ind) < 1e-9
+        assert abs(O.rho(48, emin, emax, ratio, lam)[0] - ref) < 5e-6 * (1 if ratio == 1.0 else 20)
+
+
+def test_filter_edges_and_decay():
+    lam = np.array([-5.0, 0.0, 1.0, 2.0, 3.0, 4.0, 8.0])
+    rho = O.rho(8, 1.0, 3.0, 1.0, lam)
+    assert abs(rho[2] - 0.5) < 1e-12 and abs(rho[4] - 0.5) < 1e-12  # ends of the interval
+    assert abs(rho[3] - 1.0) < 1e-14
+    assert abs(rho[0]) < 1e-4 and abs(rho[-1]) < 1e-4
+
+
+# ------------------------------------------------------------------ linear algebra
+def _rand_sym_csr(n, bw, rng, shift=0.0):
+    d = np.zeros((n, n))
+    for k in range(bw + 1):
+        v = rng.standard_normal(n - k)
+        d += np.diag(v, k) + (np.diag(v, -k) if k else 0)
+    d += shift * np.eye(n)
+    return fw.csr_from_dense(d), d
+
+
+def test_csr_mm_matches_dense():
+    rng = np.random.default_rng(0)
+    A, d = _rand_sym_csr(30, 3, rng)
+    X = rng.standard_normal((30, 4))
+    assert np.allclose(O.csr_mm(A, X), d @ X, atol=1e-13)
+
+
+@pytest.mark.parametrize("method", ["direct", "cocg"])
+@pytest.mark.parametrize("gen", [False, True])
+def test_shifted_solve(method, gen):
+    rng = np.random.default_rng(1)
+    n = 40
+    A, da = _rand_sym_csr(n, 2, rng)
+    if gen:
+        B = fw.diagonal_csr(rng.uniform(1, 2, n))
+        db = B.to_dense()
+    else:
+        B, db = None, np.eye(n)
+    z = 0.3 + 0.7j
+    R = rng.standard_normal((n, 3)) + 1j * rng.standard_normal((n, 3))
+    X, _ = O.shifted_solve(A, B, z, R, method=method, tol=1e-14)
+    ref = np.linalg.solve(z * db - da, R)
+    assert np.abs(X - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+def test_jacobi_matches_eigh():
+    rng = np.random.default_rng(2)
+    for n in [1, 2, 7, 40]:
+        a = rng.standard_normal((n, n))
+        a = a + a.T
+        w, V, _ = O.jacobi_eig(a)
+        wr = np.linalg.eigvalsh(a)
+        assert np.allclose(w, wr, atol=1e-12 * max(1, abs(wr).max()))
+        assert np.allclose(V.T @ V, np.eye(n), atol=1e-13)
+        assert np.allclose(a @ V, V * w, atol=1e-11 * max(1, abs(wr).max()))
+
+
+def test_reduced_gev_matches_scipy():
+    rng = np.random.default_rng(3)
+    m = 12
+    a = rng.standard_normal((m, m)); a = a + a.T
+    g = rng.standard_normal((m, m)); b = g @ g.T + 0.5 * np.eye(m)
+    info, lam, V = O.reduced_gev(a, b)
+    assert info == 0 and len(lam) == m
+    assert np.allclose(lam, scipy.linalg.eigh(a, b, eigvals_only=True), atol=1e-11)
+    assert np.allclose(V.T @ b @ V, np.eye(m), atol=1e-11)
+
+
+def test_reduced_gev_rank_deficient_and_indefinite():
+    rng = np.random.default_rng(4)
+    m = 8
+    Q = rng.standard_normal((50, 5))
+    Q = np.hstack([Q, Q[:, :3] @ rng.standard_normal((3, 3))])  # rank 5 of 8
+    a = rng.standard_normal((50, 50)); a = a + a.T
+    info, lam, V = O.reduced_gev(Q.T @ a @ Q, Q.T @ Q)
+    assert info == 0 and len(lam) == 5
+    # the Ritz values of the 5-dimensional span
+    qq, _ = np.linalg.qr(Q[:, :5])
+    assert np.allclose(lam, np.linalg.eigvalsh(qq.T @ a @ qq), atol=1e-8)
+    info, _, _ = O.reduced_gev(np.eye(3), -np.eye(3))
+    assert info == -3
+
+
+def test_inertia_counts():
+    rng = np.random.default_rng(5)
+    A, d = _rand_sym_csr(60, 4, rng)
+    B = fw.diagonal_csr(rng.uniform(1, 2, 60))
+    ev = scipy.linalg.eigh(d, B.to_dense(), eigvals_only=True)
+    for s in [-3.0, -0.1, 0.4, 2.5]:
+        assert O.count_below(A, B, s) == int(np.sum(ev < s))
+    L = fw.laplacian_1d(1000)
+    k = np.arange(1, 1001)
+    lam = 2 - 2 * np.cos(k * np.pi / 1001)
+    assert O.count_below(L, None, 0.01) == 31 == int(np.sum(lam < 0.01))
+
+
+def test_residual_formula():
+    rng = np.random.default_rng(6)
+    A, d = _rand_sym_csr(20, 2, rng)
+    B = fw.diagonal_csr(rng.uniform(1, 2, 20))
+    X = rng.standard_normal((20, 3))
+    lam = np.array([0.1, -0.5, 2.0])
+    res = O.residuals(A, B, X, lam, -1.0, 4.0)
+    db = B.to_dense()
+    ref = np.linalg.norm(d @ X - db @ X * lam, axis=0) / (4.0 * np.linalg.norm(db @ X, axis=0))
+    assert np.allclose(res, ref, rtol=1e-13)
+
+
+# ------------------------------------------------------------------ FEAST
+def test_helloworld_worked_example():
+    g = json.load(open(os.path.join(GOLD, "helloworld.json")))
+    run, exp = g["run"], g["expected"]
+    dense = np.array(g["matrix_dense_rows"], dtype=float)
+    assert np.allclose(np.linalg.eigvalsh(dense), g["eigenvalues_all"])
+    c = g["csr_1based"]
+    IA = np.array(c["IA"]) - 1
+    JA = np.array(c["JA"]) - 1
+    A = fw.CSR(4, IA.astype(np.int32), JA.astype(np.int32), np.array(c["sA"], dtype=float))
+    assert np.array_equal(A.to_dense(), dense)
+    Y0 = fw.gaussian_block(4, run["M0"], 0)
+    for solver in ["direct", "cocg"]:
+        r = O.feast_scsr(A, None, run["Emin"], run["Emax"], run["M0"], Y0=Y0, ne=run["Ne"],
+                         ratio=run["ratio_percent"], tol_exp=12, solver=solver)
+        assert r["info"] == 0 and r["M"] == exp["M"]
+        assert np.allclose(r["E"][:2], exp["E"], atol=1e-12)
+        assert abs(r["E"][:2].sum() - exp["trace"]) < 1e-12
+        assert r["res"][:2].max() < exp["max_residual_below"]
+
+
+def test_laplacian_1d_closed_form():
+    p = fw.tridiag_1d()
+    r = O.feast_scsr(p.A, None, p.emin, p.emax, p.m0, Y0=p.y0(), ne=p.ne, ratio=p.ratio,
+                     tol_exp=10)
+    assert r["info"] == 0 and r["M"] == 31
+    k = np.arange(1, 32)
+    lam = 2 - 2 * np.cos(k * np.pi / 1001)
+    assert np.abs(r["E"][:31] - lam).max() <= 1e-10 * lam.max()
+    assert r["res"][:31].max() <= 1e-10
+    i = np.arange(1, 1001)[:, None]
+    xs = np.sqrt(2 / 1001) * np.sin(i * k[None, :] * np.pi / 1001)
+    X = r["X"][:, :31]
+    assert np.abs(X.T @ X - np.eye(31)).max() < 1e-12
+    # per-eigenvalue eigenvectors are unique here (simple spectrum): compare up to sign
+    dots = np.abs(np.sum(X * xs, axis=0))
+    assert np.all(1 - dots < 1e-8)
+    # outside Ritz values lie outside the interval and inside ones are all found
+    assert np.all((r["E"][31:] < p.emin) | (r["E"][31:] > p.emax))
+
+
+def test_constant_potential_3d_degenerate_clusters():
+    side, v0 = 10, 0.3
+    mu = 2 - 2 * np.cos(np.arange(1, side + 1) * np.pi / (side + 1))
+    lev = np.sort((mu[:, None, None] + mu[None, :, None] + mu[None, None, :]).ravel()) + v0
+    # interval closing just above the 4th distinct level (includes 3-fold and 6-fold clusters)
+    distinct = np.unique(np.round(lev, 12))
+    emax = 0.5 * (distinct[3] + distinct[4])
+    want = lev[lev <= emax]
+    p = fw.laplace3d_constant(side, v0, emax, m0=int(1.6 * len(want)) + 4)
+    r = O.feast_scsr(p.A, None, p.emin, p.emax, p.m0, Y0=p.y0(), ne=8, ratio=100, tol_exp=11)
+    assert r["info"] == 0 and r["M"] == len(want)
+    assert np.abs(r["E"][: r["M"]] - want).max() < 1e-10 * want.max()
+    # subspace of every cluster against the closed-form eigenvectors
+    s = np.sin(np.arange(1, side + 1)[:, None] * np.arange(1, side + 1)[None, :] * np.pi / (side + 1))
+    s *= np.sqrt(2 / (side + 1))
+    full = np.einsum("ia,jb,kc->ijkabc", s, s, s).reshape(side ** 3, -1)
+    eig = (mu[:, None, None] + mu[None, :, None] + mu[None, None, :]).ravel() + v0
+    sel = eig <= emax
+    assert _angles(r["X"][:, : r["M"]], full[:, sel]) < 1e-8
+
+
+def test_generalized_problem_against_dense_and_inertia():
+    rng = np.random.default_rng(7)
+    A = fw.stencil27_spd(7, rng)
+    B = fw.diagonal_csr(rng.uniform(1.0, 2.0, A.n))
+    ev = scipy.linalg.eigh(A.to_dense(), B.to_dense(), eigvals_only=True)
+    emax = 0.5 * (ev[19] + ev[20])
+    assert O.count_below(A, B, emax) == 20
+    Y0 = fw.gaussian_block(A.n, 32, 2)
+    for solver in ["direct", "cocg"]:
+        r = O.feast_scsr(A, B, 0.0, emax, 32, Y0=Y0, ne=16, ratio=100, tol_exp=11, solver=solver)
+        assert r["info"] == 0 and r["M"] == 20
+        assert np.abs(r["E"][:20] - ev[:20]).max() < 1e-10 * ev[19]
+        X = r["X"][:, :20]
+        assert np.abs(X.T @ B.to_dense() @ X - np.eye(20)).max() < 1e-11
+
+
+def test_rii_form_equals_classic_form():
+    p = fw.laplace3d_potential(side=8, count=20, m0=32, seed=11)
+    Y0 = p.y0()
+    a = O.feast_scsr(p.A, None, p.emin, p.emax, p.m0, Y0=Y0, ne=8, ratio=100, tol_exp=11)
+    b = O.feast_scsr(p.A, None, p.emin, p.emax, p.m0, Y0=Y0, ne=8, ratio=100, tol_exp=11, rii=True)
+    assert a["info"] == b["info"] == 0 and a["M"] == b["M"]
+    assert np.abs(a["E"][: a["M"]] - b["E"][: b["M"]]).max() < 1e-11
+    # with exact solves the two forms give the same iterates
+    assert len(a["maxres"]) == len(b["maxres"])
+    ev = np.linalg.eigvalsh(p.A.to_dense())
+    assert np.abs(a["E"][: a["M"]] - ev[: a["M"]]).max() < 1e-11
+    assert O.count_below(p.A, None, p.emax) == a["M"]
+
+
+def test_initial_guess_converges_immediately():
+    p = fw.tridiag_1d(n=200, emax=0.05)
+    r = O.feast_scsr(p.A, None, p.emin, p.emax, 24, Y0=fw.gaussian_block(200, 24, 0), ratio=100)
+    assert r["info"] == 0
+    X0 = np.zeros((200, 24), order="F")
+    X0[:, : r["m0"]] = r["X"]
+    r2 = O.feast_scsr(p.A, None, p.emin, p.emax, 24, X0=X0, ratio=100)
+    assert r2["info"] == 0 and r2["loop"] <= 1 and r2["M"] == r["M"]
+
+
+def test_argument_errors():
+    A = fw.laplacian_1d(10)
+    assert O.feast_scsr(A, None, 1.0, 0.5, 4, Y0=np.zeros((10, 4)))["info"] == 200
+    assert O.feast_scsr(A, None, 0.0, 0.5, 11, Y0=np.zeros((10, 11)))["info"] == 201
+
+
+def test_no_eigenvalue_in_interval():
+    A = fw.laplacian_1d(50)
+    r = O.feast_scsr(A, None, 5.0, 6.0, 8, Y0=fw.gaussian_block(50, 8, 1), ratio=100)
+    assert r["info"] == 1 and r["M"] == 0
