@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 FEAST eigensolver: converged eigenpairs/s.
+
+Workload: 7-point 3D Laplacian on a 64^3 grid plus a seeded diagonal potential
+V ~ U[0, 0.5] (N = 262144), B = I, interval [0, Emax] around the lowest ~100
+eigenvalues, M0 = 150, Ne = 8 Gauss nodes, stop at relative residual 1e-10.
+One step = one complete FEAST solve (filter passes + Rayleigh-Ritz loops) with
+the inputs resident in HBM.  The headline runs the complex-FP32 shifted solves
+(fpm(42)=1); the FP64-solve run of the same problem is reported beside it.
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl gb300|reference]
+
+Under torchrun (N > 1) every rank solves its own replica of the workload (the
+method's independent-interval parallelism, no data exchange); value = total
+converged eigenpairs of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "converged eigenpairs/s at rel. residual 1e-10, mixed vs FP64 FEAST, 1 GB300"
+UNIT = "eigenpairs/s"
+RES_TOL = 1e-10
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--side", type=int, default=64)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(side):
+    import feast_workloads as fw
+
+    return fw.laplace3d_potential(side=side, count=100, m0=150, ne=8, ratio=100, seed=1)
+
+
+def config_dict(p, extra=None):
+    d = {"workload": f"laplace3d_7pt_{round(p.n ** (1 / 3))}^3_potential_U[0,0.5]_seed1",
+         "N": p.n, "nnz": p.A.nnz, "M0": p.m0, "Ne": p.ne, "contour_ratio_pct": p.ratio,
+         "interval": [p.emin, round(p.emax, 6)], "B": "identity", "tol": RES_TOL,
+         "inner_solver": "COCG, fpm(45)=2 (1e-2), fpm(46)=200",
+         "l2": "inputs larger than L2 (each filter block vector 2.5 GB)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def fpm_for(pkg, p, mixed, profile):
+    f = pkg.feast_init()
+    f[1], f[2], f[3], f[4], f[17] = p.ne, 10, 40, 1, p.ratio
+    f[41] = 1 if mixed else 0
+    f[44], f[45] = 2, 200
+    f[52] = 1 if profile else 0
+    return f
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index):
+        self.dev = dev_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- distributed helpers
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v, ws):
+    if ws <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- CPU baseline (oracle)
+def cpu_baseline(p, seconds, loops_hint):
+    """The FP64 oracle on the host cores, on a bounded sample of the same
+    workload: COCG shifted solves (to 1e-13, the oracle's iterative mode) of
+    `cores` start-block columns at the hardest and at a middle contour node of
+    the full N, extrapolated to all Ne x M0 solves of every filter pass of a
+    full solve (passes = loops_hint + 1).  Returns (eigenpairs/s, sample text,
+    cores)."""
+    import oracle as O
+
+    cores = O.num_threads()
+    z, _ = O.contour_gauss(p.ne, p.emin, p.emax, p.ratio / 100.0)
+    y = p.y0()
+    nodes = [int(np.argmin(z.imag)), p.ne // 2]
+    per = []
+    t_all = time.time()
+    for e in nodes:
+        cols = y[:, :cores]
+        t0 = time.time()
+        O.shifted_solve(p.A, None, z[e], cols, method="cocg", tol=1e-13)
+        per.append((time.time() - t0) / cols.shape[1] * cores)  # wall s per `cores` columns
+        if time.time() - t_all > seconds:
+            break
+    t_cols = float(np.mean(per)) / cores  # wall seconds per (node, column) with all cores busy
+    passes = loops_hint + 1
+    t_full = t_cols * p.ne * p.m0 * passes
+    M_expected = None
+    return t_full, cores, (f"COCG solves of {cores} columns at node(s) {nodes} of N={p.n}, "
+                           f"extrapolated to {p.ne}x{p.m0} solves x {passes} filter passes"), M_expected
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+
+    import paper_2002_04807_gb300 as pkg
+    from paper_2002_04807_gb300 import build
+
+    rank, ws, local = dist_setup()
+    torch.cuda.set_device(local)
+    build.build()
+    pkg.library()
+    p = workload(args.side)
+    dev = torch.device("cuda", local)
+    ia = torch.as_tensor(p.A.indptr).to(dev)
+    ja = torch.as_tensor(p.A.indices).to(dev)
+    av = torch.as_tensor(p.A.data).to(dev)
+    y0 = torch.as_tensor(np.ascontiguousarray(p.y0().T)).to(dev)  # column-major n x m0
+    x = torch.empty_like(y0)
+    stream = torch.cuda.Stream(device=dev)
+    f_mixed = fpm_for(pkg, p, True, True)
+    work = torch.empty(pkg.feast_scsr_workspace_bytes(p.n, p.A.nnz, 0, p.m0, f_mixed), dtype=torch.uint8,
+                       device=dev)
+
+    def solve(fpm):
+        x.copy_(y0)
+        r = pkg.feast_scsr_solve_dev(p.n, ia, ja, av, fpm=fpm, emin=p.emin, emax=p.emax, m0=p.m0, x=x,
+                                     work=work, stream=stream)
+        if r.info != 0:
+            raise RuntimeError(f"FEAST info {r.info}")
+        conv = int(np.sum(r.res[: r.M] <= RES_TOL))
+        return r, conv
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            solve(f_mixed)
+        torch.cuda.synchronize()
+        barrier(ws)
+        clocks = Clocks(local)
+        clocks.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        conv_total, prof_tot, loops = 0, None, []
+        t_host0 = time.time()
+        for _ in range(args.steps):
+            r, conv = solve(f_mixed)
+            conv_total += conv
+            loops.append(r.loop)
+            pr = pkg.feast_last_profile()
+            if prof_tot is None:
+                prof_tot = dict(pr)
+            else:
+                for k in ("cocg_a_ms", "cocg_b_ms", "cocg_a_launches", "cocg_b_launches", "group_iterations",
+                          "filter_ms", "project_ms", "reduce_ms", "ritz_ms", "launches"):
+                    prof_tot[k] += pr[k]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        host_s = time.time() - t_host0
+        ms = ev0.elapsed_time(ev1)
+        clk = clocks.stop()
+        barrier(ws)
+    ms_max = max_over_ranks(ms, ws)
+    conv_all = sum_over_ranks(conv_total, ws)
+    value = conv_all / (ms_max / 1000.0)
+    M = r.M
+
+    # FP64 shifted solves on the same problem
+    fp64 = None
+    if args.fp64_steps > 0:
+        f64 = fpm_for(pkg, p, False, False)
+        w64 = pkg.feast_scsr_workspace_bytes(p.n, p.A.nnz, 0, p.m0, f64)
+        if w64 > work.numel():
+            work = torch.empty(w64, dtype=torch.uint8, device=dev)
+        with torch.cuda.stream(stream):
+            solve(f64)
+            torch.cuda.synchronize()
+            barrier(ws)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c64 = 0
+            for _ in range(args.fp64_steps):
+                r64, c = solve(f64)
+                c64 += c
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms64 = max_over_ranks(e0.elapsed_time(e1), ws)
+        v64 = sum_over_ranks(c64, ws) / (ms64 / 1000.0)
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps, "loops": r64.loop,
+                "M": r64.M, "mixed_over_fp64": value / v64,
+                "max_rel_eig_diff_vs_mixed": float(np.max(np.abs(r64.E[:M] - r.E[:M]) / np.abs(r.E[:M])))}
+
+    # roofline of the dominant kernel from the per-launch events of the timed steps
+    pr = prof_tot
+    n, W, mt, sc, G = pr["n"], pr["W"], pr["mt"], pr["complex_bytes"], pr["groups"]
+    live = (p.m0 * p.ne) / (G * W)  # padded lanes are not algorithmic work
+    mat = p.A.nnz * (4 + (4 if sc == 8 else 8)) + (p.n + 1) * 4
+    tile = n * W * sc * live
+    bytes_a = pr["group_iterations"] * 3 * tile + pr["cocg_a_launches"] * mat
+    bytes_b = pr["group_iterations"] * (3 * tile + n * mt * 16 * live) + pr["cocg_b_launches"] * mat
+    gbs_a = bytes_a / (pr["cocg_a_ms"] / 1e3) / 1e9
+    gbs_b = bytes_b / (pr["cocg_b_ms"] / 1e3) / 1e9
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, peak_src = FALLBACK_HBM_GBS, "fallback"
+    if os.path.exists(peaks_path):
+        try:
+            pk = json.load(open(peaks_path))
+            for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if key in pk:
+                    peak, peak_src = float(pk[key]), "measured"
+                    break
+        except (ValueError, OSError):
+            pass
+    dom = "cocg_step_a" if pr["cocg_a_ms"] >= pr["cocg_b_ms"] else "cocg_step_b"
+    ach = gbs_a if dom == "cocg_step_a" else gbs_b
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "peak_source": peak_src,
+                "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                "cocg_step_a_gbs": gbs_a, "cocg_step_b_gbs": gbs_b,
+                "cocg_share_of_step": (pr["cocg_a_ms"] + pr["cocg_b_ms"]) / ms}
+
+    # end to end through the host C ABI (pinned host buffers, copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        import torch as T
+
+        a_h = T.as_tensor(p.A.data).pin_memory().numpy()
+        ia_h = T.as_tensor(p.A.indptr).pin_memory().numpy()
+        ja_h = T.as_tensor(p.A.indices).pin_memory().numpy()
+        y_h = T.as_tensor(p.y0()).pin_memory().numpy()
+        f_host = fpm_for(pkg, p, True, False)
+        pkg.feast_scsr_solve("F", p.n, a_h, ia_h, ja_h, fpm=f_host, emin=p.emin, emax=p.emax, m0=p.m0, x0=y_h)
+        barrier(ws)
+        t0 = time.time()
+        ce = 0
+        e2e_steps = max(1, min(args.steps, 2))
+        for _ in range(e2e_steps):
+            rh = pkg.feast_scsr_solve("F", p.n, a_h, ia_h, ja_h, fpm=f_host, emin=p.emin, emax=p.emax, m0=p.m0,
+                                      x0=y_h)
+            ce += int(np.sum(rh.res[: rh.M] <= RES_TOL))
+        t_e2e = max_over_ranks(time.time() - t0, ws)
+        h2d = p.A.data.nbytes + p.A.indptr.nbytes + p.A.indices.nbytes + y_h.nbytes
+        d2h = p.n * p.m0 * 8 + 2 * p.m0 * 8
+        e2e = {"value": sum_over_ranks(ce, ws) / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "api": "feast_scsr_solve (host buffers)",
+               "ms_per_step": 1e3 * t_e2e / e2e_steps}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t_full, cores, sample, _ = cpu_baseline(p, args.cpu_sample_seconds, int(np.median(loops)))
+        cpu = {"value": M / t_full, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "c32 solves + f64 Rayleigh-Ritz",
+               "data": "synthetic (seeded generator, no dataset)",
+               "config": config_dict(p, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                                         "M_found": M, "loops": loops, "precision": "mixed fpm(42)=1"}),
+               "e2e": e2e, "gpu_launches": int(pr["launches"]), "roofline": roofline, "cpu_baseline": cpu,
+               "fp64": fp64, "clocks": clk,
+               "phases_ms_per_step": {k: pr[k] / args.steps for k in ("filter_ms", "project_ms", "reduce_ms",
+                                                                       "ritz_ms")},
+               "host_wall_s": host_s}
+        print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import feast_workloads  # noqa: F401
+    import oracle as O
+
+    p = workload(args.side)
+    O.build()
+    loops_hint = 6
+    for _ in range(args.warmup):
+        cpu_baseline(p, min(args.cpu_sample_seconds, 5.0), loops_hint)
+    vals, samples = [], ""
+    t0 = time.time()
+    for _ in range(args.steps):
+        t_full, cores, samples, _ = cpu_baseline(p, args.cpu_sample_seconds / max(1, args.steps), loops_hint)
+        vals.append(100.0 / t_full)
+    wall = time.time() - t0
+    value = float(np.mean(vals))
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded generator, no dataset)", "impl": "reference",
+           "config": config_dict(p, {"precision": "FP64 oracle", "M_assumed": 100}),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": samples},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)

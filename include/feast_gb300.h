@@ -1,0 +1,211 @@
+/*
+ * feast_gb300.h -- C ABI of the GB300 (sm_103a) FEAST contour-filter eigensolver
+ * for real symmetric sparse problems  A x = lambda B x  (B symmetric positive
+ * definite; B = I when no B is given).
+ *
+ * Method: FEAST v4.0 user guide (Polizzi et al.), Sec. 1.2 "The FEAST
+ * Algorithm": a subspace iteration that filters a block of M0 vectors with the
+ * quadrature of the spectral projector along a half contour around
+ * [Emin, Emax] (one shifted solve (z_e B - A) Y_e = RHS per node z_e), then
+ * does a Rayleigh-Ritz step on the filtered block.  Sec. 2.2 (tips) describes
+ * the residual inverse iteration that lets the shifted solves run in single
+ * precision; Sec. 3.1 gives the driver arguments; Sec. 5 (IFEAST) the
+ * iterative inner solver.  Sec. 5.2 describes the CSR storage.
+ *
+ * Conventions shared by every entry point:
+ *  - fpm is the 64-entry parameter array of the guide's parameter table
+ *    (Sec. 2.2), C indexing fpm[i-1] = fpm(i).  Used entries:
+ *      fpm(1)  0 silent, 1 per-iteration log on stdout, n<0 append to feast<|n|>.log
+ *      fpm(2)  Ne, number of half-contour nodes (1..20, 24, 32, 40, 48, 56)
+ *      fpm(3)  stopping tolerance 10^-fpm(3) on the relative residual (0..16)
+ *      fpm(4)  maximum number of refinement loops (>= 0)
+ *      fpm(5)  1: X holds the start subspace on entry; 0: a random start block
+ *      fpm(6)  must be 1 (relative residual criterion)
+ *      fpm(16) must be 0 (Gauss-Legendre nodes)
+ *      fpm(18) ellipse ratio in percent (> 0)
+ *      fpm(42) 1: complex FP32 shifted solves (mixed precision), 0: complex FP64
+ *      fpm(45) inner solver tolerance 10^-fpm(45) (0..16)
+ *      fpm(46) inner solver iteration cap (>= 1)
+ *      fpm(60) output: total number of inner (COCG) iterations
+ *    Library options in reserved slots (0 = automatic):
+ *      fpm(50) contour nodes solved at once (node batch); fpm(51) rows per
+ *      inner-solver work item; fpm(52) seed of the random start block;
+ *      fpm(53) 1 = record per-kernel timings (see feast_last_profile).
+ *  - Return value = info (also stored in *info where that argument exists),
+ *    codes of the guide's info table (Sec. 2.2): 0 success; warnings 1 (no
+ *    eigenvalue in the interval), 2 (no convergence within fpm(4) loops),
+ *    3 (M0 too small: all Ritz values inside); errors 200 (Emin >= Emax),
+ *    201 (bad M0), 202 (bad N), 100+i (bad fpm(i)), -(100+i) (bad i-th
+ *    argument, e.g. CSR indices out of range, non-finite values), -2 (inner
+ *    solver failure), -3 (reduced eigensolver failure, e.g. B not positive
+ *    definite).  Library extension: -4 = CUDA runtime error (message in
+ *    feast_last_error()).
+ *  - "Host" arguments are ordinary CPU memory owned by the caller; "device"
+ *    arguments are CUDA global memory of the current device owned by the
+ *    caller; stream is a cudaStream_t passed as void* (NULL = legacy stream).
+ *    Entry points taking a stream enqueue work on it and return after the
+ *    results they report on the host are available.
+ *  - Dense blocks of vectors are column-major N x M0 (X(i,j) at x[i + N*j]) in
+ *    the host/driver entry points, as in the guide; the kernel-level entry
+ *    points state their own layouts.
+ */
+#ifndef FEAST_GB300_H
+#define FEAST_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Fill fpm[0..63] with the defaults of the guide's parameter table (Sec. 2.2,
+ * "feastinit").  Returns 0. */
+int feast_init(int* fpm);
+
+/* Text of the last CUDA error seen by this library in the calling thread
+ * (empty when none).  The pointer stays valid until the next call. */
+const char* feast_last_error(void);
+
+/* Half-contour Gauss-Legendre nodes and weights (guide Sec. 5.3 "Search
+ * contour", fpm(16)=0): z_e = c + r cos(t_e) + i a r sin(t_e),
+ * w_e = (omega_e r / 2)(a cos(t_e) + i sin(t_e)), t_e = (pi/2)(1 - x_e),
+ * c = (Emin+Emax)/2, r = (Emax-Emin)/2, a = ratio_pct/100, (x_e, omega_e)
+ * the Gauss-Legendre rule on [-1,1] with x descending.  z and w are host
+ * arrays of 2*ne doubles, (re, im) interleaved.  Returns 0, 102 for a bad ne,
+ * 200 for emin >= emax. */
+int feast_contour_nodes(int ne, double emin, double emax, int ratio_pct, double* z, double* w);
+
+/* Timings of the last feast_scsr_solve / feast_scsr_solve_dev of the calling
+ * thread run with fpm(53) = 1 (all zero otherwise), measured with CUDA events
+ * on the solve's stream.  out (host, 16 doubles): [0] ms in COCG step A
+ * launches, [1] ms in COCG step B launches, [2] step A launches, [3] step B
+ * launches, [4] group-iterations (column groups x COCG steps done), [5] ms in
+ * filter passes, [6] ms projecting (A Q, Q^T A Q, Q^T B Q), [7] ms in the
+ * reduced eigensolver, [8] ms forming Ritz vectors and residuals, [9] tile
+ * width W, [10] columns per group mt, [11] n, [12] bytes per complex value,
+ * [13] column groups, [14] refinement loops, [15] kernel launches issued.
+ * Library extension (the guide reports phase timings only as a text log).
+ * Returns 0. */
+int feast_last_profile(double* out);
+
+/* ---------------------------------------------------------------- drivers */
+
+/* FEAST for a real symmetric CSR problem (guide Sec. 3.1, dfeast_scsrev /
+ * dfeast_scsrgv).  All arrays are host memory; the library copies them to the
+ * device, runs the whole iteration there and copies the results back.
+ *   uplo      'F' full, 'L' lower or 'U' upper triangle stored (Sec. 5.2)
+ *   n         order of A and B (> 0)
+ *   a, ia, ja CSR of A; ia[0] is the index base (1 as in the guide, or 0);
+ *             nnz = ia[n] - ia[0]
+ *   b, ib, jb CSR of B in the same storage and base, or all NULL for B = I
+ *   fpm       parameters (in/out: fpm(60))
+ *   emin,emax search interval
+ *   m0        in: subspace size (1..n); out: live subspace size
+ *   e         [m0] out: e[0..M-1] eigenvalues inside [emin,emax] ascending,
+ *             then the outside Ritz values ascending
+ *   x         [n*m0] column-major: in: start subspace if fpm(5)=1;
+ *             out: B-orthonormal eigenvectors matching e
+ *   m         out: number of eigenvalues found in the interval
+ *   res       [m0] out: ||A x - e B x|| / ||alpha B x||, alpha = max(|emin|,|emax|)
+ *   epsout    out: relative trace change of the last loop
+ *   loop      out: refinement loops done
+ *   info      out: as the return value */
+int feast_scsr_solve(char uplo, int n, const double* a, const int* ia, const int* ja, const double* b,
+                     const int* ib, const int* jb, int* fpm, double emin, double emax, int* m0, double* e,
+                     double* x, int* m, double* res, double* epsout, int* loop, int* info);
+
+/* Device workspace, in bytes, that feast_scsr_solve_dev needs for this
+ * problem size and these parameters (fpm(2), fpm(42), fpm(50), fpm(51)). */
+size_t feast_scsr_workspace_bytes(int n, int nnz_a, int nnz_b, int m0, const int* fpm);
+
+/* Same as feast_scsr_solve with the matrices and X already on the device.
+ * d_ia/d_ja/d_a: 0-based CSR of A in full storage (device); d_ib/d_jb/d_b the
+ * same for B or NULL for B = I; d_x: device, column-major n x m0, in/out as x
+ * above.  e, res and the scalars are host memory.  d_work: device workspace of
+ * at least feast_scsr_workspace_bytes(...) bytes, 256-byte aligned; the
+ * library allocates nothing.  Work is enqueued on stream; the call returns
+ * once the results are written.  Argument errors as above; the CSR is not
+ * re-validated (use feast_scsr_solve for untrusted input). */
+int feast_scsr_solve_dev(int n, int nnz_a, const int* d_ia, const int* d_ja, const double* d_a, int nnz_b,
+                         const int* d_ib, const int* d_jb, const double* d_b, int* fpm, double emin,
+                         double emax, int* m0, double* e, double* d_x, int* m, double* res,
+                         double* epsout, int* loop, int* info, void* d_work, size_t work_bytes,
+                         void* stream);
+
+/* ---------------------------------------------------------------- kernels
+ * Device-pointer entry points of the individual steps, for testing and for
+ * callers that assemble their own iteration.  Each enqueues on stream and
+ * returns 0 or -4 (CUDA error) / -(100+i) (bad argument i); those that need
+ * scratch allocate it with cudaMallocAsync on the stream. */
+
+/* Layout of the filter's complex block vectors for nb contour nodes solved
+ * at once in precision fp64 (0: complex float, 1: complex double): a tile
+ * of W complex values per row holds mt subspace columns x nbp node lanes,
+ * node fastest; element (node e, column j, row i) sits at complex index
+ * (g*n + i)*W + (j % mt)*nbp + e with g = j / mt.  Returns 0. */
+int feast_filter_layout(int nb, int fp64, int* W, int* nbp, int* mt);
+
+/* Batched complex-shifted CSR SpMM (the inner product of every COCG step):
+ * V_e = (z_e B - A) P_e for nb nodes and m columns in one launch, in the
+ * layout of feast_filter_layout.  z: host, 2*nb doubles (re, im).  A, B:
+ * 0-based device CSR with values of the filter's real type (float if
+ * fp64 = 0, double if 1); B may be NULL (identity).  P, V: device. */
+int feast_shifted_spmm_dev(int n, const int* ia, const int* ja, const void* a, const int* ib, const int* jb,
+                           const void* b, int nb, const double* z, int m, int fp64, const void* P, void* V,
+                           void* stream);
+
+/* One filter pass over all ne nodes (guide Sec. 1.2 quadrature; Sec. 2.2
+ * residual inverse form):
+ *   rii = 0:  Q = sum_e Re(w_e Y_e),                  (z_e B - A) Y_e = R
+ *   rii = 1:  Q = X diag(rho(lam)) + sum_e Re(w_e/(z_e - lam_j) Y_e[:,j]),
+ *             rho(l) = sum_e Re(w_e/(z_e - l))
+ * with the shifted systems solved by column-batched COCG to relative residual
+ * 10^-fpm(45) or fpm(46) steps, in precision fpm(42) (1: complex float,
+ * 0: complex double).  A/B: 0-based device CSR with FP64 values (B NULL = I);
+ * R, X, Q: device row-major n x m (R(i,j) at R[i*m + j]); lam: device [m];
+ * nodes from fpm(2), fpm(18), emin, emax.  *iters (host, may be NULL): COCG
+ * steps taken (max over columns, summed over node batches). */
+int feast_filter_dev(int n, int nnz_a, const int* ia, const int* ja, const double* a, int nnz_b, const int* ib,
+                     const int* jb, const double* b, int m, const double* R, const double* X,
+                     const double* lam, int rii, const int* fpm, double emin, double emax, double* Q,
+                     int* iters, void* stream);
+
+/* C = X^T Y (m x m, row-major), X and Y device row-major n x m, FP64; the
+ * result is symmetrised ((C + C^T)/2) as the Rayleigh-Ritz matrices are. */
+int feast_gram_dev(int n, int m, const double* X, const double* Y, double* C, void* stream);
+
+/* C = A V: A device row-major n x m, V device row-major m x k, C n x k, FP64. */
+int feast_gemm_dev(int n, int m, int k, const double* A, const double* V, double* C, void* stream);
+
+/* Symmetric eigen-decomposition (cyclic Jacobi) of the device m x m matrix A
+ * (row-major, destroyed): lam ascending, V row-major with eigenvectors in
+ * columns.  *sweeps (host, may be NULL).  Returns 0, or -3 on no convergence. */
+int feast_sym_eig_dev(int m, double* A, double* lam, double* V, int* sweeps, void* stream);
+
+/* Reduced generalized problem A_q v = lambda B_q v (device row-major m x m):
+ * lam ascending with *mk (host) live values first (directions where B_q is
+ * numerically singular are dropped and sort last with values >= 1e299); V
+ * row-major m x m with V^T B_q V = I on the live columns.  Returns 0, or -3. */
+int feast_reduced_eig_dev(int m, const double* Aq, const double* Bq, double* lam, double* V, int* mk,
+                          void* stream);
+
+/* Residual block R = A X - B X diag(lam) (device row-major n x m) and
+ * res[j] = ||R_j|| / (alpha ||B x_j||) (device [m]); A/B 0-based device CSR
+ * (B NULL = I). */
+int feast_residual_dev(int n, const int* ia, const int* ja, const double* a, const int* ib, const int* jb,
+                       const double* b, int m, const double* X, const double* lam, double alpha, double* R,
+                       double* res, void* stream);
+
+/* Gradient of L = sum_k g_k lambda_k over the stored entries of a CSR
+ * pattern: grad[p] = sum_k w_k x_k[i_p] x_k[j_p] with w_k = g_k for the
+ * entries of A and w_k = -g_k lambda_k for those of B (first-order
+ * perturbation of a simple eigenpair with x^T B x = 1).  Device: ia/ja
+ * (0-based), X row-major n x m, w [m], grad [nnz].  m <= 2048. */
+int feast_eig_grad_dev(int n, const int* ia, const int* ja, int m, const double* X, const double* w,
+                       double* grad, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEAST_GB300_H */

@@ -187,6 +187,26 @@ def residuals(A, B, X, lam, emin, emax):
     return res
 
 
+def filter_block(A, B, ne, emin, emax, ratio, Y, lam=None, rii=False, solver="direct",
+                 solve_tol=1e-13):
+    """One quadrature filter pass on the block Y (n x m): classic form
+    sum_e Re(w_e (z_e B - A)^{-1} B Y), or with rii the residual-inverse form
+    on (X = Y, lam).  Returns Q (n x m, column-major)."""
+    Y = np.asfortranarray(Y, dtype=np.float64)
+    n, m = Y.shape
+    Q = np.zeros((n, m), order="F")
+    lam_a = np.zeros(m) if lam is None else _c(lam, np.float64)
+    ip, ix, v = _csr_args(A)
+    bip, bix, bv = _csr_args(B)
+    st = lib().orc_filter(C.c_int(n), _ptr(ip), _ptr(ix), _ptr(v), _ptr(bip), _ptr(bix), _ptr(bv),
+                          C.c_int(ne), C.c_double(emin), C.c_double(emax), C.c_double(ratio), C.c_int(m),
+                          _ptr(Y), _ptr(lam_a), C.c_int(1 if rii else 0), _ptr(Q),
+                          C.c_int(0 if solver == "direct" else 1), C.c_double(solve_tol))
+    if st:
+        raise RuntimeError("oracle filter failed")
+    return Q
+
+
 # ---------------------------------------------------------------- FEAST
 def feastinit():
     """fpm defaults of the guide's parameter table (C indexing fpm[i-1])."""

@@ -652,6 +652,25 @@ static int filter_rii(const ocsr* A, const ocsr* B, int ne, const double* z, con
     return st;
 }
 
+/* Exported filter passes on a block (column-major n x m): rii = 0 applies the
+ * classic quadrature to Y; rii = 1 the residual-inverse form to (X = Y, lam). */
+int orc_filter(int n, const int* ip, const int* ix, const double* av,
+               const int* bip, const int* bix, const double* bv,
+               int ne, double emin, double emax, double ratio, int m, const double* Y,
+               const double* lam, int rii, double* Q, int solver, double solve_tol)
+{
+    ocsr A = {n, ip, ix, av}, Bm = {n, bip, bix, bv};
+    const ocsr* B = bip ? &Bm : NULL;
+    double* z = (double*)malloc(sizeof(double) * 2 * ne);
+    double* w = (double*)malloc(sizeof(double) * 2 * ne);
+    orc_contour_gauss(ne, emin, emax, ratio, z, w);
+    int st = rii ? filter_rii(&A, B, ne, z, w, m, Y, lam, Q, solver, solve_tol, NULL)
+                 : filter_classic(&A, B, ne, z, w, m, Y, Q, solver, solve_tol, NULL);
+    free(z);
+    free(w);
+    return st;
+}
+
 /* ------------------------------------------------------------------------ */
 /* FEAST for real symmetric CSR problems (dfeast_scsr{ev,gv} semantics).
  * fpm is the 64-entry parameter array, C indexing fpm[i-1] = fpm(i).

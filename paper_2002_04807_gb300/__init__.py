@@ -1,0 +1,36 @@
+"""GB300-native FEAST contour-filter eigensolver (real symmetric sparse problems).
+
+Thin Python binding over the C ABI of ``libfeast_gb300.so`` (declared in
+``include/feast_gb300.h``).  Every step of the method runs in the library's
+CUDA kernels; this module only marshals arguments: numpy arrays for the host
+entry points, torch CUDA tensors (device memory, current stream) for the
+device entry points.  There is no CPU fallback: if the library is missing or
+no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+from ._lib import (  # noqa: F401
+    FeastError,
+    FeastResult,
+    feast_contour_nodes,
+    feast_eig_grad_dev,
+    feast_filter_dev,
+    feast_filter_layout,
+    feast_gemm_dev,
+    feast_gram_dev,
+    feast_init,
+    feast_last_error,
+    feast_last_profile,
+    feast_reduced_eig_dev,
+    feast_residual_dev,
+    feast_scsr_solve,
+    feast_scsr_solve_dev,
+    feast_scsr_workspace_bytes,
+    feast_shifted_spmm_dev,
+    feast_sym_eig_dev,
+    library,
+    library_path,
+)
+
+__all__ = [n for n in dir() if n.startswith("feast_")] + ["FeastError", "FeastResult", "library",
+                                                          "library_path"]

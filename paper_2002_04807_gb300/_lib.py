@@ -1,0 +1,274 @@
+"""ctypes marshalling for libfeast_gb300.so.  Names match the C ABI."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libfeast_gb300.so")
+_lock = threading.Lock()
+_lib = None
+
+_i = C.c_int
+_d = C.c_double
+_p = C.c_void_p
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "feast_init": (_i, [_p]),
+    "feast_last_error": (C.c_char_p, []),
+    "feast_contour_nodes": (_i, [_i, _d, _d, _i, _p, _p]),
+    "feast_scsr_solve": (_i, [C.c_char, _i, _p, _p, _p, _p, _p, _p, _p, _d, _d, _p, _p, _p, _p, _p, _p, _p,
+                              _p]),
+    "feast_scsr_workspace_bytes": (C.c_size_t, [_i, _i, _i, _i, _p]),
+    "feast_scsr_solve_dev": (_i, [_i, _i, _p, _p, _p, _i, _p, _p, _p, _p, _d, _d, _p, _p, _p, _p, _p, _p, _p,
+                                  _p, _p, C.c_size_t, _p]),
+    "feast_filter_layout": (_i, [_i, _i, _p, _p, _p]),
+    "feast_shifted_spmm_dev": (_i, [_i, _p, _p, _p, _p, _p, _p, _i, _p, _i, _i, _p, _p, _p]),
+    "feast_filter_dev": (_i, [_i, _i, _p, _p, _p, _i, _p, _p, _p, _i, _p, _p, _p, _i, _p, _d, _d, _p, _p, _p]),
+    "feast_gram_dev": (_i, [_i, _i, _p, _p, _p, _p]),
+    "feast_gemm_dev": (_i, [_i, _i, _i, _p, _p, _p, _p]),
+    "feast_sym_eig_dev": (_i, [_i, _p, _p, _p, _p, _p]),
+    "feast_reduced_eig_dev": (_i, [_i, _p, _p, _p, _p, _p, _p]),
+    "feast_residual_dev": (_i, [_i, _p, _p, _p, _p, _p, _p, _i, _p, _p, _d, _p, _p, _p]),
+    "feast_eig_grad_dev": (_i, [_i, _p, _p, _i, _p, _p, _p, _p]),
+    "feast_last_profile": (_i, [_p]),
+}
+
+
+class FeastError(RuntimeError):
+    pass
+
+
+def library_path() -> str:
+    return _LIBPATH
+
+
+def library():
+    """Load libfeast_gb300.so (built by paper_2002_04807_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIBPATH):
+                raise FeastError(f"{_LIBPATH} is missing: build it with "
+                                 "`python -c 'import __graft_entry__ as g; g.build()'`")
+            lib = C.CDLL(_LIBPATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def feast_last_error() -> str:
+    return library().feast_last_error().decode()
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(a.data_ptr())  # torch tensor
+
+
+def _stream(stream=None):
+    import torch
+
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        msg = feast_last_error() if code == -4 else ""
+        raise FeastError(f"{what} returned {code} {msg}".strip())
+
+
+def _dev(t, dtype):
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise FeastError(f"expected a contiguous CUDA tensor of {dtype}")
+    return t
+
+
+# ---------------------------------------------------------------- host-side helpers
+PROFILE_KEYS = ["cocg_a_ms", "cocg_b_ms", "cocg_a_launches", "cocg_b_launches", "group_iterations",
+                "filter_ms", "project_ms", "reduce_ms", "ritz_ms", "W", "mt", "n", "complex_bytes", "groups",
+                "loops", "launches"]
+
+
+def feast_last_profile() -> dict:
+    out = np.zeros(16)
+    library().feast_last_profile(_ptr(out))
+    return dict(zip(PROFILE_KEYS, out.tolist()))
+
+
+def feast_init() -> np.ndarray:
+    fpm = np.zeros(64, dtype=np.int32)
+    library().feast_init(_ptr(fpm))
+    return fpm
+
+
+def feast_contour_nodes(ne: int, emin: float, emax: float, ratio_pct: int):
+    z = np.zeros(2 * ne)
+    w = np.zeros(2 * ne)
+    _check(library().feast_contour_nodes(ne, emin, emax, ratio_pct, _ptr(z), _ptr(w)), "feast_contour_nodes")
+    return z[0::2] + 1j * z[1::2], w[0::2] + 1j * w[1::2]
+
+
+def feast_filter_layout(nb: int, fp64: bool):
+    W, nbp, mt = _i(), _i(), _i()
+    _check(library().feast_filter_layout(nb, int(fp64), C.byref(W), C.byref(nbp), C.byref(mt)),
+           "feast_filter_layout")
+    return W.value, nbp.value, mt.value
+
+
+@dataclass
+class FeastResult:
+    info: int
+    E: np.ndarray
+    X: np.ndarray  # (n, m0') column-major
+    res: np.ndarray
+    M: int
+    loop: int
+    epsout: float
+    m0: int
+    fpm: np.ndarray
+
+
+def _fpm(fpm):
+    f = feast_init() if fpm is None else np.array(fpm, dtype=np.int32, copy=True)
+    if f.shape != (64,):
+        raise FeastError("fpm must have 64 entries")
+    return np.ascontiguousarray(f)
+
+
+def feast_scsr_solve(uplo: str, n: int, a, ia, ja, b=None, ib=None, jb=None, fpm=None, emin=0.0, emax=1.0,
+                     m0: int = 1, x0=None) -> FeastResult:
+    """Host driver: CSR arrays (numpy, base ia[0] in {0,1}), returns a FeastResult.
+    x0 (n x m0) is the start subspace when fpm(5)=1."""
+    f = _fpm(fpm)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    ia = np.ascontiguousarray(ia, dtype=np.int32)
+    ja = np.ascontiguousarray(ja, dtype=np.int32)
+    if b is not None:
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        ib = np.ascontiguousarray(ib, dtype=np.int32)
+        jb = np.ascontiguousarray(jb, dtype=np.int32)
+    x = np.zeros((n, m0), order="F")
+    if x0 is not None:
+        x[:] = x0
+    E = np.zeros(m0)
+    res = np.zeros(m0)
+    M, loop, info, mm = _i(0), _i(0), _i(0), _i(m0)
+    eps = _d(0)
+    library().feast_scsr_solve(uplo.encode(), n, _ptr(a), _ptr(ia), _ptr(ja), _ptr(b), _ptr(ib), _ptr(jb),
+                               _ptr(f), emin, emax, C.byref(mm), _ptr(E), _ptr(x), C.byref(M), _ptr(res),
+                               C.byref(eps), C.byref(loop), C.byref(info))
+    k = mm.value
+    if info.value == -4:
+        raise FeastError("feast_scsr_solve: " + feast_last_error())
+    return FeastResult(info.value, E[:k].copy(), np.asfortranarray(x[:, :k]), res[:k].copy(), M.value,
+                       loop.value, eps.value, k, f)
+
+
+def feast_scsr_workspace_bytes(n: int, nnz_a: int, nnz_b: int, m0: int, fpm) -> int:
+    f = _fpm(fpm)
+    return int(library().feast_scsr_workspace_bytes(n, nnz_a, nnz_b, m0, _ptr(f)))
+
+
+def feast_scsr_solve_dev(n: int, ia, ja, a, ib=None, jb=None, b=None, fpm=None, emin=0.0, emax=1.0,
+                         m0: int = 1, x=None, work=None, stream=None) -> FeastResult:
+    """Device driver: 0-based CSR as torch CUDA tensors (int32 / float64), x a
+    CUDA float64 tensor holding the column-major n x m0 block (in/out; shape
+    (m0, n) row-major is the same memory).  work: optional preallocated uint8
+    CUDA tensor."""
+    import torch
+
+    f = _fpm(fpm)
+    ia, ja, a = _dev(ia, torch.int32), _dev(ja, torch.int32), _dev(a, torch.float64)
+    nnzb = 0
+    if b is not None:
+        ib, jb, b = _dev(ib, torch.int32), _dev(jb, torch.int32), _dev(b, torch.float64)
+        nnzb = b.numel()
+    if x is None:
+        x = torch.zeros((m0, n), dtype=torch.float64, device=a.device)
+    x = _dev(x, torch.float64)
+    need = feast_scsr_workspace_bytes(n, a.numel(), nnzb, m0, f)
+    if work is None or work.numel() < need:
+        work = torch.empty(need, dtype=torch.uint8, device=a.device)
+    E = np.zeros(m0)
+    res = np.zeros(m0)
+    M, loop, info, mm = _i(0), _i(0), _i(0), _i(m0)
+    eps = _d(0)
+    library().feast_scsr_solve_dev(n, a.numel(), _ptr(ia), _ptr(ja), _ptr(a), nnzb, _ptr(ib), _ptr(jb), _ptr(b),
+                                   _ptr(f), emin, emax, C.byref(mm), _ptr(E), _ptr(x), C.byref(M), _ptr(res),
+                                   C.byref(eps), C.byref(loop), C.byref(info), _ptr(work), work.numel(),
+                                   _stream(stream))
+    if info.value == -4:
+        raise FeastError("feast_scsr_solve_dev: " + feast_last_error())
+    k = mm.value
+    return FeastResult(info.value, E[:k].copy(), x, res[:k].copy(), M.value, loop.value, eps.value, k, f)
+
+
+# ---------------------------------------------------------------- kernel-level entry points
+def feast_shifted_spmm_dev(n, ia, ja, a, ib, jb, b, z, m, fp64, P, V, stream=None):
+    z = np.ascontiguousarray(np.column_stack([np.real(z), np.imag(z)]).ravel(), dtype=np.float64)
+    nb = len(z) // 2
+    _check(library().feast_shifted_spmm_dev(n, _ptr(ia), _ptr(ja), _ptr(a), _ptr(ib), _ptr(jb), _ptr(b), nb,
+                                            _ptr(z), m, int(fp64), _ptr(P), _ptr(V), _stream(stream)),
+           "feast_shifted_spmm_dev")
+
+
+def feast_filter_dev(n, ia, ja, a, ib, jb, b, m, R, X, lam, rii, fpm, emin, emax, Q, stream=None) -> int:
+    f = _fpm(fpm)
+    it = _i(0)
+    _check(library().feast_filter_dev(n, a.numel(), _ptr(ia), _ptr(ja), _ptr(a), 0 if b is None else b.numel(),
+                                      _ptr(ib), _ptr(jb), _ptr(b), m, _ptr(R), _ptr(X), _ptr(lam), int(rii),
+                                      _ptr(f), emin, emax, _ptr(Q), C.byref(it), _stream(stream)),
+           "feast_filter_dev")
+    return it.value
+
+
+def feast_gram_dev(n, m, X, Y, Cm, stream=None):
+    _check(library().feast_gram_dev(n, m, _ptr(X), _ptr(Y), _ptr(Cm), _stream(stream)), "feast_gram_dev")
+
+
+def feast_gemm_dev(n, m, k, A, V, Cm, stream=None):
+    _check(library().feast_gemm_dev(n, m, k, _ptr(A), _ptr(V), _ptr(Cm), _stream(stream)), "feast_gemm_dev")
+
+
+def feast_sym_eig_dev(m, A, lam, V, stream=None) -> int:
+    sw = _i(0)
+    _check(library().feast_sym_eig_dev(m, _ptr(A), _ptr(lam), _ptr(V), C.byref(sw), _stream(stream)),
+           "feast_sym_eig_dev")
+    return sw.value
+
+
+def feast_reduced_eig_dev(m, Aq, Bq, lam, V, stream=None) -> int:
+    mk = _i(0)
+    _check(library().feast_reduced_eig_dev(m, _ptr(Aq), _ptr(Bq), _ptr(lam), _ptr(V), C.byref(mk),
+                                           _stream(stream)), "feast_reduced_eig_dev")
+    return mk.value
+
+
+def feast_residual_dev(n, ia, ja, a, ib, jb, b, m, X, lam, alpha, R, res, stream=None):
+    _check(library().feast_residual_dev(n, _ptr(ia), _ptr(ja), _ptr(a), _ptr(ib), _ptr(jb), _ptr(b), m, _ptr(X),
+                                        _ptr(lam), alpha, _ptr(R), _ptr(res), _stream(stream)),
+           "feast_residual_dev")
+
+
+def feast_eig_grad_dev(n, ia, ja, m, X, w, grad, stream=None):
+    _check(library().feast_eig_grad_dev(n, _ptr(ia), _ptr(ja), m, _ptr(X), _ptr(w), _ptr(grad), _stream(stream)),
+           "feast_eig_grad_dev")

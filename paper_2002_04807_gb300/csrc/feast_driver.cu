@@ -1,0 +1,1010 @@
+// Host side of libfeast_gb300: argument checks, contour nodes, the device
+// memory plan and the FEAST subspace iteration that drives the kernels.
+//
+// FEAST v4.0 guide: Sec. 1.2 (algorithm), Sec. 2.2 (fpm and info tables,
+// residual inverse iteration and mixed precision tips), Sec. 3.1 (driver
+// arguments), Sec. 5.2 (CSR storage), Sec. 5.3 (search contour).
+//
+// One iteration, all on the device:
+//   filter  : COCG over every (node, column) pair, Q accumulated in FP64
+//   project : T = A Q, A_Q = Q^T T, B_Q = Q^T (B Q)           (FP64)
+//   reduce  : A_Q v = lambda B_Q v by two Jacobi decompositions (FP64)
+//   Ritz    : X = Q V, R = A X - B X Lambda, residual norms    (FP64)
+// and only the m0 Ritz values and residuals come back to the host, which
+// decides convergence.  The first filter pass applies the quadrature to the
+// start block (right-hand side B Y); every later pass uses the residual
+// inverse form (right-hand side R, see k_filter.cu), which keeps the
+// single-precision solves from limiting the FP64 accuracy of the result.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/feast_gb300.h"
+#include "feast_internal.cuh"
+
+using namespace feast;
+
+static thread_local std::string g_err;
+
+extern "C" const char* feast_last_error(void) { return g_err.c_str(); }
+
+static int cuda_fail(cudaError_t e, const char* where)
+{
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return -4;
+}
+
+#define CK(x)                                             \
+    do {                                                  \
+        cudaError_t _e = (x);                             \
+        if (_e != cudaSuccess) return cuda_fail(_e, #x);  \
+    } while (0)
+
+// ---------------------------------------------------------------- fpm
+extern "C" int feast_init(int* fpm)
+{
+    for (int i = 0; i < 64; ++i) fpm[i] = 0;
+    const int def[][2] = {{1, 0},  {2, 8},  {3, 12}, {4, 20},  {5, 0},  {6, 1},  {8, 16},
+                          {10, 1}, {14, 0}, {15, 2}, {16, 0},  {18, 30}, {19, 0}, {40, 0},
+                          {41, 1}, {42, 1}, {43, 0}, {45, 1},  {46, 40}};
+    for (auto& d : def) fpm[d[0] - 1] = d[1];
+    return 0;
+}
+
+static bool gauss_ne_ok(int ne)
+{
+    return (ne >= 1 && ne <= 20) || ne == 24 || ne == 32 || ne == 40 || ne == 48 || ne == 56;
+}
+
+static int check_fpm(const int* fpm)
+{
+    if (!gauss_ne_ok(fpm[1])) return 102;
+    if (fpm[2] < 0 || fpm[2] > 16) return 103;
+    if (fpm[3] < 0) return 104;
+    if (fpm[4] != 0 && fpm[4] != 1) return 105;
+    if (fpm[5] != 0 && fpm[5] != 1) return 106;
+    if (fpm[15] != 0) return 116;
+    if (fpm[17] <= 0) return 118;
+    if (fpm[41] != 0 && fpm[41] != 1) return 142;
+    if (fpm[44] < 0 || fpm[44] > 16) return 145;
+    if (fpm[45] < 1) return 146;
+    if (fpm[49] < 0) return 150;
+    if (fpm[50] < 0) return 151;
+    return 0;
+}
+
+// ---------------------------------------------------------------- contour
+// Gauss-Legendre rule by Newton's method on P_n, started from Tricomi's
+// asymptotic roots; P_n and P_n' from the three-term recurrence.
+static void gl_rule(int n, std::vector<double>& x, std::vector<double>& w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int k = 1; k <= n; ++k) {
+        const double th = M_PI * (4.0 * k - 1.0) / (4.0 * n + 2.0);
+        double t = (1.0 - (n - 1.0) / (8.0 * n * n * n)) * std::cos(th);
+        double d = 0.0;
+        for (int it = 0; it < 60; ++it) {
+            double pm = 1.0, p = t;  // P_0, P_1
+            for (int j = 2; j <= n; ++j) {
+                const double pn = ((2.0 * j - 1.0) * t * p - (j - 1.0) * pm) / j;
+                pm = p;
+                p = pn;
+            }
+            if (n == 1) { p = t; pm = 1.0; }
+            d = n * (pm - t * p) / (1.0 - t * t);
+            const double step = p / d;
+            t -= step;
+            if (std::fabs(step) <= 1e-17 * (1.0 + std::fabs(t))) break;
+        }
+        double pm = 1.0, p = t;
+        for (int j = 2; j <= n; ++j) {
+            const double pn = ((2.0 * j - 1.0) * t * p - (j - 1.0) * pm) / j;
+            pm = p;
+            p = pn;
+        }
+        if (n == 1) { p = t; pm = 1.0; }
+        d = n * (pm - t * p) / (1.0 - t * t);
+        x[k - 1] = t;
+        w[k - 1] = 2.0 / ((1.0 - t * t) * d * d);
+    }
+}
+
+// zw[4e..4e+3] = (Re z_e, Im z_e, Re w_e, Im w_e)
+static void contour(int ne, double emin, double emax, double ratio, std::vector<double>& zw)
+{
+    std::vector<double> x, om;
+    gl_rule(ne, x, om);
+    const double c = 0.5 * (emin + emax), r = 0.5 * (emax - emin);
+    zw.assign(4 * (size_t)ne, 0.0);
+    for (int e = 0; e < ne; ++e) {
+        const double th = 0.5 * M_PI * (1.0 - x[e]);
+        const double ct = std::cos(th), st = std::sin(th);
+        zw[4 * e] = c + r * ct;
+        zw[4 * e + 1] = ratio * r * st;
+        zw[4 * e + 2] = 0.5 * om[e] * r * ratio * ct;
+        zw[4 * e + 3] = 0.5 * om[e] * r * st;
+    }
+}
+
+extern "C" int feast_contour_nodes(int ne, double emin, double emax, int ratio_pct, double* z, double* w)
+{
+    if (!gauss_ne_ok(ne)) return 102;
+    if (!(emin < emax)) return 200;
+    std::vector<double> zw;
+    contour(ne, emin, emax, ratio_pct / 100.0, zw);
+    for (int e = 0; e < ne; ++e) {
+        z[2 * e] = zw[4 * e];
+        z[2 * e + 1] = zw[4 * e + 1];
+        w[2 * e] = zw[4 * e + 2];
+        w[2 * e + 1] = zw[4 * e + 3];
+    }
+    return 0;
+}
+
+extern "C" int feast_filter_layout(int nb, int fp64, int* W, int* nbp, int* mt)
+{
+    int p = 1;
+    while (p < nb) p <<= 1;
+    if (p > 32 || nb < 1) return -101;
+    const int w = fp64 ? std::max(16, p) : std::max(32, p);
+    *W = w;
+    *nbp = p;
+    *mt = w / p;
+    return 0;
+}
+
+// ---------------------------------------------------------------- memory plan
+namespace {
+
+struct Plan {
+    int n = 0, m0 = 0, ne = 0, nbp = 0, nbatch = 0, W = 0, mt = 0, G = 0, RB = 0, nrb = 0;
+    long long nitems = 0;
+    bool fp64 = false, hasB = false;
+    int nnzA = 0, nnzB = 0;
+    int ksplit = 1;
+    size_t gpart = 0, rpart = 0;
+};
+
+struct Bufs {
+    void *r = nullptr, *p0 = nullptr, *p1 = nullptr;
+    ColState* cs = nullptr;
+    double* part = nullptr;
+    unsigned* grp_count = nullptr;
+    int* grp_done = nullptr;
+    int* iter_max = nullptr;  // [nbatch]
+    int* groups_left = nullptr;
+    unsigned long long* work = nullptr;
+    FiltProb* probs = nullptr;
+    float *avf = nullptr, *bvf = nullptr;
+    double* zw = nullptr;
+    double *Y = nullptr, *Q = nullptr, *X = nullptr, *T = nullptr, *T2 = nullptr;
+    double *Aq = nullptr, *Bq = nullptr, *Vr = nullptr, *lam = nullptr, *res = nullptr;
+    double *gpart = nullptr, *rpart = nullptr;
+    int* mk = nullptr;
+    int* perm = nullptr;
+    void* eig = nullptr;
+};
+
+size_t cplx_bytes(const Plan& P) { return P.fp64 ? 16 : 8; }
+
+Plan make_plan(int n, int nnzA, int nnzB, int m0, const int* fpm, bool filter_only = false)
+{
+    Plan P;
+    P.n = n;
+    P.m0 = m0;
+    P.ne = fpm[1];
+    P.fp64 = fpm[41] == 0;
+    P.hasB = nnzB > 0;
+    P.nnzA = nnzA;
+    P.nnzB = nnzB;
+    int nb = fpm[49] > 0 ? std::min(fpm[49], P.ne) : std::min(P.ne, 16);
+    for (;;) {
+        feast_filter_layout(nb, P.fp64 ? 1 : 0, &P.W, &P.nbp, &P.mt);
+        P.G = (m0 + P.mt - 1) / P.mt;
+        const double bytes = 3.0 * P.G * (double)n * P.W * cplx_bytes(P);
+        if (fpm[49] > 0 || nb <= 1 || bytes <= 128e9) break;
+        nb = (nb + 1) / 2;
+    }
+    P.nbatch = (P.ne + P.nbp - 1) / P.nbp;
+    P.RB = fpm[50] > 0 ? fpm[50] : 256;
+    P.nrb = (n + P.RB - 1) / P.RB;
+    P.nitems = (long long)P.G * P.nrb;
+    if (!filter_only) {
+        P.gpart = gram_partial_doubles(n, m0, &P.ksplit, num_sms());
+        P.rpart = residual_partial_doubles(n, m0);
+    }
+    return P;
+}
+
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base((char*)b) {}
+    template <typename T>
+    T* take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? (T*)(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+size_t carve(const Plan& P, void* base, Bufs& B, bool filter_only = false)
+{
+    Carver c(base);
+    const size_t vec = (size_t)P.G * P.n * P.W * cplx_bytes(P);
+    B.r = c.take<char>(vec);
+    B.p0 = c.take<char>(vec);
+    B.p1 = c.take<char>(vec);
+    B.cs = c.take<ColState>((size_t)P.G * P.W);
+    B.part = c.take<double>((size_t)P.nitems * P.W * 4);
+    B.grp_count = c.take<unsigned>(P.G);
+    B.grp_done = c.take<int>(P.G);
+    B.iter_max = c.take<int>(P.nbatch);
+    B.groups_left = c.take<int>(1);
+    B.work = c.take<unsigned long long>(1);
+    B.probs = c.take<FiltProb>(1);
+    if (!P.fp64) {
+        B.avf = c.take<float>(P.nnzA);
+        if (P.hasB) B.bvf = c.take<float>(P.nnzB);
+    }
+    B.zw = c.take<double>(4 * (size_t)P.ne);
+    if (filter_only) return c.off + 256;
+    const size_t blk = (size_t)P.n * P.m0;
+    B.Y = c.take<double>(blk);
+    B.Q = c.take<double>(blk);
+    B.X = c.take<double>(blk);
+    B.T = c.take<double>(blk);
+    if (P.hasB) B.T2 = c.take<double>(blk);
+    const size_t mm = (size_t)P.m0 * P.m0;
+    B.Aq = c.take<double>(mm);
+    B.Bq = c.take<double>(mm);
+    B.Vr = c.take<double>(mm);
+    B.lam = c.take<double>(P.m0);
+    B.res = c.take<double>(P.m0);
+    B.gpart = c.take<double>(P.gpart);
+    B.rpart = c.take<double>(P.rpart);
+    B.mk = c.take<int>(1);
+    B.perm = c.take<int>(P.m0);
+    B.eig = c.take<char>(reduced_work_bytes(P.m0));
+    return c.off + 256;
+}
+
+// ---------------------------------------------------------------- small kernels
+__global__ void k_col_to_row(int n, int m, const double* xc, double* xr)
+{
+    const long long total = (long long)n * m;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / m), j = (int)(idx % m);
+        xr[idx] = xc[(size_t)j * n + i];
+    }
+}
+
+// out column c (column-major) = X row-major column perm[c] for c < mk, else 0
+__global__ void k_gather_cols(int n, int m, int mk, const double* xr, const int* perm, double* xc)
+{
+    const long long total = (long long)n * m;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(idx / n), i = (int)(idx % n);
+        xc[idx] = c < mk ? xr[(size_t)i * m + perm[c]] : 0.0;
+    }
+}
+
+// Random start block: standard normal values from a counter-based hash
+// (splitmix64 of seed and element index) and the Box-Muller transform.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_random_block(long long total, unsigned long long seed, double* y)
+{
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long h1 = splitmix64(seed * 0x100000001B3ull + 2 * (unsigned long long)idx);
+        const unsigned long long h2 = splitmix64(seed * 0x100000001B3ull + 2 * (unsigned long long)idx + 1);
+        const double u1 = ((h1 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        const double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);
+        y[idx] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    }
+}
+
+// Optional per-kernel timing (fpm(53) = 1): CUDA events recorded on the
+// solve's stream around every COCG launch and every Rayleigh-Ritz phase.
+struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<std::pair<size_t, size_t>> a, b;  // cocg_step_a / cocg_step_b launches
+    std::vector<std::pair<int, std::pair<size_t, size_t>>> phase;
+    double out[16] = {0};
+    cudaEvent_t ev()
+    {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    size_t mark(cudaStream_t s)
+    {
+        cudaEvent_t e = ev();
+        cudaEventRecord(e, s);
+        return used - 1;
+    }
+    void reset(bool enable)
+    {
+        on = enable;
+        used = 0;
+        a.clear();
+        b.clear();
+        phase.clear();
+        for (double& v : out) v = 0.0;
+    }
+    double ms(size_t i, size_t j)
+    {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, pool[i], pool[j]);
+        return t;
+    }
+};
+thread_local Prof g_prof;
+
+int grid_for(long long total)
+{
+    long long b = (total + 255) / 256;
+    const long long cap = (long long)num_sms() * 8;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+struct Csr {
+    int n = 0, nnz = 0;
+    const int* ia = nullptr;
+    const int* ja = nullptr;
+    const double* v = nullptr;
+};
+
+// One filter pass (all node batches) into B.Q.  rii selects the right-hand
+// side R (device row-major n x m0 in B.Y) and the coefficients.
+int filter_pass(const Plan& P, Bufs& B, int rii, const double* R, const double* X, int maxit, double tol,
+                cudaStream_t s)
+{
+    FilterArgs fa;
+    fa.probs = B.probs;
+    fa.nprob = 1;
+    fa.nitems = P.nitems;
+    fa.W = P.W;
+    fa.nbp = P.nbp;
+    fa.mt = P.mt;
+    fa.RB = P.RB;
+    fa.r = B.r;
+    fa.p0 = B.p0;
+    fa.p1 = B.p1;
+    fa.cs = B.cs;
+    fa.part = B.part;
+    fa.grp_count = B.grp_count;
+    fa.grp_done = B.grp_done;
+    fa.Q = B.Q;
+    fa.tol2 = tol * tol;
+    fa.groups_left = B.groups_left;
+    fa.work = B.work;
+    const int grid = (int)std::min<long long>(filter_grid(P.fp64, P.W), P.nitems);
+    CK(cudaMemsetAsync(B.iter_max, 0, sizeof(int) * P.nbatch, s));
+    int left = P.G;
+    for (int b = 0; b < P.nbatch; ++b) {
+        fa.iter_max = B.iter_max + b;
+        CK(cudaMemsetAsync(B.grp_count, 0, sizeof(unsigned) * P.G, s));
+        CK(cudaMemsetAsync(B.grp_done, 0, sizeof(int) * P.G, s));
+        CK(cudaMemcpyAsync(B.groups_left, &left, sizeof(int), cudaMemcpyHostToDevice, s));
+        CK(launch_colstate_init(fa, b * P.nbp, rii, s));
+        CK(launch_filter_init(fa, P.fp64, R, X, rii, b == 0, grid, s));
+        for (int k = 0; k < maxit; ++k) {
+            if (g_prof.on) {
+                const size_t e0 = g_prof.mark(s);
+                CK(launch_cocg_step_a(fa, P.fp64, k, grid, s));
+                const size_t e1 = g_prof.mark(s);
+                CK(launch_cocg_step_b(fa, P.fp64, k, grid, s));
+                const size_t e2 = g_prof.mark(s);
+                g_prof.a.push_back({e0, e1});
+                g_prof.b.push_back({e1, e2});
+            } else {
+                CK(launch_cocg_step_a(fa, P.fp64, k, grid, s));
+                CK(launch_cocg_step_b(fa, P.fp64, k, grid, s));
+            }
+            // every few steps: stop launching once no group iterates any more
+            if ((k & 7) == 7 && k + 1 < maxit) {
+                int h = 1;
+                CK(cudaMemcpyAsync(&h, B.groups_left, sizeof(int), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                if (h <= 0) break;
+            }
+        }
+    }
+    return 0;
+}
+
+int setup_filter(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, const std::vector<double>& zw,
+                 const double* lam, const int* mk, cudaStream_t s)
+{
+    CK(cudaMemcpyAsync(B.zw, zw.data(), sizeof(double) * zw.size(), cudaMemcpyHostToDevice, s));
+    if (!P.fp64) {
+        CK(launch_cast_values(A.v, B.avf, A.nnz, s));
+        if (P.hasB) CK(launch_cast_values(Bm.v, B.bvf, Bm.nnz, s));
+    }
+    FiltProb fp;
+    memset(&fp, 0, sizeof(fp));
+    fp.n = P.n;
+    fp.m0 = P.m0;
+    fp.G = P.G;
+    fp.nrb = P.nrb;
+    fp.item0 = 0;
+    fp.vec_off = 0;
+    fp.col_off = 0;
+    fp.grp_off = 0;
+    fp.q_off = 0;
+    fp.ia = A.ia;
+    fp.ja = A.ja;
+    fp.av = P.fp64 ? (const void*)A.v : (const void*)B.avf;
+    fp.ib = P.hasB ? Bm.ia : nullptr;
+    fp.jb = P.hasB ? Bm.ja : nullptr;
+    fp.bv = P.hasB ? (P.fp64 ? (const void*)Bm.v : (const void*)B.bvf) : nullptr;
+    fp.zw = B.zw;
+    fp.lam = lam;
+    fp.mk = mk;
+    fp.ne = P.ne;
+    CK(cudaMemcpyAsync(B.probs, &fp, sizeof(fp), cudaMemcpyHostToDevice, s));
+    // the host copy of fp goes out of scope: make the upload complete first
+    CK(cudaStreamSynchronize(s));
+    return 0;
+}
+
+void log_line(int lvl, const char* text)
+{
+    if (lvl == 0) return;
+    if (lvl > 0) {
+        fputs(text, stdout);
+        fflush(stdout);
+        return;
+    }
+    char name[64];
+    snprintf(name, sizeof(name), "feast%d.log", -lvl);
+    FILE* f = fopen(name, "a");
+    if (f) {
+        fputs(text, f);
+        fclose(f);
+    }
+}
+
+// The FEAST iteration on device data.  x_dev: column-major n x m0 in/out.
+int run_feast(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, int* fpm, double emin, double emax, int* m0io,
+              double* e_host, double* x_dev, int* M_out, double* res_host, double* epsout, int* loop_out,
+              cudaStream_t s)
+{
+    const int n = P.n, m0 = P.m0, ne = P.ne;
+    const double alpha = std::max(std::fabs(emin), std::fabs(emax));
+    const double eps = std::pow(10.0, -fpm[2]);
+    const double tol = std::pow(10.0, -fpm[44]);
+    const int maxit = fpm[45], maxloop = fpm[3];
+    std::vector<double> zw;
+    contour(ne, emin, emax, fpm[17] / 100.0, zw);
+    int st = setup_filter(P, B, A, Bm, zw, B.lam, B.mk, s);
+    if (st) return st;
+    const size_t blk = (size_t)n * m0;
+    // start block Y (row-major) and the first right-hand side B Y
+    if (fpm[4] == 1) {
+        k_col_to_row<<<grid_for(blk), 256, 0, s>>>(n, m0, x_dev, B.Y);
+        count_launches(1);
+    } else {
+        const unsigned long long seed = fpm[51] ? (unsigned long long)fpm[51] : 0x5EEDull;
+        k_random_block<<<grid_for(blk), 256, 0, s>>>((long long)blk, seed, B.Y);
+        count_launches(1);
+    }
+    CK(cudaGetLastError());
+    double* R = B.Y;
+    if (P.hasB) {
+        CK(launch_spmm_f64(n, m0, Bm.ia, Bm.ja, Bm.v, B.Y, B.T, s));
+        R = B.T;
+    }
+    size_t ph0 = g_prof.on ? g_prof.mark(s) : 0;
+    st = filter_pass(P, B, 0, R, nullptr, maxit, tol, s);
+    if (st) return st;
+    if (g_prof.on) g_prof.phase.push_back({0, {ph0, g_prof.mark(s)}});
+    std::vector<int> itmax(P.nbatch);
+    long long total_iters = 0;
+    CK(cudaMemcpyAsync(itmax.data(), B.iter_max, sizeof(int) * P.nbatch, cudaMemcpyDeviceToHost, s));
+
+    std::vector<double> lam(m0), res(m0);
+    int mk = m0, M = 0, info = 0, k = 0;
+    double trace_prev = 0.0, eo = 1.0;
+    char line[256];
+    snprintf(line, sizeof(line), "#It |  #Eig  |          Trace            |     Error-Trace          |     Max-Residual\n");
+    log_line(fpm[0], line);
+    for (k = 0;; ++k) {
+        // Rayleigh-Ritz on Q
+        if (g_prof.on) ph0 = g_prof.mark(s);
+        CK(launch_spmm_f64(n, m0, A.ia, A.ja, A.v, B.Q, B.T, s));
+        CK(launch_gram_f64(n, m0, B.Q, B.T, B.Aq, B.gpart, P.ksplit, 1, s));
+        if (P.hasB) {
+            CK(launch_spmm_f64(n, m0, Bm.ia, Bm.ja, Bm.v, B.Q, B.T2, s));
+            CK(launch_gram_f64(n, m0, B.Q, B.T2, B.Bq, B.gpart, P.ksplit, 1, s));
+        } else {
+            CK(launch_gram_f64(n, m0, B.Q, B.Q, B.Bq, B.gpart, P.ksplit, 1, s));
+        }
+        for (int b = 0; b < P.nbatch; ++b) total_iters += itmax[b];
+        size_t ph1 = 0, ph2 = 0;
+        if (g_prof.on) ph1 = g_prof.mark(s);
+        const int rst = reduced_gev_dev(m0, B.Aq, B.Bq, B.lam, B.Vr, B.mk, B.eig, s);
+        if (rst == -4) return cuda_fail(cudaGetLastError(), "reduced eigensolver");
+        if (rst) { info = -3; break; }
+        if (g_prof.on) ph2 = g_prof.mark(s);
+        CK(launch_gemm_nn_f64(n, m0, m0, B.Q, B.Vr, B.X, s));
+        CK(launch_residual_f64(n, m0, A.ia, A.ja, A.v, P.hasB ? Bm.ia : nullptr, P.hasB ? Bm.ja : nullptr,
+                               P.hasB ? Bm.v : nullptr, B.X, B.lam, B.Y, B.rpart, nullptr, B.res, alpha, s));
+        if (g_prof.on) {
+            const size_t ph3 = g_prof.mark(s);
+            g_prof.phase.push_back({1, {ph0, ph1}});
+            g_prof.phase.push_back({2, {ph1, ph2}});
+            g_prof.phase.push_back({3, {ph2, ph3}});
+        }
+        CK(cudaMemcpyAsync(lam.data(), B.lam, sizeof(double) * m0, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(res.data(), B.res, sizeof(double) * m0, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&mk, B.mk, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (mk < 1) { info = -3; break; }
+        M = 0;
+        double trace = 0.0, maxres = 0.0;
+        for (int j = 0; j < mk; ++j)
+            if (lam[j] >= emin && lam[j] <= emax) {
+                ++M;
+                trace += lam[j];
+                maxres = std::max(maxres, res[j]);
+            }
+        eo = k == 0 ? 1.0 : std::fabs(trace - trace_prev) / alpha;
+        trace_prev = trace;
+        snprintf(line, sizeof(line), "%3d  %6d      %.16E      %.16E      %.16E\n", k, M, trace, eo,
+                 M ? maxres : 1.0);
+        log_line(fpm[0], line);
+        const bool conv = M >= 1 && (fpm[5] == 1 ? maxres < eps : (k >= 1 && eo < eps));
+        if (conv) { info = 0; break; }
+        if (M == 0 && k >= 1) { info = 1; break; }
+        if (k >= maxloop) { info = 2; break; }
+        if (g_prof.on) ph0 = g_prof.mark(s);
+        st = filter_pass(P, B, 1, B.Y, B.X, maxit, tol, s);
+        if (st) return st;
+        if (g_prof.on) g_prof.phase.push_back({0, {ph0, g_prof.mark(s)}});
+        CK(cudaMemcpyAsync(itmax.data(), B.iter_max, sizeof(int) * P.nbatch, cudaMemcpyDeviceToHost, s));
+    }
+    fpm[59] = (int)std::min<long long>(total_iters, 2147483647LL);
+    if (info == 0 && M >= mk) info = 3;
+    // output order: inside ascending, then outside ascending
+    std::vector<int> perm;
+    if (info != -3) {
+        for (int pass = 0; pass < 2; ++pass)
+            for (int j = 0; j < mk; ++j) {
+                const bool in = lam[j] >= emin && lam[j] <= emax;
+                if ((pass == 0) == in) perm.push_back(j);
+            }
+        for (int c = 0; c < mk; ++c) {
+            e_host[c] = lam[perm[c]];
+            res_host[c] = res[perm[c]];
+        }
+        for (int c = mk; c < m0; ++c) { e_host[c] = 0.0; res_host[c] = 0.0; }
+        perm.resize(m0, 0);
+        CK(cudaMemcpyAsync(B.perm, perm.data(), sizeof(int) * m0, cudaMemcpyHostToDevice, s));
+        k_gather_cols<<<grid_for(blk), 256, 0, s>>>(n, m0, mk, B.X, B.perm, x_dev);
+        count_launches(1);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s));
+        *m0io = mk;
+    }
+    *M_out = M;
+    *loop_out = k;
+    *epsout = eo;
+    if (g_prof.on) {
+        unsigned long long work = 0;
+        CK(cudaMemcpyAsync(&work, B.work, sizeof(work), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        double* o = g_prof.out;
+        for (auto& pr : g_prof.a) o[0] += g_prof.ms(pr.first, pr.second);
+        for (auto& pr : g_prof.b) o[1] += g_prof.ms(pr.first, pr.second);
+        o[2] = (double)g_prof.a.size();
+        o[3] = (double)g_prof.b.size();
+        o[4] = (double)work;
+        for (auto& ph : g_prof.phase) o[5 + ph.first] += g_prof.ms(ph.second.first, ph.second.second);
+        o[9] = (double)P.W;
+        o[10] = (double)P.mt;
+        o[11] = (double)P.n;
+        o[12] = (double)cplx_bytes(P);
+        o[13] = (double)P.G;
+        o[14] = (double)k;
+    }
+    return info;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- device driver
+extern "C" size_t feast_scsr_workspace_bytes(int n, int nnz_a, int nnz_b, int m0, const int* fpm)
+{
+    if (n <= 0 || m0 <= 0 || !fpm) return 0;
+    Plan P = make_plan(n, nnz_a, nnz_b, m0, fpm);
+    Bufs B;
+    return carve(P, nullptr, B);
+}
+
+extern "C" int feast_scsr_solve_dev(int n, int nnz_a, const int* d_ia, const int* d_ja, const double* d_a,
+                                    int nnz_b, const int* d_ib, const int* d_jb, const double* d_b, int* fpm,
+                                    double emin, double emax, int* m0, double* e, double* d_x, int* m,
+                                    double* res, double* epsout, int* loop, int* info, void* d_work,
+                                    size_t work_bytes, void* stream)
+{
+    int inf = 0;
+    auto ret = [&](int v) { if (info) *info = v; return v; };
+    if (!fpm) return ret(-109);
+    if (n <= 0) return ret(202);
+    if (!m0 || *m0 <= 0 || *m0 > n) return ret(201);
+    if (!(emin < emax)) return ret(200);
+    if ((inf = check_fpm(fpm))) return ret(inf);
+    if (!d_ia || !d_ja || !d_a || nnz_a < 0) return ret(-103);
+    if (d_b && (!d_ib || !d_jb || nnz_b <= 0)) return ret(-106);
+    if (!e || !d_x || !m || !res || !epsout || !loop) return ret(-113);
+    Plan P = make_plan(n, nnz_a, d_b ? nnz_b : 0, *m0, fpm);
+    Bufs B;
+    const size_t need = carve(P, nullptr, B);
+    if (!d_work || work_bytes < need) return ret(-120);
+    carve(P, d_work, B);
+    Csr A{n, nnz_a, d_ia, d_ja, d_a}, Bm{n, d_b ? nnz_b : 0, d_ib, d_jb, d_b};
+    g_err.clear();
+    g_prof.reset(fpm[52] == 1);
+    const long long l0 = launch_count();
+    CK(cudaMemsetAsync(B.work, 0, sizeof(unsigned long long), (cudaStream_t)stream));
+    inf = run_feast(P, B, A, Bm, fpm, emin, emax, m0, e, d_x, m, res, epsout, loop, (cudaStream_t)stream);
+    g_prof.out[15] = (double)(launch_count() - l0);
+    return ret(inf);
+}
+
+// ---------------------------------------------------------------- host driver
+namespace {
+
+// Validate a host CSR (base = ia[0] in {0,1}) and expand it to 0-based full
+// storage.  Returns 0 or the argument's error code.
+int host_csr(char uplo, int n, const double* v, const int* ia, const int* ja, int arg0, std::vector<int>& oia,
+             std::vector<int>& oja, std::vector<double>& ov)
+{
+    if (!v) return -(100 + arg0);
+    if (!ia) return -(100 + arg0 + 1);
+    if (!ja) return -(100 + arg0 + 2);
+    const int base = ia[0];
+    if (base != 0 && base != 1) return -(100 + arg0 + 1);
+    for (int i = 0; i < n; ++i)
+        if (ia[i + 1] < ia[i]) return -(100 + arg0 + 1);
+    const long long nnz = (long long)ia[n] - base;
+    std::vector<std::vector<std::pair<int, double>>> rows(n);
+    for (int i = 0; i < n; ++i)
+        for (int p = ia[i] - base; p < ia[i + 1] - base; ++p) {
+            const int j = ja[p] - base;
+            if (j < 0 || j >= n) return -(100 + arg0 + 2);
+            if (!std::isfinite(v[p])) return -(100 + arg0);
+            if (uplo == 'L' && j > i) return -(100 + arg0 + 2);
+            if (uplo == 'U' && j < i) return -(100 + arg0 + 2);
+            rows[i].push_back({j, v[p]});
+            if (uplo != 'F' && j != i) rows[j].push_back({i, v[p]});
+        }
+    (void)nnz;
+    oia.assign(n + 1, 0);
+    oja.clear();
+    ov.clear();
+    for (int i = 0; i < n; ++i) {
+        std::sort(rows[i].begin(), rows[i].end(),
+                  [](const std::pair<int, double>& a, const std::pair<int, double>& b) { return a.first < b.first; });
+        for (auto& pr : rows[i]) {
+            oja.push_back(pr.first);
+            ov.push_back(pr.second);
+        }
+        oia[i + 1] = (int)oja.size();
+    }
+    return 0;
+}
+
+struct DevMem {
+    std::vector<void*> ptrs;
+    ~DevMem()
+    {
+        for (void* p : ptrs) cudaFree(p);
+    }
+    template <typename T>
+    cudaError_t alloc(T** p, size_t count)
+    {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 256);
+        if (e == cudaSuccess) {
+            ptrs.push_back(q);
+            *p = (T*)q;
+        }
+        return e;
+    }
+};
+
+}  // namespace
+
+extern "C" int feast_scsr_solve(char uplo, int n, const double* a, const int* ia, const int* ja, const double* b,
+                                const int* ib, const int* jb, int* fpm, double emin, double emax, int* m0,
+                                double* e, double* x, int* m, double* res, double* epsout, int* loop, int* info)
+{
+    auto ret = [&](int v) { if (info) *info = v; return v; };
+    if (uplo != 'F' && uplo != 'L' && uplo != 'U') return ret(-101);
+    if (n <= 0) return ret(202);
+    if (!fpm) return ret(-109);
+    int inf = check_fpm(fpm);
+    if (inf) return ret(inf);
+    if (!(emin < emax)) return ret(200);
+    if (!m0 || *m0 <= 0 || *m0 > n) return ret(201);
+    if (!e) return ret(-113);
+    if (!x) return ret(-114);
+    if (!m) return ret(-115);
+    if (!res) return ret(-116);
+    if (!epsout) return ret(-117);
+    if (!loop) return ret(-118);
+    std::vector<int> aia, aja, bia, bja;
+    std::vector<double> av, bv;
+    inf = host_csr(uplo, n, a, ia, ja, 3, aia, aja, av);
+    if (inf) return ret(inf);
+    const bool hasB = b || ib || jb;
+    if (hasB) {
+        inf = host_csr(uplo, n, b, ib, jb, 6, bia, bja, bv);
+        if (inf) return ret(inf);
+    }
+    g_err.clear();
+    const int mm0 = *m0;
+    DevMem dm;
+    int *d_ia = nullptr, *d_ja = nullptr, *d_ib = nullptr, *d_jb = nullptr;
+    double *d_a = nullptr, *d_b = nullptr, *d_x = nullptr;
+    void* d_work = nullptr;
+    cudaStream_t s = nullptr;
+    const size_t wb = feast_scsr_workspace_bytes(n, (int)aja.size(), hasB ? (int)bja.size() : 0, mm0, fpm);
+#define HK(x)                                                        \
+    do {                                                             \
+        cudaError_t _e = (x);                                        \
+        if (_e != cudaSuccess) return ret(cuda_fail(_e, #x));        \
+    } while (0)
+    HK(dm.alloc(&d_ia, aia.size()));
+    HK(dm.alloc(&d_ja, std::max<size_t>(1, aja.size())));
+    HK(dm.alloc(&d_a, std::max<size_t>(1, av.size())));
+    HK(dm.alloc(&d_x, (size_t)n * mm0));
+    HK(dm.alloc((char**)&d_work, wb));
+    HK(cudaMemcpy(d_ia, aia.data(), sizeof(int) * aia.size(), cudaMemcpyHostToDevice));
+    HK(cudaMemcpy(d_ja, aja.data(), sizeof(int) * aja.size(), cudaMemcpyHostToDevice));
+    HK(cudaMemcpy(d_a, av.data(), sizeof(double) * av.size(), cudaMemcpyHostToDevice));
+    if (hasB) {
+        HK(dm.alloc(&d_ib, bia.size()));
+        HK(dm.alloc(&d_jb, std::max<size_t>(1, bja.size())));
+        HK(dm.alloc(&d_b, std::max<size_t>(1, bv.size())));
+        HK(cudaMemcpy(d_ib, bia.data(), sizeof(int) * bia.size(), cudaMemcpyHostToDevice));
+        HK(cudaMemcpy(d_jb, bja.data(), sizeof(int) * bja.size(), cudaMemcpyHostToDevice));
+        HK(cudaMemcpy(d_b, bv.data(), sizeof(double) * bv.size(), cudaMemcpyHostToDevice));
+    }
+    if (fpm[4] == 1) HK(cudaMemcpy(d_x, x, sizeof(double) * (size_t)n * mm0, cudaMemcpyHostToDevice));
+    inf = feast_scsr_solve_dev(n, (int)aja.size(), d_ia, d_ja, d_a, hasB ? (int)bja.size() : 0, d_ib, d_jb, d_b,
+                               fpm, emin, emax, m0, e, d_x, m, res, epsout, loop, info, d_work, wb, s);
+    if (inf >= 0 || inf == -3 || inf == -2)
+        HK(cudaMemcpy(x, d_x, sizeof(double) * (size_t)n * mm0, cudaMemcpyDeviceToHost));
+#undef HK
+    return ret(inf);
+}
+
+// ---------------------------------------------------------------- kernel-level entry points
+namespace {
+struct AsyncMem {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit AsyncMem(cudaStream_t st) : s(st) {}
+    ~AsyncMem()
+    {
+        for (void* p : ptrs) cudaFreeAsync(p, s);
+    }
+    cudaError_t alloc(void** p, size_t bytes)
+    {
+        cudaError_t e = cudaMallocAsync(p, bytes + 256, s);
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+};
+}  // namespace
+
+extern "C" int feast_shifted_spmm_dev(int n, const int* ia, const int* ja, const void* a, const int* ib,
+                                      const int* jb, const void* b, int nb, const double* z, int m, int fp64,
+                                      const void* P, void* V, void* stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n <= 0) return -101;
+    if (nb < 1 || nb > 32) return -108;
+    if (m <= 0) return -110;
+    int W, nbp, mt;
+    feast_filter_layout(nb, fp64, &W, &nbp, &mt);
+    const int G = (m + mt - 1) / mt;
+    const int RB = 256;
+    const int nrb = (n + RB - 1) / RB;
+    std::vector<ColState> cs((size_t)G * W);
+    memset(cs.data(), 0, sizeof(ColState) * cs.size());
+    for (int c = 0; c < G * W; ++c) {
+        const int e = (c % W) % nbp;
+        if (e < nb) cs[c].z = make_double2(z[2 * e], z[2 * e + 1]);
+    }
+    FiltProb fp;
+    memset(&fp, 0, sizeof(fp));
+    fp.n = n;
+    fp.m0 = m;
+    fp.G = G;
+    fp.nrb = nrb;
+    fp.ia = ia;
+    fp.ja = ja;
+    fp.av = a;
+    fp.ib = ib;
+    fp.jb = jb;
+    fp.bv = b;
+    AsyncMem am(s);
+    void *d_cs = nullptr, *d_fp = nullptr;
+    CK(am.alloc(&d_cs, sizeof(ColState) * cs.size()));
+    CK(am.alloc(&d_fp, sizeof(FiltProb)));
+    CK(cudaMemcpyAsync(d_cs, cs.data(), sizeof(ColState) * cs.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_fp, &fp, sizeof(fp), cudaMemcpyHostToDevice, s));
+    FilterArgs fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.probs = (const FiltProb*)d_fp;
+    fa.nprob = 1;
+    fa.nitems = (long long)G * nrb;
+    fa.W = W;
+    fa.nbp = nbp;
+    fa.mt = mt;
+    fa.RB = RB;
+    fa.p0 = const_cast<void*>(P);
+    fa.p1 = V;
+    fa.cs = (ColState*)d_cs;
+    const int grid = (int)std::min<long long>(filter_grid(fp64 != 0, W), fa.nitems);
+    CK(launch_shifted_spmm(fa, fp64 != 0, grid, s));
+    CK(cudaStreamSynchronize(s));
+    return 0;
+}
+
+extern "C" int feast_filter_dev(int n, int nnz_a, const int* ia, const int* ja, const double* a, int nnz_b,
+                                const int* ib, const int* jb, const double* b, int m, const double* R,
+                                const double* X, const double* lam, int rii, const int* fpm, double emin,
+                                double emax, double* Q, int* iters, void* stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n <= 0) return -101;
+    if (m <= 0 || m > n) return -110;
+    if (!fpm) return -115;
+    int inf = check_fpm(fpm);
+    if (inf) return inf;
+    if (!(emin < emax)) return 200;
+    Plan P = make_plan(n, nnz_a, b ? nnz_b : 0, m, fpm, true);
+    Bufs B;
+    const size_t bytes = carve(P, nullptr, B, true);
+    AsyncMem am(s);
+    void* base = nullptr;
+    CK(am.alloc(&base, bytes));
+    carve(P, base, B, true);
+    Csr A{n, nnz_a, ia, ja, a}, Bm{n, b ? nnz_b : 0, ib, jb, b};
+    std::vector<double> zw;
+    contour(P.ne, emin, emax, fpm[17] / 100.0, zw);
+    int st = setup_filter(P, B, A, Bm, zw, lam, nullptr, s);
+    if (st) return st;
+    B.Q = Q;
+    st = filter_pass(P, B, rii, R, X, fpm[45], std::pow(10.0, -fpm[44]), s);
+    if (st) return st;
+    std::vector<int> itm(P.nbatch);
+    CK(cudaMemcpyAsync(itm.data(), B.iter_max, sizeof(int) * P.nbatch, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (iters) {
+        int t = 0;
+        for (int v : itm) t += v;
+        *iters = t;
+    }
+    return 0;
+}
+
+extern "C" int feast_gram_dev(int n, int m, const double* X, const double* Y, double* C, void* stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n <= 0) return -101;
+    if (m <= 0) return -102;
+    int ks = 1;
+    const size_t gp = gram_partial_doubles(n, m, &ks, num_sms());
+    AsyncMem am(s);
+    void* part = nullptr;
+    CK(am.alloc(&part, gp * sizeof(double)));
+    CK(launch_gram_f64(n, m, X, Y, C, (double*)part, ks, 1, s));
+    CK(cudaStreamSynchronize(s));
+    return 0;
+}
+
+extern "C" int feast_gemm_dev(int n, int m, int k, const double* A, const double* V, double* C, void* stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n <= 0) return -101;
+    if (m <= 0) return -102;
+    if (k <= 0) return -103;
+    CK(launch_gemm_nn_f64(n, m, k, A, V, C, s));
+    CK(cudaStreamSynchronize(s));
+    return 0;
+}
+
+extern "C" int feast_sym_eig_dev(int m, double* A, double* lam, double* V, int* sweeps, void* stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m <= 0) return -101;
+    AsyncMem am(s);
+    void* w = nullptr;
+    CK(am.alloc(&w, jacobi_work_bytes(m)));
+    int sw = 0;
+    const int st = jacobi_eig_dev(m, A, lam, V, w, s, &sw);
+    if (sweeps) *sweeps = sw;
+    if (st == -3) return cuda_fail(cudaGetLastError(), "jacobi");
+    return st ? -3 : 0;
+}
+
+extern "C" int feast_reduced_eig_dev(int m, const double* Aq, const double* Bq, double* lam, double* V, int* mk,
+                                     void* stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m <= 0) return -101;
+    AsyncMem am(s);
+    void* w = nullptr;
+    void* dmk = nullptr;
+    CK(am.alloc(&w, reduced_work_bytes(m)));
+    CK(am.alloc(&dmk, sizeof(int)));
+    const int st = reduced_gev_dev(m, Aq, Bq, lam, V, (int*)dmk, w, s);
+    if (st == -4) return cuda_fail(cudaGetLastError(), "reduced eigensolver");
+    if (st) return -3;
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, dmk, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (mk) *mk = h;
+    return 0;
+}
+
+extern "C" int feast_residual_dev(int n, const int* ia, const int* ja, const double* a, const int* ib,
+                                  const int* jb, const double* b, int m, const double* X, const double* lam,
+                                  double alpha, double* R, double* res, void* stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n <= 0) return -101;
+    if (m <= 0) return -108;
+    AsyncMem am(s);
+    void* part = nullptr;
+    CK(am.alloc(&part, residual_partial_doubles(n, m) * sizeof(double)));
+    CK(launch_residual_f64(n, m, ia, ja, a, ib, jb, b, X, lam, R, (double*)part, nullptr, res, alpha, s));
+    CK(cudaStreamSynchronize(s));
+    return 0;
+}
+
+extern "C" int feast_eig_grad_dev(int n, const int* ia, const int* ja, int m, const double* X, const double* w,
+                                  double* grad, void* stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n <= 0) return -101;
+    if (m <= 0 || m > 2048) return -104;
+    CK(launch_eig_grad(n, ia, ja, m, X, w, grad, s));
+    CK(cudaStreamSynchronize(s));
+    return 0;
+}
+
+extern "C" int feast_last_profile(double* out)
+{
+    for (int i = 0; i < 16; ++i) out[i] = g_prof.out[i];
+    return 0;
+}

@@ -1,0 +1,141 @@
+// Internal declarations shared by the CUDA translation units of libfeast_gb300.
+// Nothing here is part of the public C ABI (include/feast_gb300.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+namespace feast {
+
+// ---------------------------------------------------------------- complex helpers
+template <typename T> struct C2;
+template <> struct C2<float> { using type = float2; };
+template <> struct C2<double> { using type = double2; };
+template <typename T> using c2_t = typename C2<T>::type;
+
+template <typename V> __device__ __forceinline__ V cmk(decltype(V::x) r, decltype(V::x) i) { V v; v.x = r; v.y = i; return v; }
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) { return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+// a + b*c
+template <typename V> __device__ __forceinline__ V cfma(V b, V c, V a) {
+    return cmk<V>(fma(b.x, c.x, fma(-b.y, c.y, a.x)), fma(b.x, c.y, fma(b.y, c.x, a.y)));
+}
+
+// ---------------------------------------------------------------- filter problem table
+// One entry per independent eigenproblem handled by a filter launch.  All
+// pointers are device pointers; row pointers are 0-based and local to the problem.
+struct FiltProb {
+    int n;              // rows
+    int m0;             // subspace columns of this problem
+    int G;              // column groups = ceil(m0 / Mt)
+    int nrb;            // row blocks per group = ceil(n / RB)
+    long long item0;    // first work item (items of one problem are contiguous: g-major, rb fastest)
+    long long vec_off;  // offset of this problem's block vectors, in complex elements (G*n*W)
+    int col_off;        // offset of this problem's columns in the per-column arrays (G*W)
+    int grp_off;        // offset of this problem's groups in the per-group arrays (G)
+    long long q_off;    // offset of this problem's FP64 n x m0 blocks (row-major)
+    const int* ia;      // A row pointers [n+1]
+    const int* ja;      // A column indices
+    const void* av;     // A values (float or double, the filter's real type)
+    const int* ib;      // B row pointers, or nullptr for B = I
+    const int* jb;
+    const void* bv;
+    const double* zw;   // Ne nodes and weights, [Ne][4] = (Re z, Im z, Re w, Im w)
+    const double* lam;  // Ritz values of the previous Rayleigh-Ritz step [m0]
+    const int* mk;      // live subspace columns (device), or nullptr for m0
+    int ne;             // number of contour nodes
+};
+
+// Per-column COCG state (FP64 for stability of the scalar recurrences).
+struct ColState {
+    double2 rho;    // r^T r (unconjugated)
+    double2 alpha;  // step length of the current iteration
+    double2 beta;   // p update coefficient of the current iteration
+    double2 z;      // shift z_e of the column's node
+    double2 c;      // filter coefficient applied to the column's solution
+    double2 ca;     // c * alpha
+    double bn2;     // ||b||^2
+    double rn2;     // ||r||^2 of the last iteration
+    int active;     // 1 while the column iterates
+    double rq;      // rho(lambda_m): filter value of the column's Ritz value
+    int iters;      // iterations taken
+    int status;     // 0 ok, 1 converged, 2 breakdown
+};
+
+struct FilterArgs {
+    const FiltProb* probs;
+    int nprob;
+    long long nitems;
+    int W;          // lanes (complex columns) per row of a group tile
+    int nbp;        // node lanes per subspace column (power of two)
+    int mt;         // subspace columns per group = W / nbp
+    int RB;         // rows per work item
+    void* r;        // residual block vectors (complex T)
+    void* p0;       // search directions, ping
+    void* p1;       // search directions, pong
+    ColState* cs;   // per-column state
+    double* part;   // per-item partial sums [nitems][W][4]
+    unsigned* grp_count;  // per-group finished-item counters
+    int* grp_done;  // per-group "no active column" flags
+    double* Q;      // FP64 filter accumulator (row-major n x m0 per problem)
+    double tol2;    // squared relative COCG tolerance
+    int* iter_max;  // per-problem max iteration reached
+    int* groups_left;  // per-problem number of groups still iterating
+    unsigned long long* work;  // group-iterations done (one per group per COCG step)
+};
+
+// ---------------------------------------------------------------- launchers (k_filter.cu)
+cudaError_t launch_cocg_step_a(const FilterArgs& a, bool fp64, int k, int grid, cudaStream_t s);
+cudaError_t launch_cocg_step_b(const FilterArgs& a, bool fp64, int k, int grid, cudaStream_t s);
+cudaError_t launch_filter_init(const FilterArgs& a, bool fp64, const double* R, const double* X, int rii,
+                               int init_q, int grid, cudaStream_t s);
+cudaError_t launch_colstate_init(const FilterArgs& a, int node0, int rii, cudaStream_t s);
+cudaError_t launch_shifted_spmm(const FilterArgs& a, bool fp64, int grid, cudaStream_t s);
+cudaError_t launch_cast_values(const double* src, float* dst, long long n, cudaStream_t s);
+// persistent grid size of the COCG kernels: SMs x resident CTAs per SM
+int filter_grid(bool fp64, int W);
+
+// ---------------------------------------------------------------- Rayleigh-Ritz (k_rr.cu)
+// Y = A X (and optionally Z = B X) for row-major n x m FP64 blocks.
+cudaError_t launch_spmm_f64(int n, int m, const int* ia, const int* ja, const double* av,
+                            const double* X, double* Y, cudaStream_t s);
+// C (m x m) = X^T Y with X, Y row-major n x m; split-K partial buffer part
+// [ksplit][m][m]; result symmetrised (C + C^T)/2 when sym != 0.
+cudaError_t launch_gram_f64(int n, int m, const double* X, const double* Y, double* C,
+                            double* part, int ksplit, int sym, cudaStream_t s);
+size_t gram_partial_doubles(int n, int m, int* ksplit_out, int nsm);
+// C (n x k) = A (n x m, row-major) * V (m x k, row-major)
+cudaError_t launch_gemm_nn_f64(int n, int m, int k, const double* A, const double* V, double* C,
+                               cudaStream_t s);
+// R = AX - BX diag(lam) with per-column partial norms; res_j = ||R_j|| / (alpha ||BX_j||)
+cudaError_t launch_residual_f64(int n, int m, const int* ia, const int* ja, const double* av,
+                                const int* ib, const int* jb, const double* bv, const double* X,
+                                const double* lam, double* R, double* part, unsigned* counter,
+                                double* res, double alpha, cudaStream_t s);
+size_t residual_partial_doubles(int n, int m);
+
+// ---------------------------------------------------------------- reduced eigensolver (k_eig.cu)
+// Symmetric eigen-decomposition of the m x m row-major matrix A (destroyed):
+// eigenvalues ascending in lam, eigenvectors in the columns of V (row-major).
+// Returns the number of sweeps (>= 0), or -1 when the sweep limit was hit,
+// or -2 when a grid barrier timed out.  work: device scratch of
+// jacobi_work_bytes(m).
+size_t jacobi_work_bytes(int m);
+int jacobi_eig_dev(int m, double* A, double* lam, double* V, void* work, cudaStream_t s,
+                   int* sweeps_host);
+// Reduced generalized problem; see k_eig.cu.  work: reduced_work_bytes(m).
+size_t reduced_work_bytes(int m);
+int reduced_gev_dev(int m, const double* Aq, const double* Bq, double* lam, double* V, int* mk,
+                    void* work, cudaStream_t s);
+
+// ---------------------------------------------------------------- gradient (k_grad.cu)
+cudaError_t launch_eig_grad(int n, const int* ia, const int* ja, int m, const double* Xr,
+                            const double* gw, double* grad, cudaStream_t s);
+
+int num_sms();
+// kernel launches issued by this library (all threads), for launch accounting
+long long launch_count();
+void count_launches(int k);
+
+}  // namespace feast

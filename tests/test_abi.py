@@ -1,0 +1,140 @@
+"""CPU checks of the C ABI: the library builds/loads, exports every symbol the
+header declares, and its host-side logic (defaults, contour nodes, tile
+layout, argument validation) agrees with the oracle and the guide.  None of
+these calls reaches the GPU."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import feast_workloads as fw
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "feast_gb300.h")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2002_04807_gb300 import build
+
+    build.build()
+    import paper_2002_04807_gb300 as p
+
+    p.library()
+    return p
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(feast_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_symbols_exported(pkg):
+    out = subprocess.run(["nm", "-D", "--defined-only", pkg.library_path()], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r" T (feast_[a-z0-9_]+)", out))
+    declared = _declared()
+    assert declared, "no declarations found"
+    missing = [s for s in declared if s not in exported]
+    assert not missing, missing
+    from paper_2002_04807_gb300 import _lib
+
+    assert sorted(_lib.exported_symbols()) == declared
+
+
+def test_library_built_for_sm103a(pkg):
+    from paper_2002_04807_gb300 import build
+
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_fpm_defaults_match_guide_table(pkg):
+    f = pkg.feast_init()
+    ref = O.feastinit()
+    assert np.array_equal(f, ref)
+    assert f[1] == 8 and f[2] == 12 and f[3] == 20 and f[17] == 30 and f[41] == 1 and f[45] == 40
+
+
+@pytest.mark.parametrize("ne,ratio", [(1, 100), (8, 30), (8, 100), (16, 100), (56, 30)])
+def test_contour_nodes_match_oracle(pkg, ne, ratio):
+    z, w = pkg.feast_contour_nodes(ne, -1.5, 2.5, ratio)
+    zo, wo = O.contour_gauss(ne, -1.5, 2.5, ratio / 100.0)
+    assert np.abs(z - zo).max() < 1e-14 and np.abs(w - wo).max() < 1e-14
+
+
+def test_contour_node_errors(pkg):
+    from paper_2002_04807_gb300 import FeastError
+
+    with pytest.raises(FeastError):
+        pkg.feast_contour_nodes(21, 0.0, 1.0, 30)
+    with pytest.raises(FeastError):
+        pkg.feast_contour_nodes(8, 1.0, 0.0, 30)
+
+
+@pytest.mark.parametrize("nb,fp64,expect", [(8, 0, (32, 8, 4)), (16, 0, (32, 16, 2)), (8, 1, (16, 8, 2)),
+                                            (16, 1, (16, 16, 1)), (5, 0, (32, 8, 4)), (20, 1, (32, 32, 1)),
+                                            (1, 0, (32, 1, 32))])
+def test_filter_layout(pkg, nb, fp64, expect):
+    assert pkg.feast_filter_layout(nb, fp64) == expect
+
+
+def test_argument_errors_are_host_side(pkg):
+    A = fw.laplacian_1d(20)
+    ok = dict(uplo="F", n=20, a=A.data, ia=A.indptr, ja=A.indices, emin=0.0, emax=0.5, m0=6)
+
+    def run(**kw):
+        args = dict(ok)
+        args.update(kw)
+        return pkg.feast_scsr_solve(**args).info
+
+    assert run(uplo="X") == -101
+    assert run(n=0) == 202
+    assert run(emin=1.0, emax=0.5) == 200
+    assert run(m0=0) == 201 and run(m0=21) == 201
+    f = pkg.feast_init()
+    f[1] = 21
+    assert run(fpm=f) == 102
+    f = pkg.feast_init()
+    f[15] = 1
+    assert run(fpm=f) == 116
+    bad = A.indices.copy()
+    bad[3] = 99
+    assert run(ja=bad) == -105
+    nan = A.data.copy()
+    nan[0] = np.nan
+    assert run(a=nan) == -103
+    bad_ia = A.indptr.copy()
+    bad_ia[5] = bad_ia[4] - 1
+    assert run(ia=bad_ia) == -104
+    # lower storage with an upper entry
+    assert run(uplo="L") == -105
+
+
+def test_no_cpu_fallback_without_gpu(pkg):
+    """With valid arguments the host driver goes to the GPU; without one it
+    must fail with the CUDA error code, never compute on the CPU."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    A = fw.laplacian_1d(20)
+    r = None
+    from paper_2002_04807_gb300 import FeastError
+
+    with pytest.raises(FeastError):
+        r = pkg.feast_scsr_solve("F", 20, A.data, A.indptr, A.indices, emin=0.0, emax=0.5, m0=6)
+    assert r is None
+
+
+def test_workspace_size_grows_with_problem(pkg):
+    f = pkg.feast_init()
+    small = pkg.feast_scsr_workspace_bytes(1000, 3000, 0, 48, f)
+    big = pkg.feast_scsr_workspace_bytes(262144, 1810432, 0, 150, f)
+    assert 0 < small < big
+    f64 = f.copy()
+    f64[41] = 0
+    assert pkg.feast_scsr_workspace_bytes(262144, 1810432, 0, 150, f64) > big

@@ -1,0 +1,253 @@
+"""End-to-end GPU FEAST through the C ABI against the FP64 CPU oracle.
+
+Bars (from the method's accuracy targets): eigenvalue relative error
+<= 1e-10, relative residual <= 1e-10, subspace angles <= 1e-8."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import feast_workloads as fw
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+EIG_TOL, RES_TOL, ANG_TOL = 1e-10, 1e-10, 1e-8
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2002_04807_gb300 import build
+
+    build.build()
+    import paper_2002_04807_gb300 as p
+
+    p.library()
+    assert torch.cuda.is_available()
+    return p
+
+
+def sin_angle(U, V):
+    qu, _ = np.linalg.qr(U)
+    qv, _ = np.linalg.qr(V)
+    return float(np.linalg.norm(qu - qv @ (qv.T @ qu), 2))
+
+
+def cluster_angles(E, X, Eo, Xo, scale):
+    """Max subspace angle over clusters of eigenvalues closer than 1e-8 * scale."""
+    worst = 0.0
+    i = 0
+    while i < len(Eo):
+        j = i + 1
+        while j < len(Eo) and Eo[j] - Eo[j - 1] < 1e-8 * scale:
+            j += 1
+        worst = max(worst, sin_angle(X[:, i:j], Xo[:, i:j]))
+        i = j
+    return worst
+
+
+def run_gpu(pkg, p, mixed, y0=None, tol_exp=10, inner=(2, 200), maxloop=30, B=None, uplo="F", csr=None,
+            nb=0):
+    fpm = pkg.feast_init()
+    fpm[1], fpm[2], fpm[3], fpm[17], fpm[41] = p.ne, tol_exp, maxloop, p.ratio, mixed
+    fpm[44], fpm[45] = inner
+    fpm[49] = nb
+    if y0 is None:
+        y0 = p.y0()
+    fpm[4] = 1
+    A = p.A if csr is None else csr
+    Bm = p.B if B is None else B
+    kw = {}
+    if Bm is not None:
+        kw = dict(b=Bm.data, ib=Bm.indptr, jb=Bm.indices)
+    return pkg.feast_scsr_solve(uplo, p.n, A.data, A.indptr, A.indices, fpm=fpm, emin=p.emin, emax=p.emax,
+                                m0=p.m0, x0=y0, **kw)
+
+
+def check_against(r, ref, scale, B=None):
+    assert r.info == 0, r.info
+    assert r.M == ref["M"], (r.M, ref["M"])
+    M = r.M
+    rel = np.abs(r.E[:M] - ref["E"][:M]) / np.maximum(np.abs(ref["E"][:M]), 1e-300)
+    assert rel.max() <= EIG_TOL, rel.max()
+    assert r.res[:M].max() <= RES_TOL
+    ang = cluster_angles(r.E[:M], r.X[:, :M], ref["E"][:M], ref["X"][:, :M], scale)
+    assert ang <= ANG_TOL, ang
+    X = r.X[:, :M]
+    BX = X if B is None else O.csr_mm(B, X)
+    assert np.abs(X.T @ BX - np.eye(M)).max() < 1e-11
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_helloworld_worked_example(pkg, mixed):
+    g = json.load(open(os.path.join(GOLD, "helloworld.json")))
+    c, run = g["csr_1based"], g["run"]
+    a = np.array(c["sA"], dtype=float)
+    ia = np.array(c["IA"], dtype=np.int32)
+    ja = np.array(c["JA"], dtype=np.int32)
+    fpm = pkg.feast_init()
+    fpm[41] = mixed
+    fpm[44], fpm[45] = 2, 100
+    fpm[4] = 1
+    y0 = fw.gaussian_block(4, run["M0"], 0)
+    r = pkg.feast_scsr_solve("F", 4, a, ia, ja, fpm=fpm, emin=run["Emin"], emax=run["Emax"], m0=run["M0"], x0=y0)
+    assert r.info == 0 and r.M == g["expected"]["M"]
+    assert np.allclose(r.E[:2], g["expected"]["E"], atol=1e-12)
+    assert r.res[:2].max() < g["expected"]["max_residual_below"]
+
+
+@pytest.mark.parametrize("uplo", ["L", "U"])
+def test_half_storage(pkg, uplo):
+    d = fw.helloworld_dense()
+    tri = np.tril(d) if uplo == "L" else np.triu(d)
+    A = fw.csr_from_dense(tri)
+    fpm = pkg.feast_init()
+    fpm[4] = 1
+    fpm[44], fpm[45] = 2, 100
+    y0 = fw.gaussian_block(4, 3, 0)
+    r = pkg.feast_scsr_solve(uplo, 4, A.data, A.indptr, A.indices, fpm=fpm, emin=3.0, emax=5.0, m0=3, x0=y0)
+    assert r.info == 0 and r.M == 2 and np.allclose(r.E[:2], [4.0, 4.0], atol=1e-12)
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_laplacian_1d_closed_form(pkg, mixed):
+    p = fw.tridiag_1d()
+    ref = O.feast_scsr(p.A, None, p.emin, p.emax, p.m0, Y0=p.y0(), ne=p.ne, ratio=p.ratio, tol_exp=10)
+    r = run_gpu(pkg, p, mixed, inner=(2, 400), maxloop=60)
+    check_against(r, ref, 0.01)
+    k = np.arange(1, 32)
+    lam = 2 - 2 * np.cos(k * np.pi / 1001)
+    assert np.abs(r.E[:31] - lam).max() <= EIG_TOL * lam.max()
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_laplace3d_potential_vs_oracle(pkg, mixed):
+    p = fw.laplace3d_potential(side=16, count=30, m0=48, seed=7)
+    ref = O.feast_scsr(p.A, None, p.emin, p.emax, p.m0, Y0=p.y0(), ne=8, ratio=100, tol_exp=10)
+    assert ref["info"] == 0
+    r = run_gpu(pkg, p, mixed)
+    check_against(r, ref, p.emax)
+
+
+def test_constant_potential_degenerate_clusters(pkg):
+    side, v0 = 12, 0.3
+    mu = 2 - 2 * np.cos(np.arange(1, side + 1) * np.pi / (side + 1))
+    eig = (mu[:, None, None] + mu[None, :, None] + mu[None, None, :]).ravel() + v0
+    lev = np.sort(eig)
+    distinct = np.unique(np.round(lev, 12))
+    emax = 0.5 * (distinct[4] + distinct[5])
+    sel = eig <= emax
+    p = fw.laplace3d_constant(side, v0, emax, m0=int(1.6 * sel.sum()) + 4)
+    r = run_gpu(pkg, p, 1)
+    assert r.info == 0 and r.M == sel.sum()
+    assert np.abs(r.E[: r.M] - np.sort(eig[sel])).max() < EIG_TOL * emax
+    s = np.sin(np.arange(1, side + 1)[:, None] * np.arange(1, side + 1)[None, :] * np.pi / (side + 1))
+    s *= np.sqrt(2 / (side + 1))
+    full = np.einsum("ia,jb,kc->ijkabc", s, s, s).reshape(side ** 3, -1)
+    assert sin_angle(r.X[:, : r.M], full[:, sel]) < ANG_TOL
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_generalized_27pt(pkg, mixed):
+    rng = np.random.default_rng(7)
+    A = fw.stencil27_spd(9, rng)
+    B = fw.diagonal_csr(rng.uniform(1.0, 2.0, A.n))
+    ev = np.linalg.eigvalsh(np.diag(1 / np.sqrt(B.data)) @ A.to_dense() @ np.diag(1 / np.sqrt(B.data)))
+    emax = 0.5 * (ev[24] + ev[25])
+    p = fw.Problem("s27", A, B, 0.0, emax, 40, 16, 100, 2)
+    ref = O.feast_scsr(A, B, 0.0, emax, 40, Y0=p.y0(), ne=16, ratio=100, tol_exp=10)
+    assert ref["M"] == 25 == O.count_below(A, B, emax)
+    r = run_gpu(pkg, p, mixed)
+    check_against(r, ref, emax, B=B)
+
+
+def test_node_batches_agree(pkg):
+    """Solving the 16 nodes in batches of 4 gives the same eigenpairs."""
+    p = fw.laplace3d_potential(side=12, count=16, m0=28, ne=16, seed=9)
+    a = run_gpu(pkg, p, 1, nb=4)
+    b = run_gpu(pkg, p, 1, nb=16)
+    assert a.info == b.info == 0 and a.M == b.M
+    assert np.abs(a.E[: a.M] - b.E[: b.M]).max() < 1e-10 * p.emax
+
+
+def test_no_eigenvalue_and_small_subspace(pkg):
+    p = fw.tridiag_1d(n=300, emin=5.0, emax=6.0, m0=8, ratio=100)
+    r = run_gpu(pkg, p, 1)
+    assert r.info == 1 and r.M == 0
+    # interval holding more eigenvalues than M0: warning 3 (or no convergence)
+    p2 = fw.tridiag_1d(n=300, emin=0.0, emax=0.2, m0=8, ratio=100)
+    r2 = run_gpu(pkg, p2, 1, maxloop=5)
+    assert r2.info in (2, 3)
+
+
+def test_tiny_full_subspace(pkg):
+    A = fw.laplacian_1d(6)
+    lam = 2 - 2 * np.cos(np.arange(1, 7) * np.pi / 7)
+    fpm = pkg.feast_init()
+    fpm[4] = 1
+    fpm[17] = 100
+    fpm[44], fpm[45] = 2, 100
+    r = pkg.feast_scsr_solve("F", 6, A.data, A.indptr, A.indices, fpm=fpm, emin=0.0, emax=1.0, m0=6,
+                             x0=fw.gaussian_block(6, 6, 1))
+    inside = lam[lam <= 1.0]
+    assert r.M == len(inside) and np.abs(r.E[: r.M] - inside).max() < 1e-12
+
+
+def test_restart_from_solution(pkg):
+    p = fw.laplace3d_potential(side=12, count=16, m0=28, seed=9)
+    r = run_gpu(pkg, p, 1)
+    assert r.info == 0
+    X0 = np.zeros((p.n, p.m0), order="F")
+    X0[:, : r.m0] = r.X
+    r2 = run_gpu(pkg, p, 1, y0=X0)
+    assert r2.info == 0 and r2.loop <= 1 and r2.M == r.M
+
+
+def test_device_driver_with_torch_stream(pkg):
+    p = fw.laplace3d_potential(side=12, count=16, m0=28, seed=9)
+    host = run_gpu(pkg, p, 1)
+    fpm = host.fpm.copy()
+    s = torch.cuda.Stream()
+    ia = torch.as_tensor(p.A.indptr).cuda()
+    ja = torch.as_tensor(p.A.indices).cuda()
+    av = torch.as_tensor(p.A.data).cuda()
+    x = torch.as_tensor(np.ascontiguousarray(p.y0().T)).cuda()  # (m0, n) row-major == column-major n x m0
+    with torch.cuda.stream(s):
+        r = pkg.feast_scsr_solve_dev(p.n, ia, ja, av, fpm=fpm, emin=p.emin, emax=p.emax, m0=p.m0, x=x, stream=s)
+    assert r.info == 0 and r.M == host.M
+    assert np.array_equal(r.E, host.E)  # deterministic: same kernels, same order
+    Xd = x.cpu().numpy().T[:, : r.m0]
+    assert np.array_equal(Xd, host.X)
+
+
+def test_random_start_block(pkg):
+    p = fw.laplace3d_potential(side=12, count=16, m0=28, seed=9)
+    fpm = pkg.feast_init()
+    fpm[17], fpm[44], fpm[45] = 100, 2, 200
+    fpm[2] = 10
+    r = pkg.feast_scsr_solve("F", p.n, p.A.data, p.A.indptr, p.A.indices, fpm=fpm, emin=p.emin, emax=p.emax,
+                             m0=p.m0)
+    ev = np.linalg.eigvalsh(p.A.to_dense())
+    want = ev[(ev >= p.emin) & (ev <= p.emax)]
+    assert r.info == 0 and r.M == len(want)
+    assert np.abs(r.E[: r.M] - want).max() < 1e-10 * p.emax
+
+
+def test_bench_workload_properties(pkg):
+    """The 64^3 Laplacian + potential workload at full size (N = 262144, M0 =
+    150, Ne = 8): residuals recomputed by the oracle, B-orthonormality, and
+    agreement of the mixed and FP64 solvers."""
+    p = fw.laplace3d_potential()
+    mixed = run_gpu(pkg, p, 1)
+    assert mixed.info == 0 and 80 <= mixed.M <= 140
+    M = mixed.M
+    res = O.residuals(p.A, None, mixed.X[:, :M], mixed.E[:M], p.emin, p.emax)
+    assert res.max() <= RES_TOL
+    X = mixed.X[:, :M]
+    assert np.abs(X.T @ X - np.eye(M)).max() < 1e-11
+    full = run_gpu(pkg, p, 0)
+    assert full.info == 0 and full.M == M
+    assert (np.abs(mixed.E[:M] - full.E[:M]) / mixed.E[:M]).max() <= EIG_TOL
+    assert cluster_angles(mixed.E[:M], X, full.E[:M], full.X[:, :M], p.emax) <= ANG_TOL

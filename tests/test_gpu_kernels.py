@@ -1,0 +1,263 @@
+"""GPU parity of the individual kernels against the FP64 CPU oracle (or, for
+plain contractions, numpy FP64), element by element, at sizes that span
+several tiles plus a ragged tail."""
+import numpy as np
+import pytest
+import torch
+
+import feast_workloads as fw
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2002_04807_gb300 import build
+
+    build.build()
+    import paper_2002_04807_gb300 as p
+
+    p.library()
+    assert torch.cuda.is_available()
+    return p
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype).contiguous()
+
+
+def dcsr(M, dtype=torch.float64):
+    return dev(M.indptr, torch.int32), dev(M.indices, torch.int32), dev(M.data, dtype)
+
+
+def to_tiles(Pstd, nb, fp64, pkg):
+    """Pstd[e, i, j] complex (nb x n x m) -> tiled layout tensor (complex64/128 viewed as real pairs)."""
+    W, nbp, mt = pkg.feast_filter_layout(nb, fp64)
+    nbn, n, m = Pstd.shape
+    G = -(-m // mt)
+    T = np.zeros((G, n, W), dtype=np.complex128)
+    for j in range(m):
+        g, jl = divmod(j, mt)
+        for e in range(nb):
+            T[g, :, jl * nbp + e] = Pstd[e, :, j]
+    return T, (W, nbp, mt, G)
+
+
+def from_tiles(T, nb, m, lay):
+    W, nbp, mt, G = lay
+    n = T.shape[1]
+    out = np.zeros((nb, n, m), dtype=np.complex128)
+    for j in range(m):
+        g, jl = divmod(j, mt)
+        for e in range(nb):
+            out[e, :, j] = T[g, :, jl * nbp + e]
+    return out
+
+
+def shifted_ref(A, B, z, Pstd):
+    out = np.zeros_like(Pstd)
+    for e, ze in enumerate(z):
+        Pe = Pstd[e]
+        ar = O.csr_mm(A, Pe.real) + 1j * O.csr_mm(A, Pe.imag)
+        br = Pe if B is None else O.csr_mm(B, Pe.real) + 1j * O.csr_mm(B, Pe.imag)
+        out[e] = ze * br - ar
+    return out
+
+
+@pytest.mark.parametrize("fp64", [0, 1])
+@pytest.mark.parametrize("gen", [False, True])
+@pytest.mark.parametrize("nb,m", [(8, 10), (16, 3), (5, 7)])
+def test_shifted_spmm(pkg, fp64, gen, nb, m):
+    rng = np.random.default_rng(10 + nb + m)
+    p = fw.laplace3d_potential(side=11, count=10, m0=m, seed=4)  # n = 1331: 5 row blocks + tail
+    A = p.A
+    B = fw.diagonal_csr(rng.uniform(1, 2, A.n)) if gen else None
+    n = A.n
+    z = rng.uniform(0, 2, nb) + 1j * rng.uniform(0.05, 1, nb)
+    Pstd = rng.standard_normal((nb, n, m)) + 1j * rng.standard_normal((nb, n, m))
+    T, lay = to_tiles(Pstd, nb, fp64, pkg)
+    cdt = torch.complex128 if fp64 else torch.complex64
+    rdt = torch.float64 if fp64 else torch.float32
+    Pd = torch.as_tensor(T).to(device="cuda", dtype=cdt).contiguous()
+    Vd = torch.zeros_like(Pd)
+    ia, ja, av = dcsr(A, rdt)
+    ib = jb = bv = None
+    if B is not None:
+        ib, jb, bv = dcsr(B, rdt)
+    pkg.feast_shifted_spmm_dev(n, ia, ja, av, ib, jb, bv, z, m, fp64, Pd, Vd)
+    got = from_tiles(Vd.cpu().numpy().astype(np.complex128), nb, m, lay)
+    if not fp64:  # reference on the same rounded inputs
+        Pstd = from_tiles(Pd.cpu().numpy().astype(np.complex128), nb, m, lay)
+        A = fw.CSR(A.n, A.indptr, A.indices, A.data.astype(np.float32).astype(np.float64))
+        if B is not None:
+            B = fw.CSR(B.n, B.indptr, B.indices, B.data.astype(np.float32).astype(np.float64))
+        z = z.astype(np.complex64).astype(np.complex128)
+    ref = shifted_ref(A, B, z, Pstd)
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    assert err < (1e-14 if fp64 else 2e-6), err
+
+
+def _filter_case(side=10, m=12, seed=5):
+    p = fw.laplace3d_potential(side=side, count=8, m0=m, seed=seed)
+    return p
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_filter_classic_matches_oracle(pkg, mixed):
+    p = _filter_case()
+    n, m = p.n, p.m0
+    Y = p.y0()
+    fpm = pkg.feast_init()
+    fpm[1], fpm[17], fpm[41] = 8, 100, mixed
+    fpm[44], fpm[45] = (12, 3000) if not mixed else (6, 3000)
+    ia, ja, av = dcsr(p.A)
+    R = dev(Y)  # row-major n x m == C-order copy
+    Q = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+    it = pkg.feast_filter_dev(n, ia, ja, av, None, None, None, m, R, R, dev(np.zeros(m)), 0, fpm, p.emin, p.emax,
+                              Q)
+    assert it > 0
+    ref = O.filter_block(p.A, None, 8, p.emin, p.emax, 1.0, Y)
+    err = np.abs(Q.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err < (1e-8 if not mixed else 2e-3), err
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_filter_rii_matches_oracle(pkg, mixed):
+    p = _filter_case(side=9, m=10, seed=6)
+    n, m = p.n, p.m0
+    # a block near an invariant subspace, as in later FEAST passes
+    ev, V = np.linalg.eigh(p.A.to_dense())
+    rng = np.random.default_rng(0)
+    X = V[:, :m] + 1e-3 * rng.standard_normal((n, m))
+    lam = ev[:m] + 1e-4 * rng.standard_normal(m)
+    fpm = pkg.feast_init()
+    fpm[1], fpm[17], fpm[41] = 8, 100, mixed
+    fpm[44], fpm[45] = (12, 3000) if not mixed else (6, 3000)
+    ia, ja, av = dcsr(p.A)
+    # right-hand side of the residual-inverse form: R = A X - X diag(lam)
+    Rm = O.csr_mm(p.A, X) - X * lam
+    Q = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+    pkg.feast_filter_dev(n, ia, ja, av, None, None, None, m, dev(Rm), dev(X), dev(lam), 1, fpm, p.emin, p.emax, Q)
+    ref = O.filter_block(p.A, None, 8, p.emin, p.emax, 1.0, X, lam=lam, rii=True)
+    err = np.abs(Q.cpu().numpy() - ref).max() / np.abs(ref).max()
+    # the solve error is relative to ||R|| << ||X||, so even FP32 solves give a tight Q
+    assert err < (1e-10 if not mixed else 1e-5), err
+
+
+@pytest.mark.parametrize("n,m", [(1000, 70), (4097, 150), (33, 1), (262144, 150)])
+def test_gram(pkg, n, m):
+    rng = np.random.default_rng(n + m)
+    X = rng.standard_normal((n, m))
+    Y = rng.standard_normal((n, m))
+    C = torch.zeros((m, m), dtype=torch.float64, device="cuda")
+    pkg.feast_gram_dev(n, m, dev(X), dev(Y), C)
+    ref = X.T @ Y
+    ref = 0.5 * (ref + ref.T)
+    got = C.cpu().numpy()
+    # off-diagonal tiles keep the upper product, diagonal tiles are symmetrised
+    scale = np.sqrt(n)
+    assert np.abs(got - got.T).max() == 0.0
+    full = X.T @ Y
+    up = np.where(np.arange(m)[:, None] // 64 < np.arange(m)[None, :] // 64, full, full.T)
+    exp = np.where(np.arange(m)[:, None] // 64 == np.arange(m)[None, :] // 64, ref, up)
+    assert np.abs(got - exp).max() < 1e-13 * scale, np.abs(got - exp).max()
+
+
+@pytest.mark.parametrize("n,m,k", [(1000, 70, 65), (129, 150, 150), (7, 3, 2)])
+def test_gemm(pkg, n, m, k):
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, m))
+    V = rng.standard_normal((m, k))
+    C = torch.zeros((n, k), dtype=torch.float64, device="cuda")
+    pkg.feast_gemm_dev(n, m, k, dev(A), dev(V), C)
+    assert np.abs(C.cpu().numpy() - A @ V).max() < 1e-13 * np.sqrt(m)
+
+
+@pytest.mark.parametrize("m", [1, 2, 7, 64, 151, 300])
+def test_sym_eig_matches_oracle(pkg, m):
+    rng = np.random.default_rng(m)
+    a = rng.standard_normal((m, m))
+    a = a + a.T
+    A = dev(a)
+    lam = torch.zeros(m, dtype=torch.float64, device="cuda")
+    V = torch.zeros((m, m), dtype=torch.float64, device="cuda")
+    sweeps = pkg.feast_sym_eig_dev(m, A, lam, V)
+    w, _, _ = O.jacobi_eig(a)
+    lg = lam.cpu().numpy()
+    Vg = V.cpu().numpy()
+    nrm = max(1.0, np.abs(w).max())
+    assert np.abs(lg - w).max() < 1e-12 * nrm
+    assert np.abs(Vg.T @ Vg - np.eye(m)).max() < 1e-12
+    assert np.abs(a @ Vg - Vg * lg).max() < 1e-11 * nrm
+    assert sweeps < 40
+
+
+def test_sym_eig_degenerate_and_diagonal(pkg):
+    m = 40
+    rng = np.random.default_rng(1)
+    Qm, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    d = np.repeat([1.0, 2.0, 5.0, -3.0], 10)
+    a = Qm @ np.diag(d) @ Qm.T
+    a = 0.5 * (a + a.T)
+    lam = torch.zeros(m, dtype=torch.float64, device="cuda")
+    V = torch.zeros((m, m), dtype=torch.float64, device="cuda")
+    pkg.feast_sym_eig_dev(m, dev(a), lam, V)
+    assert np.abs(lam.cpu().numpy() - np.sort(d)).max() < 1e-12
+    # already diagonal: no rotation needed
+    lam2 = torch.zeros(m, dtype=torch.float64, device="cuda")
+    sw = pkg.feast_sym_eig_dev(m, dev(np.diag(d)), lam2, V)
+    assert sw <= 1 and np.array_equal(lam2.cpu().numpy(), np.sort(d))
+
+
+def test_reduced_eig_matches_oracle(pkg):
+    rng = np.random.default_rng(3)
+    m = 40
+    a = rng.standard_normal((m, m)); a = a + a.T
+    g = rng.standard_normal((m, m)); b = g @ g.T + 0.5 * np.eye(m)
+    lam = torch.zeros(m, dtype=torch.float64, device="cuda")
+    V = torch.zeros((m, m), dtype=torch.float64, device="cuda")
+    mk = pkg.feast_reduced_eig_dev(m, dev(a), dev(b), lam, V)
+    info, lo, Vo = O.reduced_gev(a, b)
+    assert mk == len(lo) == m
+    assert np.abs(lam.cpu().numpy() - lo).max() < 1e-11 * np.abs(lo).max()
+    Vg = V.cpu().numpy()
+    assert np.abs(Vg.T @ b @ Vg - np.eye(m)).max() < 1e-11
+
+
+def test_reduced_eig_rank_deficient(pkg):
+    rng = np.random.default_rng(4)
+    Qb = rng.standard_normal((60, 7))
+    Qb = np.hstack([Qb, Qb[:, :3] @ rng.standard_normal((3, 3))])  # rank 7 of 10
+    a = rng.standard_normal((60, 60)); a = a + a.T
+    Aq, Bq = Qb.T @ a @ Qb, Qb.T @ Qb
+    m = 10
+    lam = torch.zeros(m, dtype=torch.float64, device="cuda")
+    V = torch.zeros((m, m), dtype=torch.float64, device="cuda")
+    mk = pkg.feast_reduced_eig_dev(m, dev(Aq), dev(Bq), lam, V)
+    info, lo, _ = O.reduced_gev(Aq, Bq)
+    assert mk == len(lo) == 7
+    lg = lam.cpu().numpy()
+    assert np.abs(lg[:7] - lo).max() < 1e-8 * np.abs(lo).max()
+    assert np.all(lg[7:] >= 1e299)
+
+
+@pytest.mark.parametrize("gen", [False, True])
+def test_residual_matches_oracle(pkg, gen):
+    rng = np.random.default_rng(8)
+    p = fw.laplace3d_potential(side=13, count=10, m0=37, seed=2)
+    A = p.A
+    B = fw.diagonal_csr(rng.uniform(1, 2, A.n)) if gen else None
+    X = rng.standard_normal((A.n, 37))
+    lam = rng.uniform(0, 1, 37)
+    R = torch.zeros((A.n, 37), dtype=torch.float64, device="cuda")
+    res = torch.zeros(37, dtype=torch.float64, device="cuda")
+    ia, ja, av = dcsr(A)
+    ib = jb = bv = None
+    if gen:
+        ib, jb, bv = dcsr(B)
+    pkg.feast_residual_dev(A.n, ia, ja, av, ib, jb, bv, 37, dev(X), dev(lam), 1.7, R, res)
+    ref = O.residuals(A, B, X, lam, -1.7, 0.5)
+    assert np.abs(res.cpu().numpy() - ref).max() < 1e-13 * ref.max()
+    BX = X if B is None else O.csr_mm(B, X)
+    assert np.abs(R.cpu().numpy() - (O.csr_mm(A, X) - BX * lam)).max() < 1e-12
