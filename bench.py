@@ -59,7 +59,7 @@ def config_dict(p, extra=None):
     d = {"workload": f"laplace3d_7pt_{round(p.n ** (1 / 3))}^3_potential_U[0,0.5]_seed1",
          "N": p.n, "nnz": p.A.nnz, "M0": p.m0, "Ne": p.ne, "contour_ratio_pct": p.ratio,
          "interval": [p.emin, round(p.emax, 6)], "B": "identity", "tol": RES_TOL,
-         "inner_solver": "COCG, fpm(45)=2 (1e-2), fpm(46)=200",
+         "inner_solver": "COCG, fpm(45)=2 (1e-2), fpm(46)=80, one node per batch (fpm(50)=1)",
          "l2": "inputs larger than L2 (each filter block vector 2.5 GB)"}
     if extra:
         d.update(extra)
@@ -70,7 +70,8 @@ def fpm_for(pkg, p, mixed, profile):
     f = pkg.feast_init()
     f[1], f[2], f[3], f[4], f[17] = p.ne, 10, 40, 1, p.ratio
     f[41] = 1 if mixed else 0
-    f[44], f[45] = 2, 200
+    f[44], f[45] = 2, 80
+    f[49] = 1  # one contour node per batch: groups of a fast node stop early
     f[52] = 1 if profile else 0
     return f
 
@@ -289,11 +290,13 @@ def run_gpu(args):
     # roofline of the dominant kernel from the per-launch events of the timed steps
     pr = prof_tot
     n, W, mt, sc, G = pr["n"], pr["W"], pr["mt"], pr["complex_bytes"], pr["groups"]
-    live = (p.m0 * p.ne) / (G * W)  # padded lanes are not algorithmic work
+    nbp = W / mt  # node lanes per column in a tile
+    live = (p.m0 * min(nbp, p.ne)) / (G * W)  # padded lanes are not algorithmic work
     mat = p.A.nnz * (4 + (4 if sc == 8 else 8)) + (p.n + 1) * 4
     tile = n * W * sc * live
     bytes_a = pr["group_iterations"] * 3 * tile + pr["cocg_a_launches"] * mat
-    bytes_b = pr["group_iterations"] * (3 * tile + n * mt * 16 * live) + pr["cocg_b_launches"] * mat
+    qb = 4 if sc == 8 else 8  # quadrature accumulator: FP32 in mixed precision
+    bytes_b = pr["group_iterations"] * (3 * tile + n * mt * 2 * qb * live) + pr["cocg_b_launches"] * mat
     gbs_a = bytes_a / (pr["cocg_a_ms"] / 1e3) / 1e9
     gbs_b = bytes_b / (pr["cocg_b_ms"] / 1e3) / 1e9
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")

@@ -148,11 +148,12 @@ int feast_filter_layout(int nb, int fp64, int* W, int* nbp, int* mt);
 /* Batched complex-shifted CSR SpMM (the inner product of every COCG step):
  * V_e = (z_e B - A) P_e for nb nodes and m columns in one launch, in the
  * layout of feast_filter_layout.  z: host, 2*nb doubles (re, im).  A, B:
- * 0-based device CSR with values of the filter's real type (float if
- * fp64 = 0, double if 1); B may be NULL (identity).  P, V: device. */
-int feast_shifted_spmm_dev(int n, const int* ia, const int* ja, const void* a, const int* ib, const int* jb,
-                           const void* b, int nb, const double* z, int m, int fp64, const void* P, void* V,
-                           void* stream);
+ * 0-based device CSR with FP64 values, rounded to float when fp64 = 0 (as
+ * the mixed-precision solver does); B may be NULL (identity).  P, V: device
+ * complex float (fp64 = 0) or complex double (fp64 = 1) tiles. */
+int feast_shifted_spmm_dev(int n, int nnz_a, const int* ia, const int* ja, const double* a, int nnz_b,
+                           const int* ib, const int* jb, const double* b, int nb, const double* z, int m,
+                           int fp64, const void* P, void* V, void* stream);
 
 /* One filter pass over all ne nodes (guide Sec. 1.2 quadrature; Sec. 2.2
  * residual inverse form):

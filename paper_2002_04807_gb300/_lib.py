@@ -28,7 +28,7 @@ _SIGS = {
     "feast_scsr_solve_dev": (_i, [_i, _i, _p, _p, _p, _i, _p, _p, _p, _p, _d, _d, _p, _p, _p, _p, _p, _p, _p,
                                   _p, _p, C.c_size_t, _p]),
     "feast_filter_layout": (_i, [_i, _i, _p, _p, _p]),
-    "feast_shifted_spmm_dev": (_i, [_i, _p, _p, _p, _p, _p, _p, _i, _p, _i, _i, _p, _p, _p]),
+    "feast_shifted_spmm_dev": (_i, [_i, _i, _p, _p, _p, _i, _p, _p, _p, _i, _p, _i, _i, _p, _p, _p]),
     "feast_filter_dev": (_i, [_i, _i, _p, _p, _p, _i, _p, _p, _p, _i, _p, _p, _p, _i, _p, _d, _d, _p, _p, _p]),
     "feast_gram_dev": (_i, [_i, _i, _p, _p, _p, _p]),
     "feast_gemm_dev": (_i, [_i, _i, _i, _p, _p, _p, _p]),
@@ -226,9 +226,9 @@ def feast_scsr_solve_dev(n: int, ia, ja, a, ib=None, jb=None, b=None, fpm=None, 
 def feast_shifted_spmm_dev(n, ia, ja, a, ib, jb, b, z, m, fp64, P, V, stream=None):
     z = np.ascontiguousarray(np.column_stack([np.real(z), np.imag(z)]).ravel(), dtype=np.float64)
     nb = len(z) // 2
-    _check(library().feast_shifted_spmm_dev(n, _ptr(ia), _ptr(ja), _ptr(a), _ptr(ib), _ptr(jb), _ptr(b), nb,
-                                            _ptr(z), m, int(fp64), _ptr(P), _ptr(V), _stream(stream)),
-           "feast_shifted_spmm_dev")
+    _check(library().feast_shifted_spmm_dev(n, a.numel(), _ptr(ia), _ptr(ja), _ptr(a), 0 if b is None else b.numel(),
+                                            _ptr(ib), _ptr(jb), _ptr(b), nb, _ptr(z), m, int(fp64), _ptr(P), _ptr(V),
+                                            _stream(stream)), "feast_shifted_spmm_dev")
 
 
 def feast_filter_dev(n, ia, ja, a, ib, jb, b, m, R, X, lam, rii, fpm, emin, emax, Q, stream=None) -> int:

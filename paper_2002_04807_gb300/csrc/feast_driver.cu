@@ -179,7 +179,8 @@ struct Bufs {
     int* groups_left = nullptr;
     unsigned long long* work = nullptr;
     FiltProb* probs = nullptr;
-    float *avf = nullptr, *bvf = nullptr;
+    void *apk = nullptr, *bpk = nullptr;  // packed (column, value) CSR entries
+    void* dQ = nullptr;                   // per-pass quadrature accumulator (filter precision)
     double* zw = nullptr;
     double *Y = nullptr, *Q = nullptr, *X = nullptr, *T = nullptr, *T2 = nullptr;
     double *Aq = nullptr, *Bq = nullptr, *Vr = nullptr, *lam = nullptr, *res = nullptr;
@@ -249,10 +250,10 @@ size_t carve(const Plan& P, void* base, Bufs& B, bool filter_only = false)
     B.groups_left = c.take<int>(1);
     B.work = c.take<unsigned long long>(1);
     B.probs = c.take<FiltProb>(1);
-    if (!P.fp64) {
-        B.avf = c.take<float>(P.nnzA);
-        if (P.hasB) B.bvf = c.take<float>(P.nnzB);
-    }
+    const size_t pk = P.fp64 ? 16 : 8;
+    B.apk = c.take<char>((size_t)P.nnzA * pk);
+    if (P.hasB) B.bpk = c.take<char>((size_t)P.nnzB * pk);
+    B.dQ = c.take<char>((size_t)P.n * P.m0 * (P.fp64 ? 8 : 4));
     B.zw = c.take<double>(4 * (size_t)P.ne);
     if (filter_only) return c.off + 256;
     const size_t blk = (size_t)P.n * P.m0;
@@ -390,6 +391,7 @@ int filter_pass(const Plan& P, Bufs& B, int rii, const double* R, const double* 
     fa.nbp = P.nbp;
     fa.mt = P.mt;
     fa.RB = P.RB;
+    fa.hasB = P.hasB ? 1 : 0;
     fa.r = B.r;
     fa.p0 = B.p0;
     fa.p1 = B.p1;
@@ -398,6 +400,7 @@ int filter_pass(const Plan& P, Bufs& B, int rii, const double* R, const double* 
     fa.grp_count = B.grp_count;
     fa.grp_done = B.grp_done;
     fa.Q = B.Q;
+    fa.dQ = B.dQ;
     fa.tol2 = tol * tol;
     fa.groups_left = B.groups_left;
     fa.work = B.work;
@@ -433,6 +436,7 @@ int filter_pass(const Plan& P, Bufs& B, int rii, const double* R, const double* 
             }
         }
     }
+    CK(launch_fold_dq((long long)P.n * P.m0, B.dQ, P.fp64, B.Q, s));
     return 0;
 }
 
@@ -440,10 +444,8 @@ int setup_filter(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, const std:
                  const double* lam, const int* mk, cudaStream_t s)
 {
     CK(cudaMemcpyAsync(B.zw, zw.data(), sizeof(double) * zw.size(), cudaMemcpyHostToDevice, s));
-    if (!P.fp64) {
-        CK(launch_cast_values(A.v, B.avf, A.nnz, s));
-        if (P.hasB) CK(launch_cast_values(Bm.v, B.bvf, Bm.nnz, s));
-    }
+    CK(launch_pack_csr(A.nnz, A.ja, A.v, P.fp64, B.apk, s));
+    if (P.hasB) CK(launch_pack_csr(Bm.nnz, Bm.ja, Bm.v, P.fp64, B.bpk, s));
     FiltProb fp;
     memset(&fp, 0, sizeof(fp));
     fp.n = P.n;
@@ -457,10 +459,12 @@ int setup_filter(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, const std:
     fp.q_off = 0;
     fp.ia = A.ia;
     fp.ja = A.ja;
-    fp.av = P.fp64 ? (const void*)A.v : (const void*)B.avf;
+    fp.av = A.v;
     fp.ib = P.hasB ? Bm.ia : nullptr;
     fp.jb = P.hasB ? Bm.ja : nullptr;
-    fp.bv = P.hasB ? (P.fp64 ? (const void*)Bm.v : (const void*)B.bvf) : nullptr;
+    fp.bv = P.hasB ? Bm.v : nullptr;
+    fp.apk = B.apk;
+    fp.bpk = P.hasB ? B.bpk : nullptr;
     fp.zw = B.zw;
     fp.lam = lam;
     fp.mk = mk;
@@ -502,6 +506,8 @@ int run_feast(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, int* fpm, dou
     contour(ne, emin, emax, fpm[17] / 100.0, zw);
     int st = setup_filter(P, B, A, Bm, zw, B.lam, B.mk, s);
     if (st) return st;
+    // every subspace column is live until a reduced solve drops some
+    CK(cudaMemcpyAsync(B.mk, &m0, sizeof(int), cudaMemcpyHostToDevice, s));
     const size_t blk = (size_t)n * m0;
     // start block Y (row-major) and the first right-hand side B Y
     if (fpm[4] == 1) {
@@ -513,15 +519,23 @@ int run_feast(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, int* fpm, dou
         count_launches(1);
     }
     CK(cudaGetLastError());
-    double* R = B.Y;
-    if (P.hasB) {
-        CK(launch_spmm_f64(n, m0, Bm.ia, Bm.ja, Bm.v, B.Y, B.T, s));
-        R = B.T;
+    size_t ph0 = 0;
+    if (fpm[4] == 1) {
+        // a given subspace is tested by Rayleigh-Ritz before any filtering, so
+        // a converged subspace (e.g. a previous solution) returns at loop 0
+        CK(cudaMemcpyAsync(B.Q, B.Y, sizeof(double) * blk, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(B.iter_max, 0, sizeof(int) * P.nbatch, s));
+    } else {
+        double* R = B.Y;
+        if (P.hasB) {
+            CK(launch_spmm_f64(n, m0, Bm.ia, Bm.ja, Bm.v, B.Y, B.T, s));
+            R = B.T;
+        }
+        ph0 = g_prof.on ? g_prof.mark(s) : 0;
+        st = filter_pass(P, B, 0, R, nullptr, maxit, tol, s);
+        if (st) return st;
+        if (g_prof.on) g_prof.phase.push_back({0, {ph0, g_prof.mark(s)}});
     }
-    size_t ph0 = g_prof.on ? g_prof.mark(s) : 0;
-    st = filter_pass(P, B, 0, R, nullptr, maxit, tol, s);
-    if (st) return st;
-    if (g_prof.on) g_prof.phase.push_back({0, {ph0, g_prof.mark(s)}});
     std::vector<int> itmax(P.nbatch);
     long long total_iters = 0;
     CK(cudaMemcpyAsync(itmax.data(), B.iter_max, sizeof(int) * P.nbatch, cudaMemcpyDeviceToHost, s));
@@ -824,14 +838,14 @@ struct AsyncMem {
 };
 }  // namespace
 
-extern "C" int feast_shifted_spmm_dev(int n, const int* ia, const int* ja, const void* a, const int* ib,
-                                      const int* jb, const void* b, int nb, const double* z, int m, int fp64,
-                                      const void* P, void* V, void* stream)
+extern "C" int feast_shifted_spmm_dev(int n, int nnz_a, const int* ia, const int* ja, const double* a, int nnz_b,
+                                      const int* ib, const int* jb, const double* b, int nb, const double* z, int m,
+                                      int fp64, const void* P, void* V, void* stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
     if (n <= 0) return -101;
-    if (nb < 1 || nb > 32) return -108;
-    if (m <= 0) return -110;
+    if (nb < 1 || nb > 32) return -110;
+    if (m <= 0) return -112;
     int W, nbp, mt;
     feast_filter_layout(nb, fp64, &W, &nbp, &mt);
     const int G = (m + mt - 1) / mt;
@@ -843,6 +857,17 @@ extern "C" int feast_shifted_spmm_dev(int n, const int* ia, const int* ja, const
         const int e = (c % W) % nbp;
         if (e < nb) cs[c].z = make_double2(z[2 * e], z[2 * e + 1]);
     }
+    AsyncMem am(s);
+    void *d_cs = nullptr, *d_fp = nullptr, *apk = nullptr, *bpk = nullptr;
+    const size_t pk = fp64 ? 16 : 8;
+    CK(am.alloc(&d_cs, sizeof(ColState) * cs.size()));
+    CK(am.alloc(&d_fp, sizeof(FiltProb)));
+    CK(am.alloc(&apk, pk * (size_t)std::max(1, nnz_a)));
+    CK(launch_pack_csr(nnz_a, ja, a, fp64 != 0, apk, s));
+    if (b) {
+        CK(am.alloc(&bpk, pk * (size_t)std::max(1, nnz_b)));
+        CK(launch_pack_csr(nnz_b, jb, b, fp64 != 0, bpk, s));
+    }
     FiltProb fp;
     memset(&fp, 0, sizeof(fp));
     fp.n = n;
@@ -852,13 +877,11 @@ extern "C" int feast_shifted_spmm_dev(int n, const int* ia, const int* ja, const
     fp.ia = ia;
     fp.ja = ja;
     fp.av = a;
-    fp.ib = ib;
-    fp.jb = jb;
+    fp.ib = b ? ib : nullptr;
+    fp.jb = b ? jb : nullptr;
     fp.bv = b;
-    AsyncMem am(s);
-    void *d_cs = nullptr, *d_fp = nullptr;
-    CK(am.alloc(&d_cs, sizeof(ColState) * cs.size()));
-    CK(am.alloc(&d_fp, sizeof(FiltProb)));
+    fp.apk = apk;
+    fp.bpk = b ? bpk : nullptr;
     CK(cudaMemcpyAsync(d_cs, cs.data(), sizeof(ColState) * cs.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(d_fp, &fp, sizeof(fp), cudaMemcpyHostToDevice, s));
     FilterArgs fa;
@@ -870,6 +893,7 @@ extern "C" int feast_shifted_spmm_dev(int n, const int* ia, const int* ja, const
     fa.nbp = nbp;
     fa.mt = mt;
     fa.RB = RB;
+    fa.hasB = b ? 1 : 0;
     fa.p0 = const_cast<void*>(P);
     fa.p1 = V;
     fa.cs = (ColState*)d_cs;

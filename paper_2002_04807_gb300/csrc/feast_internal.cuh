@@ -41,6 +41,8 @@ struct FiltProb {
     const int* ib;      // B row pointers, or nullptr for B = I
     const int* jb;
     const void* bv;
+    const void* apk;    // A as packed (column, value) entries: int2 (float) or int4 (double)
+    const void* bpk;    // B packed, or nullptr
     const double* zw;   // Ne nodes and weights, [Ne][4] = (Re z, Im z, Re w, Im w)
     const double* lam;  // Ritz values of the previous Rayleigh-Ritz step [m0]
     const int* mk;      // live subspace columns (device), or nullptr for m0
@@ -71,6 +73,7 @@ struct FilterArgs {
     int nbp;        // node lanes per subspace column (power of two)
     int mt;         // subspace columns per group = W / nbp
     int RB;         // rows per work item
+    int hasB;       // 1 when the problems have a B matrix (all or none)
     void* r;        // residual block vectors (complex T)
     void* p0;       // search directions, ping
     void* p1;       // search directions, pong
@@ -79,6 +82,7 @@ struct FilterArgs {
     unsigned* grp_count;  // per-group finished-item counters
     int* grp_done;  // per-group "no active column" flags
     double* Q;      // FP64 filter accumulator (row-major n x m0 per problem)
+    void* dQ;       // per-pass accumulator of the quadrature sum, filter precision, same layout
     double tol2;    // squared relative COCG tolerance
     int* iter_max;  // per-problem max iteration reached
     int* groups_left;  // per-problem number of groups still iterating
@@ -93,6 +97,8 @@ cudaError_t launch_filter_init(const FilterArgs& a, bool fp64, const double* R, 
 cudaError_t launch_colstate_init(const FilterArgs& a, int node0, int rii, cudaStream_t s);
 cudaError_t launch_shifted_spmm(const FilterArgs& a, bool fp64, int grid, cudaStream_t s);
 cudaError_t launch_cast_values(const double* src, float* dst, long long n, cudaStream_t s);
+cudaError_t launch_fold_dq(long long total, const void* dQ, bool fp64, double* Q, cudaStream_t s);
+cudaError_t launch_pack_csr(long long nnz, const int* ja, const double* av, bool fp64, void* out, cudaStream_t s);
 // persistent grid size of the COCG kernels: SMs x resident CTAs per SM
 int filter_grid(bool fp64, int W);
 

@@ -39,6 +39,13 @@ namespace feast {
 
 static constexpr int kThreads = 256;
 static constexpr int kPartStride = 4;
+#ifndef FEAST_ROWS
+#define FEAST_ROWS 4
+#endif
+#ifndef FEAST_MINB
+#define FEAST_MINB 3
+#endif
+static constexpr int kRows = FEAST_ROWS;  // rows per thread gathered in lockstep
 
 __device__ __forceinline__ int find_prob(const FiltProb* probs, int nprob, long long item)
 {
@@ -57,48 +64,114 @@ __device__ __forceinline__ unsigned seg_mask(int sub)
     return W == 32 ? 0xffffffffu : (((1u << W) - 1u) << (sub * W));
 }
 
-// Gather sum_k v_k x[j_k] over one CSR row for the lane's column; the row's
-// indices and values are loaded once, coalesced, and broadcast by shuffles.
-// With UPD, x[j] = r[j] + beta * p[j] is formed on the fly.
+// One CSR row of packed (column, value) entries, read with uniform loads (all
+// lanes of a row segment read the same entry, served as one broadcast) and
+// gathered against the lane's column of x (and of p when UPD):
+//   ax = sum_k a_k x[j_k],  ap = sum_k a_k p[j_k].
+// U entries are fetched before any is used, so each warp keeps U (or 2U)
+// independent row-segment loads in flight.
+template <typename T> __device__ __forceinline__ void load_pk(const void* pk, int t, int& j, T& a);
+template <> __device__ __forceinline__ void load_pk<float>(const void* pk, int t, int& j, float& a)
+{
+    const int2 v = __ldg((const int2*)pk + t);
+    j = v.x;
+    a = __int_as_float(v.y);
+}
+template <> __device__ __forceinline__ void load_pk<double>(const void* pk, int t, int& j, double& a)
+{
+    const int4 v = __ldg((const int4*)pk + t);
+    j = v.x;
+    a = __hiloint2double(v.w, v.z);
+}
+
 template <typename T, int W, bool UPD>
-__device__ __forceinline__ c2_t<T> row_gather(const int* __restrict__ ia, const int* __restrict__ ja,
-                                              const T* __restrict__ av, int i, unsigned mask, int cl,
-                                              const c2_t<T>* __restrict__ x, const c2_t<T>* __restrict__ p,
-                                              c2_t<T> beta, bool use_p)
+__device__ __forceinline__ void row_gather(const int* __restrict__ ia, const void* __restrict__ pk, int i, int cl,
+                                           const c2_t<T>* __restrict__ x, const c2_t<T>* __restrict__ p,
+                                           bool use_p, c2_t<T>& ax, c2_t<T>& ap)
 {
     using V = c2_t<T>;
-    V acc = cmk<V>(T(0), T(0));
+    constexpr int U = UPD ? 4 : 8;
+    ax = cmk<V>(T(0), T(0));
+    ap = cmk<V>(T(0), T(0));
     const int s = __ldg(ia + i), e = __ldg(ia + i + 1);
-    for (int base = s; base < e; base += W) {
-        const int cnt = min(W, e - base);
-        int jl = 0;
-        T al = T(0);
-        if (cl < cnt) {
-            jl = __ldg(ja + base + cl);
-            al = __ldg(av + base + cl);
+    for (int t0 = s; t0 < e; t0 += U) {
+        V xv[U], pv[U];
+        T av[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + u;
+            int j = 0;
+            T aa = T(0);
+            if (t < e) load_pk<T>(pk, t, j, aa);
+            av[u] = aa;
+            xv[u] = (t < e) ? __ldg(x + (size_t)j * W + cl) : cmk<V>(T(0), T(0));
+            if (UPD) pv[u] = (t < e && use_p) ? __ldg(p + (size_t)j * W + cl) : cmk<V>(T(0), T(0));
         }
-        for (int t = 0; t < cnt; ++t) {
-            const int j = __shfl_sync(mask, jl, t, W);
-            const T a = __shfl_sync(mask, al, t, W);
-            V v = __ldg(x + (size_t)j * W + cl);
-            if (UPD && use_p) v = cfma(beta, __ldg(p + (size_t)j * W + cl), v);
-            acc.x = fma(a, v.x, acc.x);
-            acc.y = fma(a, v.y, acc.y);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            ax.x = fma(av[u], xv[u].x, ax.x);
+            ax.y = fma(av[u], xv[u].y, ax.y);
+            if (UPD) {
+                ap.x = fma(av[u], pv[u].x, ap.x);
+                ap.y = fma(av[u], pv[u].y, ap.y);
+            }
         }
     }
-    return acc;
+}
+
+// R rows gathered in lockstep by one thread (rows of the same tile, R*RPP
+// apart): the t-th entries of all R rows are fetched together, so the loads
+// that miss L2 (the leading edge of a wide stencil) of R rows overlap.
+template <typename T, int W, bool UPD, int R>
+__device__ __forceinline__ void rows_gather(const int* __restrict__ ia, const void* __restrict__ pk, const int (&row)[R],
+                                            int cl, const c2_t<T>* __restrict__ x, const c2_t<T>* __restrict__ p,
+                                            bool use_p, c2_t<T> (&ax)[R], c2_t<T> (&ap)[R])
+{
+    using V = c2_t<T>;
+    int s[R], e[R], len = 0;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        s[q] = row[q] >= 0 ? __ldg(ia + row[q]) : 0;
+        e[q] = row[q] >= 0 ? __ldg(ia + row[q] + 1) : 0;
+        len = max(len, e[q] - s[q]);
+        ax[q] = cmk<V>(T(0), T(0));
+        ap[q] = cmk<V>(T(0), T(0));
+    }
+    for (int t = 0; t < len; ++t) {
+        V xv[R], pv[R];
+        T av[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const bool ok = s[q] + t < e[q];
+            int j = 0;
+            T aa = T(0);
+            if (ok) load_pk<T>(pk, s[q] + t, j, aa);
+            av[q] = aa;
+            xv[q] = ok ? __ldg(x + (size_t)j * W + cl) : cmk<V>(T(0), T(0));
+            if (UPD) pv[q] = (ok && use_p) ? __ldg(p + (size_t)j * W + cl) : cmk<V>(T(0), T(0));
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            ax[q].x = fma(av[q], xv[q].x, ax[q].x);
+            ax[q].y = fma(av[q], xv[q].y, ax[q].y);
+            if (UPD) {
+                ap[q].x = fma(av[q], pv[q].x, ap[q].x);
+                ap[q].y = fma(av[q], pv[q].y, ap[q].y);
+            }
+        }
+    }
 }
 
 // Block-wide reduction of NV per-thread doubles for each of the W lane
 // columns, written to part[item][cl][0..NV).  Fixed order => deterministic.
-template <int W, int NV>
-__device__ __forceinline__ void block_partials(double (&v)[NV], double* sm, double* out)
+template <int W, int NV, typename T>
+__device__ __forceinline__ void block_partials(T (&v)[NV], double* sm, double* out)
 {
     constexpr int SEGS = kThreads / W;
     const int tid = threadIdx.x;
     const int cl = tid % W, seg = tid / W;
 #pragma unroll
-    for (int q = 0; q < NV; ++q) sm[(seg * W + cl) * NV + q] = v[q];
+    for (int q = 0; q < NV; ++q) sm[(seg * W + cl) * NV + q] = (double)v[q];
     __syncthreads();
     if (tid < W) {
         double s[NV];
@@ -162,8 +235,8 @@ __device__ __forceinline__ bool arrive_group(unsigned* counter, int nrb, int* fl
 }
 
 // ---------------------------------------------------------------- kernel A
-template <typename T, int W>
-__global__ void __launch_bounds__(kThreads) cocg_step_a(FilterArgs a, int k)
+template <typename T, int W, bool HASB>
+__global__ void __launch_bounds__(kThreads, FEAST_MINB) cocg_step_a(FilterArgs a, int k)
 {
     using V = c2_t<T>;
     constexpr int RPP = kThreads / W;  // rows per pass of the CTA
@@ -192,24 +265,35 @@ __global__ void __launch_bounds__(kThreads) cocg_step_a(FilterArgs a, int k)
         const V* r = (const V*)a.r + tile;
         const V* po = pold + tile;
         V* pn = pnew + tile;
-        const T* av = (const T*)P.av;
-        const T* bv = (const T*)P.bv;
-        double acc[3] = {0.0, 0.0, 0.0};  // sigma.re, sigma.im, ||b||^2 (first)
+        T acc[3] = {T(0), T(0), T(0)};  // sigma.re, sigma.im, ||b||^2 (first); FP32 in mixed precision
         const int row0 = rb * a.RB;
-        for (int rl = rowslot; rl < a.RB; rl += RPP) {
-            const int i = row0 + rl;
-            if (i >= P.n) break;
-            const V ax = row_gather<T, W, true>(P.ia, P.ja, av, i, mask, cl, r, po, beta, use_p);
-            V pi_ = __ldg(r + (size_t)i * W + cl);
-            if (use_p) pi_ = cfma(beta, __ldg(po + (size_t)i * W + cl), pi_);
-            V bx;
-            if (P.ib == nullptr) bx = pi_;
-            else bx = row_gather<T, W, true>(P.ib, P.jb, bv, i, mask, cl, r, po, beta, use_p);
-            const V q = csub(cmul(z, bx), ax);
-            pn[(size_t)i * W + cl] = pi_;
-            acc[0] += (double)(pi_.x * q.x - pi_.y * q.y);
-            acc[1] += (double)(pi_.x * q.y + pi_.y * q.x);
-            if (first) acc[2] += (double)(pi_.x * pi_.x + pi_.y * pi_.y);
+        for (int rl = rowslot; rl < a.RB; rl += RPP * kRows) {
+            int rows[kRows];
+#pragma unroll
+            for (int q = 0; q < kRows; ++q) {
+                const int i = row0 + rl + q * RPP;
+                rows[q] = (rl + q * RPP < a.RB && i < P.n) ? i : -1;
+            }
+            if (rows[0] < 0) break;
+            V ar[kRows], ap[kRows];
+            rows_gather<T, W, true, kRows>(P.ia, P.apk, rows, cl, r, po, use_p, ar, ap);
+            V br[kRows], bp[kRows];
+            if (HASB) rows_gather<T, W, true, kRows>(P.ib, P.bpk, rows, cl, r, po, use_p, br, bp);
+#pragma unroll
+            for (int q = 0; q < kRows; ++q) {
+                if (rows[q] < 0) continue;
+                const int i = rows[q];
+                V pi_ = __ldg(r + (size_t)i * W + cl);
+                if (use_p) pi_ = cfma(beta, __ldg(po + (size_t)i * W + cl), pi_);
+                const V ax = use_p ? cfma(beta, ap[q], ar[q]) : ar[q];  // A (r + beta p)
+                V bx = pi_;
+                if (HASB) bx = use_p ? cfma(beta, bp[q], br[q]) : br[q];
+                const V qv = csub(cmul(z, bx), ax);
+                pn[(size_t)i * W + cl] = pi_;
+                acc[0] = fma(pi_.x, qv.x, fma(-pi_.y, qv.y, acc[0]));
+                acc[1] = fma(pi_.x, qv.y, fma(pi_.y, qv.x, acc[1]));
+                if (first) acc[2] = fma(pi_.x, pi_.x, fma(pi_.y, pi_.y, acc[2]));
+            }
         }
         block_partials<W, 3>(acc, sm, a.part + (size_t)item * W * kPartStride);
         if (arrive_group(a.grp_count + P.grp_off + g, P.nrb, &flag)) {
@@ -244,8 +328,8 @@ __global__ void __launch_bounds__(kThreads) cocg_step_a(FilterArgs a, int k)
 }
 
 // ---------------------------------------------------------------- kernel B
-template <typename T, int W>
-__global__ void __launch_bounds__(kThreads) cocg_step_b(FilterArgs a, int k)
+template <typename T, int W, bool HASB>
+__global__ void __launch_bounds__(kThreads, FEAST_MINB) cocg_step_b(FilterArgs a, int k)
 {
     using V = c2_t<T>;
     constexpr int RPP = kThreads / W;
@@ -273,33 +357,44 @@ __global__ void __launch_bounds__(kThreads) cocg_step_b(FilterArgs a, int k)
         const size_t tile = (size_t)P.vec_off + (size_t)g * P.n * W;
         V* r = (V*)a.r + tile;
         const V* p = pk + tile;
-        const T* av = (const T*)P.av;
-        const T* bv = (const T*)P.bv;
         const int m = g * a.mt + mloc;
-        double* Qrow = a.Q + P.q_off + m;
-        double acc[3] = {0.0, 0.0, 0.0};  // rho.re, rho.im, ||r||^2
+        T* dQrow = (T*)a.dQ + P.q_off + m;
+        T acc[3] = {T(0), T(0), T(0)};  // rho.re, rho.im, ||r||^2
         const int row0 = rb * a.RB;
-        for (int rl = rowslot; rl < a.RB; rl += RPP) {
-            const int i = row0 + rl;
-            if (i >= P.n) break;
-            const V ax = row_gather<T, W, false>(P.ia, P.ja, av, i, mask, cl, p, nullptr, alpha, false);
-            const V pi_ = __ldg(p + (size_t)i * W + cl);
-            V bx;
-            if (P.ib == nullptr) bx = pi_;
-            else bx = row_gather<T, W, false>(P.ib, P.jb, bv, i, mask, cl, p, nullptr, alpha, false);
-            V ri = r[(size_t)i * W + cl];
-            T qc = T(0);
-            if (active) {
-                const V q = csub(cmul(z, bx), ax);
-                ri = csub(ri, cmul(alpha, q));
-                r[(size_t)i * W + cl] = ri;
-                qc = ca.x * pi_.x - ca.y * pi_.y;  // Re(c alpha p)
+        for (int rl = rowslot; rl < a.RB; rl += RPP * kRows) {
+            int rows[kRows];
+#pragma unroll
+            for (int q = 0; q < kRows; ++q) {
+                const int i = row0 + rl + q * RPP;
+                rows[q] = (rl + q * RPP < a.RB && i < P.n) ? i : -1;
             }
-            for (int o = 1; o < a.nbp; o <<= 1) qc += __shfl_xor_sync(mask, qc, o, W);
-            if (e == 0 && m < P.m0) Qrow[(size_t)i * P.m0] += (double)qc;
-            acc[0] += (double)(ri.x * ri.x - ri.y * ri.y);
-            acc[1] += (double)(2 * ri.x * ri.y);
-            acc[2] += (double)(ri.x * ri.x + ri.y * ri.y);
+            if (rows[0] < 0) break;
+            V ax[kRows], unused[kRows], bxs[kRows];
+            rows_gather<T, W, false, kRows>(P.ia, P.apk, rows, cl, p, nullptr, false, ax, unused);
+            if (HASB) rows_gather<T, W, false, kRows>(P.ib, P.bpk, rows, cl, p, nullptr, false, bxs, unused);
+#pragma unroll
+            for (int q = 0; q < kRows; ++q) {
+                const int i = rows[q] < 0 ? 0 : rows[q];
+                const bool ok = rows[q] >= 0;
+                V pi_ = cmk<V>(T(0), T(0)), ri = cmk<V>(T(0), T(0));
+                if (ok) {
+                    pi_ = __ldg(p + (size_t)i * W + cl);
+                    ri = r[(size_t)i * W + cl];
+                }
+                const V bx = HASB ? bxs[q] : pi_;
+                T qc = T(0);
+                if (active && ok) {
+                    const V qv = csub(cmul(z, bx), ax[q]);
+                    ri = csub(ri, cmul(alpha, qv));
+                    r[(size_t)i * W + cl] = ri;
+                    qc = ca.x * pi_.x - ca.y * pi_.y;  // Re(c alpha p)
+                }
+                for (int o = 1; o < a.nbp; o <<= 1) qc += __shfl_xor_sync(mask, qc, o, W);
+                if (ok && e == 0 && m < P.m0) dQrow[(size_t)i * P.m0] += qc;
+                acc[0] = fma(ri.x, ri.x, fma(-ri.y, ri.y, acc[0]));
+                acc[1] = fma(T(2) * ri.x, ri.y, acc[1]);
+                acc[2] = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[2]));
+            }
         }
         block_partials<W, 3>(acc, sm, a.part + (size_t)item * W * kPartStride);
         if (arrive_group(a.grp_count + P.grp_off + g, P.nrb, &flag)) {
@@ -418,8 +513,10 @@ __global__ void __launch_bounds__(kThreads) filter_init(FilterArgs a, const doub
             double v = 0.0;
             if (live) v = R[P.q_off + (size_t)i * P.m0 + m];
             r[(size_t)i * W + cl] = cmk<V>((T)v, T(0));
-            if (init_q && e == 0 && m < P.m0)
+            if (init_q && e == 0 && m < P.m0) {
                 a.Q[P.q_off + (size_t)i * P.m0 + m] = (rii && live) ? rq * X[P.q_off + (size_t)i * P.m0 + m] : 0.0;
+                ((T*)a.dQ)[P.q_off + (size_t)i * P.m0 + m] = T(0);
+            }
         }
     }
 }
@@ -449,13 +546,55 @@ __global__ void __launch_bounds__(kThreads) shifted_spmm(FilterArgs a)
         for (int rl = rowslot; rl < a.RB; rl += RPP) {
             const int i = row0 + rl;
             if (i >= P.n) break;
-            const V ax = row_gather<T, W, false>(P.ia, P.ja, (const T*)P.av, i, mask, cl, x, nullptr, z, false);
-            V bx;
+            V ax, unused, bx;
+            row_gather<T, W, false>(P.ia, P.apk, i, cl, x, nullptr, false, ax, unused);
             if (P.ib == nullptr) bx = __ldg(x + (size_t)i * W + cl);
-            else bx = row_gather<T, W, false>(P.ib, P.jb, (const T*)P.bv, i, mask, cl, x, nullptr, z, false);
+            else row_gather<T, W, false>(P.ib, P.bpk, i, cl, x, nullptr, false, bx, unused);
             y[(size_t)i * W + cl] = csub(cmul(z, bx), ax);
         }
     }
+}
+
+// Q += dQ after all node batches of a pass (dQ: FP32 in mixed precision).
+template <typename T>
+__global__ void fold_dq(long long total, const T* dQ, double* Q)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+        Q[i] += (double)dQ[i];
+}
+
+// Packed (column, value) CSR entries for the uniform-load gathers.
+__global__ void pack_csr(long long nnz, const int* ja, const double* av, int fp64, void* out)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nnz; t += (long long)gridDim.x * blockDim.x) {
+        if (fp64) {
+            const double v = av[t];
+            ((int4*)out)[t] = make_int4(ja[t], 0, __double2loint(v), __double2hiint(v));
+        } else {
+            ((int2*)out)[t] = make_int2(ja[t], __float_as_int((float)av[t]));
+        }
+    }
+}
+
+cudaError_t launch_fold_dq(long long total, const void* dQ, bool fp64, double* Q, cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    long long blocks = (total + 255) / 256;
+    if (blocks > (long long)num_sms() * 8) blocks = (long long)num_sms() * 8;
+    if (fp64) fold_dq<double><<<(int)blocks, 256, 0, s>>>(total, (const double*)dQ, Q);
+    else fold_dq<float><<<(int)blocks, 256, 0, s>>>(total, (const float*)dQ, Q);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_csr(long long nnz, const int* ja, const double* av, bool fp64, void* out, cudaStream_t s)
+{
+    if (nnz <= 0) return cudaSuccess;
+    long long blocks = (nnz + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    pack_csr<<<(int)blocks, 256, 0, s>>>(nnz, ja, av, fp64 ? 1 : 0, out);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 __global__ void cast_values(const double* src, float* dst, long long n)
@@ -480,14 +619,41 @@ __global__ void cast_values(const double* src, float* dst, long long n)
         return cudaGetLastError();                                                         \
     } while (0)
 
+#define FEAST_DISPATCH_B(KERNEL, ...)                                                      \
+    do {                                                                                   \
+        if (a.hasB) {                                                                      \
+            if (fp64) {                                                                    \
+                if (a.W == 16) KERNEL<double, 16, true><<<grid, kThreads, 0, s>>>(__VA_ARGS__);      \
+                else if (a.W == 32) KERNEL<double, 32, true><<<grid, kThreads, 0, s>>>(__VA_ARGS__); \
+                else return cudaErrorInvalidValue;                                         \
+            } else {                                                                       \
+                if (a.W == 16) KERNEL<float, 16, true><<<grid, kThreads, 0, s>>>(__VA_ARGS__);       \
+                else if (a.W == 32) KERNEL<float, 32, true><<<grid, kThreads, 0, s>>>(__VA_ARGS__);  \
+                else return cudaErrorInvalidValue;                                         \
+            }                                                                              \
+        } else {                                                                           \
+            if (fp64) {                                                                    \
+                if (a.W == 16) KERNEL<double, 16, false><<<grid, kThreads, 0, s>>>(__VA_ARGS__);      \
+                else if (a.W == 32) KERNEL<double, 32, false><<<grid, kThreads, 0, s>>>(__VA_ARGS__); \
+                else return cudaErrorInvalidValue;                                         \
+            } else {                                                                       \
+                if (a.W == 16) KERNEL<float, 16, false><<<grid, kThreads, 0, s>>>(__VA_ARGS__);       \
+                else if (a.W == 32) KERNEL<float, 32, false><<<grid, kThreads, 0, s>>>(__VA_ARGS__);  \
+                else return cudaErrorInvalidValue;                                         \
+            }                                                                              \
+        }                                                                                  \
+        count_launches(1);                                                                 \
+        return cudaGetLastError();                                                         \
+    } while (0)
+
 cudaError_t launch_cocg_step_a(const FilterArgs& a, bool fp64, int k, int grid, cudaStream_t s)
 {
-    FEAST_DISPATCH(cocg_step_a, a, k);
+    FEAST_DISPATCH_B(cocg_step_a, a, k);
 }
 
 cudaError_t launch_cocg_step_b(const FilterArgs& a, bool fp64, int k, int grid, cudaStream_t s)
 {
-    FEAST_DISPATCH(cocg_step_b, a, k);
+    FEAST_DISPATCH_B(cocg_step_b, a, k);
 }
 
 cudaError_t launch_filter_init(const FilterArgs& a, bool fp64, const double* R, const double* X, int rii,
@@ -513,10 +679,10 @@ int filter_grid(bool fp64, int W)
 {
     int occ = 0;
     cudaError_t e;
-    if (fp64) e = W == 16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cocg_step_b<double, 16>, kThreads, 0)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cocg_step_b<double, 32>, kThreads, 0);
-    else e = W == 16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cocg_step_b<float, 16>, kThreads, 0)
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cocg_step_b<float, 32>, kThreads, 0);
+    if (fp64) e = W == 16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cocg_step_b<double, 16, false>, kThreads, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cocg_step_b<double, 32, false>, kThreads, 0);
+    else e = W == 16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cocg_step_b<float, 16, false>, kThreads, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cocg_step_b<float, 32, false>, kThreads, 0);
     if (e != cudaSuccess || occ < 1) occ = 1;
     return num_sms() * occ;
 }

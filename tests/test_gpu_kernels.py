@@ -81,10 +81,10 @@ def test_shifted_spmm(pkg, fp64, gen, nb, m):
     rdt = torch.float64 if fp64 else torch.float32
     Pd = torch.as_tensor(T).to(device="cuda", dtype=cdt).contiguous()
     Vd = torch.zeros_like(Pd)
-    ia, ja, av = dcsr(A, rdt)
+    ia, ja, av = dcsr(A)
     ib = jb = bv = None
     if B is not None:
-        ib, jb, bv = dcsr(B, rdt)
+        ib, jb, bv = dcsr(B)
     pkg.feast_shifted_spmm_dev(n, ia, ja, av, ib, jb, bv, z, m, fp64, Pd, Vd)
     got = from_tiles(Vd.cpu().numpy().astype(np.complex128), nb, m, lay)
     if not fp64:  # reference on the same rounded inputs
