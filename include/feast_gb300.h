@@ -175,6 +175,27 @@ int feast_filter_dev(int n, int nnz_a, const int* ia, const int* ja, const doubl
  * result is symmetrised ((C + C^T)/2) as the Rayleigh-Ritz matrices are. */
 int feast_gram_dev(int n, int m, const double* X, const double* Y, double* C, void* stream);
 
+/* Allocation-free variant of feast_gram_dev (the paper has no counterpart:
+ * it is a library convenience).  Same arguments and result, but the split-K
+ * partial sums live in a fixed 16 MiB array that the library keeps in the
+ * device memory of every GPU that loads it, so the call needs no cudaMalloc,
+ * no cudaMallocAsync and no caller workspace.  It serves callers that cannot
+ * allocate device memory at the point of the call, e.g. code working inside
+ * a memory pool owned by another runtime, code that must avoid the implicit
+ * synchronisation of cudaMalloc/cudaFree, or an interface with no room for a
+ * workspace argument.
+ *   - Limit: m*m <= 2097152 (m <= 1448); larger m returns -102 with a message
+ *     in feast_last_error().  n > 0, else -101.  CUDA failures return -4.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before capturing a stream into a CUDA graph.
+ *   - All calls share the one array and it keeps the last call's partial sums;
+ *     each call overwrites every partial it reads, so nothing needs clearing.
+ *     Calls whose execution overlaps on the GPU (different streams, or host
+ *     threads not ordered by the caller) race on the array: serialise them.
+ *   - Enqueues on stream and returns after C is written. */
+int feast_gram_noalloc_dev(int n, int m, const double* X, const double* Y, double* C, void* stream);
+
 /* C = A V: A device row-major n x m, V device row-major m x k, C n x k, FP64. */
 int feast_gemm_dev(int n, int m, int k, const double* A, const double* V, double* C, void* stream);
 

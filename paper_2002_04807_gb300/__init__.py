@@ -18,6 +18,7 @@ from ._lib import (  # noqa: F401
     feast_filter_layout,
     feast_gemm_dev,
     feast_gram_dev,
+    feast_gram_noalloc_dev,
     feast_init,
     feast_last_error,
     feast_last_profile,

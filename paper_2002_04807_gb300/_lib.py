@@ -37,6 +37,7 @@ _SIGS = {
     "feast_residual_dev": (_i, [_i, _p, _p, _p, _p, _p, _p, _i, _p, _p, _d, _p, _p, _p]),
     "feast_eig_grad_dev": (_i, [_i, _p, _p, _i, _p, _p, _p, _p]),
     "feast_last_profile": (_i, [_p]),
+    "feast_gram_noalloc_dev": (_i, [_i, _i, _p, _p, _p, _p]),
 }
 
 
@@ -243,6 +244,13 @@ def feast_filter_dev(n, ia, ja, a, ib, jb, b, m, R, X, lam, rii, fpm, emin, emax
 
 def feast_gram_dev(n, m, X, Y, Cm, stream=None):
     _check(library().feast_gram_dev(n, m, _ptr(X), _ptr(Y), _ptr(Cm), _stream(stream)), "feast_gram_dev")
+
+
+def feast_gram_noalloc_dev(n, m, X, Y, Cm, stream=None):
+    """C = X^T Y like feast_gram_dev, with the library's fixed device scratch
+    instead of any allocation (for callers that cannot allocate)."""
+    _check(library().feast_gram_noalloc_dev(n, m, _ptr(X), _ptr(Y), _ptr(Cm), _stream(stream)),
+           "feast_gram_noalloc_dev")
 
 
 def feast_gemm_dev(n, m, k, A, V, Cm, stream=None):

@@ -31,6 +31,14 @@ static thread_local std::string g_err;
 
 extern "C" const char* feast_last_error(void) { return g_err.c_str(); }
 
+namespace feast {
+const char* set_last_error(const char* msg)
+{
+    g_err = msg;
+    return g_err.c_str();
+}
+}  // namespace feast
+
 static int cuda_fail(cudaError_t e, const char* where)
 {
     g_err = std::string(where) + ": " + cudaGetErrorString(e);
