@@ -294,9 +294,10 @@ def run_gpu(args):
     live = (p.m0 * min(nbp, p.ne)) / (G * W)  # padded lanes are not algorithmic work
     mat = p.A.nnz * (4 + (4 if sc == 8 else 8)) + (p.n + 1) * 4
     tile = n * W * sc * live
-    bytes_a = pr["group_iterations"] * 3 * tile + pr["cocg_a_launches"] * mat
+    # step A: r (gathered) + p, q read + p, q written; step B: r, p, q read + r written + accumulator
+    bytes_a = pr["group_iterations"] * 5 * tile + pr["cocg_a_launches"] * mat
     qb = 4 if sc == 8 else 8  # quadrature accumulator: FP32 in mixed precision
-    bytes_b = pr["group_iterations"] * (3 * tile + n * mt * 2 * qb * live) + pr["cocg_b_launches"] * mat
+    bytes_b = pr["group_iterations"] * (4 * tile + n * mt * 2 * qb * live)
     gbs_a = bytes_a / (pr["cocg_a_ms"] / 1e3) / 1e9
     gbs_b = bytes_b / (pr["cocg_b_ms"] / 1e3) / 1e9
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")

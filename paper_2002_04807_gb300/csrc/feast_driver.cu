@@ -170,10 +170,12 @@ namespace {
 
 struct Plan {
     int n = 0, m0 = 0, ne = 0, nbp = 0, nbatch = 0, W = 0, mt = 0, G = 0, RB = 0, nrb = 0;
-    long long nitems = 0;
+    int RBb = 0, nrb_b = 0;
+    long long nitems = 0, nitems_b = 0;
     bool fp64 = false, hasB = false;
     int nnzA = 0, nnzB = 0;
     int ksplit = 1;
+    int nslot = 1;  // upper bound of the COCG grid (partial-sum slots per group)
     size_t gpart = 0, rpart = 0;
 };
 
@@ -187,7 +189,10 @@ struct Bufs {
     int* groups_left = nullptr;
     unsigned long long* work = nullptr;
     FiltProb* probs = nullptr;
-    void *apk = nullptr, *bpk = nullptr;  // packed (column, value) CSR entries
+    void *apk = nullptr, *bpk = nullptr;  // packed (column, value) CSR entries, rows padded to chunks
+    int *app = nullptr, *bpp = nullptr;   // padded row pointers
+    void* bd = nullptr;                   // diagonal of B (filter precision) when B is diagonal
+    int bmode = 0;
     void* dQ = nullptr;                   // per-pass quadrature accumulator (filter precision)
     double* zw = nullptr;
     double *Y = nullptr, *Q = nullptr, *X = nullptr, *T = nullptr, *T2 = nullptr;
@@ -219,9 +224,13 @@ Plan make_plan(int n, int nnzA, int nnzB, int m0, const int* fpm, bool filter_on
         nb = (nb + 1) / 2;
     }
     P.nbatch = (P.ne + P.nbp - 1) / P.nbp;
-    P.RB = fpm[50] > 0 ? fpm[50] : 256;
+    P.RB = fpm[50] > 0 ? std::min(fpm[50], 512) : 128;
+    P.nslot = num_sms() * 8;
     P.nrb = (n + P.RB - 1) / P.RB;
     P.nitems = (long long)P.G * P.nrb;
+    P.RBb = 512;
+    P.nrb_b = (n + P.RBb - 1) / P.RBb;
+    P.nitems_b = (long long)P.G * P.nrb_b;
     if (!filter_only) {
         P.gpart = gram_partial_doubles(n, m0, &P.ksplit, num_sms());
         P.rpart = residual_partial_doubles(n, m0);
@@ -251,7 +260,7 @@ size_t carve(const Plan& P, void* base, Bufs& B, bool filter_only = false)
     B.p0 = c.take<char>(vec);
     B.p1 = c.take<char>(vec);
     B.cs = c.take<ColState>((size_t)P.G * P.W);
-    B.part = c.take<double>((size_t)P.nitems * P.W * 4);
+    B.part = c.take<double>((size_t)P.G * P.nslot * P.W * 4);
     B.grp_count = c.take<unsigned>(P.G);
     B.grp_done = c.take<int>(P.G);
     B.iter_max = c.take<int>(P.nbatch);
@@ -259,9 +268,14 @@ size_t carve(const Plan& P, void* base, Bufs& B, bool filter_only = false)
     B.work = c.take<unsigned long long>(1);
     B.probs = c.take<FiltProb>(1);
     const size_t pk = P.fp64 ? 16 : 8;
-    B.apk = c.take<char>((size_t)P.nnzA * pk);
-    if (P.hasB) B.bpk = c.take<char>((size_t)P.nnzB * pk);
-    B.dQ = c.take<char>((size_t)P.n * P.m0 * (P.fp64 ? 8 : 4));
+    B.app = c.take<int>((size_t)P.n + 1);
+    B.apk = c.take<char>(((size_t)P.nnzA + 7 * (size_t)P.n) * pk);
+    if (P.hasB) {
+        B.bpp = c.take<int>((size_t)P.n + 1);
+        B.bpk = c.take<char>(((size_t)P.nnzB + 7 * (size_t)P.n) * pk);
+        B.bd = c.take<double>((size_t)P.n);
+    }
+    B.dQ = c.take<char>((size_t)P.G * P.mt * P.n * (P.fp64 ? 8 : 4));
     B.zw = c.take<double>(4 * (size_t)P.ne);
     if (filter_only) return c.off + 256;
     const size_t blk = (size_t)P.n * P.m0;
@@ -395,11 +409,14 @@ int filter_pass(const Plan& P, Bufs& B, int rii, const double* R, const double* 
     fa.probs = B.probs;
     fa.nprob = 1;
     fa.nitems = P.nitems;
+    fa.nitems_b = P.nitems_b;
+    fa.RBb = P.RBb;
     fa.W = P.W;
     fa.nbp = P.nbp;
     fa.mt = P.mt;
     fa.RB = P.RB;
     fa.hasB = P.hasB ? 1 : 0;
+    fa.bmode = B.bmode;
     fa.r = B.r;
     fa.p0 = B.p0;
     fa.p1 = B.p1;
@@ -412,28 +429,34 @@ int filter_pass(const Plan& P, Bufs& B, int rii, const double* R, const double* 
     fa.tol2 = tol * tol;
     fa.groups_left = B.groups_left;
     fa.work = B.work;
-    const int grid = (int)std::min<long long>(filter_grid(P.fp64, P.W), P.nitems);
+    int grid_a = 1, grid_b = 1;
+    filter_grids(P.fp64, P.W, &grid_a, &grid_b);
+    grid_a = (int)std::min<long long>(std::min(grid_a, P.nslot), P.nitems);
+    grid_b = (int)std::min<long long>(std::min(grid_b, P.nslot), P.nitems_b);
+    const int grid = std::max(grid_a, grid_b);  // filter_init
+    fa.nslot = grid;
     CK(cudaMemsetAsync(B.iter_max, 0, sizeof(int) * P.nbatch, s));
     int left = P.G;
     for (int b = 0; b < P.nbatch; ++b) {
         fa.iter_max = B.iter_max + b;
         CK(cudaMemsetAsync(B.grp_count, 0, sizeof(unsigned) * P.G, s));
         CK(cudaMemsetAsync(B.grp_done, 0, sizeof(int) * P.G, s));
+        CK(cudaMemsetAsync(B.part, 0, sizeof(double) * (size_t)P.G * grid * P.W * 4, s));
         CK(cudaMemcpyAsync(B.groups_left, &left, sizeof(int), cudaMemcpyHostToDevice, s));
         CK(launch_colstate_init(fa, b * P.nbp, rii, s));
         CK(launch_filter_init(fa, P.fp64, R, X, rii, b == 0, grid, s));
         for (int k = 0; k < maxit; ++k) {
             if (g_prof.on) {
                 const size_t e0 = g_prof.mark(s);
-                CK(launch_cocg_step_a(fa, P.fp64, k, grid, s));
+                CK(launch_cocg_step_a(fa, P.fp64, k, grid_a, s));
                 const size_t e1 = g_prof.mark(s);
-                CK(launch_cocg_step_b(fa, P.fp64, k, grid, s));
+                CK(launch_cocg_step_b(fa, P.fp64, k, grid_b, s));
                 const size_t e2 = g_prof.mark(s);
                 g_prof.a.push_back({e0, e1});
                 g_prof.b.push_back({e1, e2});
             } else {
-                CK(launch_cocg_step_a(fa, P.fp64, k, grid, s));
-                CK(launch_cocg_step_b(fa, P.fp64, k, grid, s));
+                CK(launch_cocg_step_a(fa, P.fp64, k, grid_a, s));
+                CK(launch_cocg_step_b(fa, P.fp64, k, grid_b, s));
             }
             // every few steps: stop launching once no group iterates any more
             if ((k & 7) == 7 && k + 1 < maxit) {
@@ -444,7 +467,41 @@ int filter_pass(const Plan& P, Bufs& B, int rii, const double* R, const double* 
             }
         }
     }
-    CK(launch_fold_dq((long long)P.n * P.m0, B.dQ, P.fp64, B.Q, s));
+    CK(launch_fold_dq(fa, (long long)P.n * P.m0, P.fp64, s));
+    return 0;
+}
+
+// Pack a device CSR for the filter kernels: rows padded to chunks of 8
+// entries (padded row pointers computed on the host from a copy of ia), or,
+// when allow_diag and the matrix is diagonal, just its diagonal values.
+// *mode: 1 diagonal, 2 packed.
+int pack_matrix(const Csr& M, bool fp64, bool allow_diag, int* d_pp, void* d_pk, void* d_bd, int* mode, cudaStream_t s)
+{
+    const int n = M.n;
+    std::vector<int> ia(n + 1);
+    CK(cudaMemcpyAsync(ia.data(), M.ia, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (allow_diag && M.nnz == n && ia[n] - ia[0] == n) {
+        std::vector<int> ja(n);
+        CK(cudaMemcpyAsync(ja.data(), M.ja, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        bool diag = true;
+        for (int i = 0; i < n && diag; ++i) diag = (ia[i + 1] - ia[i] == 1) && ja[ia[i] - ia[0]] == i;
+        if (diag) {
+            CK(launch_cast_diag(n, M.ia, M.v, fp64, d_bd, s));
+            *mode = 1;
+            return 0;
+        }
+    }
+    std::vector<int> pp(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        const int len = ia[i + 1] - ia[i];
+        pp[i + 1] = pp[i] + (len + 7) / 8 * 8;
+    }
+    CK(cudaMemcpyAsync(d_pp, pp.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
+    CK(launch_pack_csr(n, M.ia, M.ja, M.v, d_pp, fp64, d_pk, s));
+    CK(cudaStreamSynchronize(s));  // pp is a host temporary
+    *mode = 2;
     return 0;
 }
 
@@ -452,8 +509,14 @@ int setup_filter(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, const std:
                  const double* lam, const int* mk, cudaStream_t s)
 {
     CK(cudaMemcpyAsync(B.zw, zw.data(), sizeof(double) * zw.size(), cudaMemcpyHostToDevice, s));
-    CK(launch_pack_csr(A.nnz, A.ja, A.v, P.fp64, B.apk, s));
-    if (P.hasB) CK(launch_pack_csr(Bm.nnz, Bm.ja, Bm.v, P.fp64, B.bpk, s));
+    int amode = 0;
+    int st = pack_matrix(A, P.fp64, false, B.app, B.apk, nullptr, &amode, s);
+    if (st) return st;
+    B.bmode = 0;
+    if (P.hasB) {
+        st = pack_matrix(Bm, P.fp64, true, B.bpp, B.bpk, B.bd, &B.bmode, s);
+        if (st) return st;
+    }
     FiltProb fp;
     memset(&fp, 0, sizeof(fp));
     fp.n = P.n;
@@ -461,18 +524,24 @@ int setup_filter(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, const std:
     fp.G = P.G;
     fp.nrb = P.nrb;
     fp.item0 = 0;
+    fp.nrb_b = P.nrb_b;
+    fp.item0_b = 0;
     fp.vec_off = 0;
     fp.col_off = 0;
     fp.grp_off = 0;
     fp.q_off = 0;
+    fp.dq_off = 0;
     fp.ia = A.ia;
     fp.ja = A.ja;
     fp.av = A.v;
     fp.ib = P.hasB ? Bm.ia : nullptr;
     fp.jb = P.hasB ? Bm.ja : nullptr;
     fp.bv = P.hasB ? Bm.v : nullptr;
+    fp.app = B.app;
     fp.apk = B.apk;
-    fp.bpk = P.hasB ? B.bpk : nullptr;
+    fp.bpp = B.bmode == 2 ? B.bpp : nullptr;
+    fp.bpk = B.bmode == 2 ? B.bpk : nullptr;
+    fp.bd = B.bmode == 1 ? B.bd : nullptr;
     fp.zw = B.zw;
     fp.lam = lam;
     fp.mk = mk;
@@ -866,15 +935,22 @@ extern "C" int feast_shifted_spmm_dev(int n, int nnz_a, const int* ia, const int
         if (e < nb) cs[c].z = make_double2(z[2 * e], z[2 * e + 1]);
     }
     AsyncMem am(s);
-    void *d_cs = nullptr, *d_fp = nullptr, *apk = nullptr, *bpk = nullptr;
+    void *d_cs = nullptr, *d_fp = nullptr, *apk = nullptr, *bpk = nullptr, *app = nullptr, *bpp = nullptr,
+         *bd = nullptr;
     const size_t pk = fp64 ? 16 : 8;
     CK(am.alloc(&d_cs, sizeof(ColState) * cs.size()));
     CK(am.alloc(&d_fp, sizeof(FiltProb)));
-    CK(am.alloc(&apk, pk * (size_t)std::max(1, nnz_a)));
-    CK(launch_pack_csr(nnz_a, ja, a, fp64 != 0, apk, s));
+    CK(am.alloc(&app, sizeof(int) * ((size_t)n + 1)));
+    CK(am.alloc(&apk, pk * ((size_t)nnz_a + 7 * (size_t)n)));
+    int amode = 0, bmode = 0;
+    int st = pack_matrix(Csr{n, nnz_a, ia, ja, a}, fp64 != 0, false, (int*)app, apk, nullptr, &amode, s);
+    if (st) return st;
     if (b) {
-        CK(am.alloc(&bpk, pk * (size_t)std::max(1, nnz_b)));
-        CK(launch_pack_csr(nnz_b, jb, b, fp64 != 0, bpk, s));
+        CK(am.alloc(&bpp, sizeof(int) * ((size_t)n + 1)));
+        CK(am.alloc(&bpk, pk * ((size_t)nnz_b + 7 * (size_t)n)));
+        CK(am.alloc(&bd, sizeof(double) * (size_t)n));
+        st = pack_matrix(Csr{n, nnz_b, ib, jb, b}, fp64 != 0, true, (int*)bpp, bpk, bd, &bmode, s);
+        if (st) return st;
     }
     FiltProb fp;
     memset(&fp, 0, sizeof(fp));
@@ -888,8 +964,11 @@ extern "C" int feast_shifted_spmm_dev(int n, int nnz_a, const int* ia, const int
     fp.ib = b ? ib : nullptr;
     fp.jb = b ? jb : nullptr;
     fp.bv = b;
+    fp.app = (const int*)app;
     fp.apk = apk;
-    fp.bpk = b ? bpk : nullptr;
+    fp.bpp = bmode == 2 ? (const int*)bpp : nullptr;
+    fp.bpk = bmode == 2 ? bpk : nullptr;
+    fp.bd = bmode == 1 ? bd : nullptr;
     CK(cudaMemcpyAsync(d_cs, cs.data(), sizeof(ColState) * cs.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(d_fp, &fp, sizeof(fp), cudaMemcpyHostToDevice, s));
     FilterArgs fa;
@@ -902,6 +981,7 @@ extern "C" int feast_shifted_spmm_dev(int n, int nnz_a, const int* ia, const int
     fa.mt = mt;
     fa.RB = RB;
     fa.hasB = b ? 1 : 0;
+    fa.bmode = bmode;
     fa.p0 = const_cast<void*>(P);
     fa.p1 = V;
     fa.cs = (ColState*)d_cs;

@@ -31,18 +31,24 @@ struct FiltProb {
     int G;              // column groups = ceil(m0 / Mt)
     int nrb;            // row blocks per group = ceil(n / RB)
     long long item0;    // first work item (items of one problem are contiguous: g-major, rb fastest)
+    int nrb_b;          // row blocks per group of the streaming step = ceil(n / RBb)
+    long long item0_b;  // first work item of the streaming step
     long long vec_off;  // offset of this problem's block vectors, in complex elements (G*n*W)
     int col_off;        // offset of this problem's columns in the per-column arrays (G*W)
     int grp_off;        // offset of this problem's groups in the per-group arrays (G)
     long long q_off;    // offset of this problem's FP64 n x m0 blocks (row-major)
+    long long dq_off;   // offset of this problem's quadrature accumulator tiles ([G][n][mt])
     const int* ia;      // A row pointers [n+1]
     const int* ja;      // A column indices
     const void* av;     // A values (float or double, the filter's real type)
     const int* ib;      // B row pointers, or nullptr for B = I
     const int* jb;
     const void* bv;
+    const int* app;     // A row pointers into apk, rows padded to chunks of 8 entries
     const void* apk;    // A as packed (column, value) entries: int2 (float) or int4 (double)
-    const void* bpk;    // B packed, or nullptr
+    const int* bpp;     // B padded row pointers (general B), or nullptr
+    const void* bpk;    // B packed entries (general B), or nullptr
+    const void* bd;     // B diagonal values in the filter's real type (diagonal B), or nullptr
     const double* zw;   // Ne nodes and weights, [Ne][4] = (Re z, Im z, Re w, Im w)
     const double* lam;  // Ritz values of the previous Rayleigh-Ritz step [m0]
     const int* mk;      // live subspace columns (device), or nullptr for m0
@@ -72,17 +78,21 @@ struct FilterArgs {
     int W;          // lanes (complex columns) per row of a group tile
     int nbp;        // node lanes per subspace column (power of two)
     int mt;         // subspace columns per group = W / nbp
-    int RB;         // rows per work item
+    int RB;         // rows per work item of the gathering step
+    int RBb;        // rows per work item of the streaming step
+    long long nitems_b;  // work items of the streaming step
     int hasB;       // 1 when the problems have a B matrix (all or none)
+    int bmode;      // 0: B = I, 1: B diagonal, 2: general B (same for all problems)
+    int nslot;      // partial-sum slots per group = grid size of the COCG launches
     void* r;        // residual block vectors (complex T)
     void* p0;       // search directions, ping
     void* p1;       // search directions, pong
     ColState* cs;   // per-column state
-    double* part;   // per-item partial sums [nitems][W][4]
+    double* part;   // partial sums, [group][nslot][W][4], zero between launches
     unsigned* grp_count;  // per-group finished-item counters
     int* grp_done;  // per-group "no active column" flags
     double* Q;      // FP64 filter accumulator (row-major n x m0 per problem)
-    void* dQ;       // per-pass accumulator of the quadrature sum, filter precision, same layout
+    void* dQ;       // per-pass accumulator of the quadrature sum, filter precision, [group][row][mt] tiles
     double tol2;    // squared relative COCG tolerance
     int* iter_max;  // per-problem max iteration reached
     int* groups_left;  // per-problem number of groups still iterating
@@ -97,10 +107,13 @@ cudaError_t launch_filter_init(const FilterArgs& a, bool fp64, const double* R, 
 cudaError_t launch_colstate_init(const FilterArgs& a, int node0, int rii, cudaStream_t s);
 cudaError_t launch_shifted_spmm(const FilterArgs& a, bool fp64, int grid, cudaStream_t s);
 cudaError_t launch_cast_values(const double* src, float* dst, long long n, cudaStream_t s);
-cudaError_t launch_fold_dq(long long total, const void* dQ, bool fp64, double* Q, cudaStream_t s);
-cudaError_t launch_pack_csr(long long nnz, const int* ja, const double* av, bool fp64, void* out, cudaStream_t s);
+cudaError_t launch_fold_dq(const FilterArgs& a, long long max_total, bool fp64, cudaStream_t s);
+cudaError_t launch_pack_csr(int n, const int* ia, const int* ja, const double* av, const int* pp, bool fp64, void* out,
+                            cudaStream_t s);
+cudaError_t launch_cast_diag(int n, const int* ia, const double* av, bool fp64, void* out, cudaStream_t s);
 // persistent grid size of the COCG kernels: SMs x resident CTAs per SM
 int filter_grid(bool fp64, int W);
+void filter_grids(bool fp64, int W, int* grid_a, int* grid_b);
 
 // ---------------------------------------------------------------- Rayleigh-Ritz (k_rr.cu)
 // Y = A X (and optionally Z = B X) for row-major n x m FP64 blocks.

@@ -22,30 +22,43 @@
 // that concurrently running CTAs gather from stay inside one tile (L2 reuse).
 //
 // One COCG iteration is two launches:
-//   A: p_k = r_k + beta p_{k-1} (computed on the fly for every gathered row),
-//      q = (zB - A) p_k, write p_k, partial sums of p_k^T q;
-//      the last item of a group reduces them and sets alpha = rho / p^T q.
-//   B: recompute q from p_k, r -= alpha q, Q += Re(c alpha p_k),
-//      partial sums of r^T r and |r|^2; the last item sets beta and the
-//      convergence state of each column.
-// Recomputing q instead of storing it saves a full write+read of the block
-// vector; the matrix itself is a few MB and stays in L2.
-// Reductions are deterministic: fixed per-thread order, fixed block order, and
-// the partials of a group are summed in item order by whichever CTA finishes
-// the group last.
+//   A: s = (zB - A) r_k (the only gather), p_k = r_k + beta p_{k-1} and
+//      q_k = s + beta q_{k-1} = (zB - A) p_k in place, partial sums of
+//      p_k^T q_k; the last item of a group sets alpha = rho / p^T q.
+//   B: streaming only: r -= alpha q, Q += Re(c alpha p_k), partial sums of
+//      r^T r and |r|^2; the last item sets beta and each column's state.
+// Carrying q by its recurrence means one gathered vector per step: on GB300
+// a gather of a wide 3D stencil moves data at roughly half the rate of a
+// plain stream (far neighbours come through L2), so trading a second gather
+// for two extra streams is faster even though it moves more bytes.
+// Rows of a CSR matrix are stored as packed (column, value) entries padded to
+// chunks of 8 with zero-weight entries on the diagonal, so a row is gathered
+// with unpredicated, fully unrolled loads: 8 (or 16) independent row-segment
+// loads in flight per thread.  Before working on an item, a CTA asks the TMA
+// engine to prefetch into L2 the tile rows of the item it will take next
+// (cp.async.bulk.prefetch), so the gathers of the current item hit L2 instead
+// of waiting on DRAM row by row.
+// Reductions are deterministic: fixed per-thread order, fixed block order;
+// each CTA accumulates its items of a group into its own slot, and whichever
+// CTA finishes the group's last item sums the slots in CTA order.
 #include "feast_internal.cuh"
 
 namespace feast {
 
 static constexpr int kThreads = 256;
 static constexpr int kPartStride = 4;
-#ifndef FEAST_ROWS
-#define FEAST_ROWS 4
+static constexpr int kChunk = 8;  // padded CSR chunk (entries)
+static constexpr int kStageEntries = 2048;  // packed entries of one item staged in shared memory
+static constexpr int kMaxRB = 512;  // rows per work item, at most
+#ifndef FEAST_PREFETCH
+#define FEAST_PREFETCH 1
 #endif
 #ifndef FEAST_MINB
-#define FEAST_MINB 3
+#define FEAST_MINB 4
 #endif
-static constexpr int kRows = FEAST_ROWS;  // rows per thread gathered in lockstep
+#ifndef FEAST_MINB_B
+#define FEAST_MINB_B 6
+#endif
 
 __device__ __forceinline__ int find_prob(const FiltProb* probs, int nprob, long long item)
 {
@@ -64,108 +77,145 @@ __device__ __forceinline__ unsigned seg_mask(int sub)
     return W == 32 ? 0xffffffffu : (((1u << W) - 1u) << (sub * W));
 }
 
-// One CSR row of packed (column, value) entries, read with uniform loads (all
-// lanes of a row segment read the same entry, served as one broadcast) and
-// gathered against the lane's column of x (and of p when UPD):
-//   ax = sum_k a_k x[j_k],  ap = sum_k a_k p[j_k].
-// U entries are fetched before any is used, so each warp keeps U (or 2U)
-// independent row-segment loads in flight.
-template <typename T> __device__ __forceinline__ void load_pk(const void* pk, int t, int& j, T& a);
-template <> __device__ __forceinline__ void load_pk<float>(const void* pk, int t, int& j, float& a)
+// TMA bulk prefetch of a contiguous range into L2 (16-byte aligned, size a
+// multiple of 16 bytes).
+__device__ __forceinline__ void l2_prefetch(const void* ptr, unsigned bytes)
 {
-    const int2 v = __ldg((const int2*)pk + t);
-    j = v.x;
-    a = __int_as_float(v.y);
-}
-template <> __device__ __forceinline__ void load_pk<double>(const void* pk, int t, int& j, double& a)
-{
-    const int4 v = __ldg((const int4*)pk + t);
-    j = v.x;
-    a = __hiloint2double(v.w, v.z);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ptr), "r"(bytes) : "memory");
 }
 
-template <typename T, int W, bool UPD>
-__device__ __forceinline__ void row_gather(const int* __restrict__ ia, const void* __restrict__ pk, int i, int cl,
-                                           const c2_t<T>* __restrict__ x, const c2_t<T>* __restrict__ p,
-                                           bool use_p, c2_t<T>& ax, c2_t<T>& ap)
+// ---------------------------------------------------------------- padded CSR chunks
+// Entries of a packed row chunk: float entries are 8 bytes (two per int4),
+// double entries 16 bytes (one per int4).  SH: the entries sit in shared
+// memory (plain loads) rather than global memory (read-only cache loads).
+template <typename T, bool SH> __device__ __forceinline__ void load_chunk(const int4* ent, int c, int (&j)[kChunk], T (&a)[kChunk]);
+template <> __device__ __forceinline__ void load_chunk<float, true>(const int4* ent, int c, int (&j)[kChunk], float (&a)[kChunk])
+{
+    const int4* q = ent + (c >> 1);
+#pragma unroll
+    for (int u = 0; u < kChunk / 2; ++u) {
+        const int4 v = q[u];
+        j[2 * u] = v.x;
+        a[2 * u] = __int_as_float(v.y);
+        j[2 * u + 1] = v.z;
+        a[2 * u + 1] = __int_as_float(v.w);
+    }
+}
+template <> __device__ __forceinline__ void load_chunk<float, false>(const int4* ent, int c, int (&j)[kChunk], float (&a)[kChunk])
+{
+    const int4* q = ent + (c >> 1);
+#pragma unroll
+    for (int u = 0; u < kChunk / 2; ++u) {
+        const int4 v = __ldg(q + u);
+        j[2 * u] = v.x;
+        a[2 * u] = __int_as_float(v.y);
+        j[2 * u + 1] = v.z;
+        a[2 * u + 1] = __int_as_float(v.w);
+    }
+}
+template <> __device__ __forceinline__ void load_chunk<double, true>(const int4* ent, int c, int (&j)[kChunk], double (&a)[kChunk])
+{
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) {
+        const int4 v = ent[c + u];
+        j[u] = v.x;
+        a[u] = __hiloint2double(v.w, v.z);
+    }
+}
+template <> __device__ __forceinline__ void load_chunk<double, false>(const int4* ent, int c, int (&j)[kChunk], double (&a)[kChunk])
+{
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) {
+        const int4 v = __ldg(ent + c + u);
+        j[u] = v.x;
+        a[u] = __hiloint2double(v.w, v.z);
+    }
+}
+
+// ax = sum a_k x[j_k] (and with UPD ap = sum a_k p[j_k]) over the padded row
+// entries [c0, c1) of ent.  The row's own values x[i] (and p[i]) come out of
+// the same loads when the row has an entry in column i (its diagonal, or a
+// zero-weight padding entry); *own says whether they did.
+template <typename T, int W, bool UPD, bool SH>
+__device__ __forceinline__ void row_gather(const int4* __restrict__ ent, int c0, int c1, int i,
+                                           const c2_t<T>* __restrict__ xl, const c2_t<T>* __restrict__ pl,
+                                           bool use_p, c2_t<T>& ax, c2_t<T>& ap, c2_t<T>& xo, c2_t<T>& po,
+                                           bool& own)
 {
     using V = c2_t<T>;
-    constexpr int U = UPD ? 4 : 8;
     ax = cmk<V>(T(0), T(0));
     ap = cmk<V>(T(0), T(0));
-    const int s = __ldg(ia + i), e = __ldg(ia + i + 1);
-    for (int t0 = s; t0 < e; t0 += U) {
-        V xv[U], pv[U];
-        T av[U];
+    own = false;
+    for (int c = c0; c < c1; c += kChunk) {
+        int j[kChunk];
+        T av[kChunk];
+        load_chunk<T, SH>(ent, c, j, av);
+        V xv[kChunk], pv[kChunk];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int t = t0 + u;
-            int j = 0;
-            T aa = T(0);
-            if (t < e) load_pk<T>(pk, t, j, aa);
-            av[u] = aa;
-            xv[u] = (t < e) ? __ldg(x + (size_t)j * W + cl) : cmk<V>(T(0), T(0));
-            if (UPD) pv[u] = (t < e && use_p) ? __ldg(p + (size_t)j * W + cl) : cmk<V>(T(0), T(0));
+        for (int u = 0; u < kChunk; ++u) xv[u] = __ldg(xl + (size_t)j[u] * W);
+        if (UPD && use_p) {
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u) pv[u] = __ldg(pl + (size_t)j[u] * W);
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
+        for (int u = 0; u < kChunk; ++u) {
             ax.x = fma(av[u], xv[u].x, ax.x);
             ax.y = fma(av[u], xv[u].y, ax.y);
-            if (UPD) {
+            if (j[u] == i) {
+                xo = xv[u];
+                own = true;
+            }
+        }
+        if (UPD && use_p) {
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u) {
                 ap.x = fma(av[u], pv[u].x, ap.x);
                 ap.y = fma(av[u], pv[u].y, ap.y);
+                if (j[u] == i) po = pv[u];
             }
         }
     }
 }
 
-// R rows gathered in lockstep by one thread (rows of the same tile, R*RPP
-// apart): the t-th entries of all R rows are fetched together, so the loads
-// that miss L2 (the leading edge of a wide stencil) of R rows overlap.
-template <typename T, int W, bool UPD, int R>
-__device__ __forceinline__ void rows_gather(const int* __restrict__ ia, const void* __restrict__ pk, const int (&row)[R],
-                                            int cl, const c2_t<T>* __restrict__ x, const c2_t<T>* __restrict__ p,
-                                            bool use_p, c2_t<T> (&ax)[R], c2_t<T> (&ap)[R])
+// Row gather that reads the entries from global memory (rows of B, and the
+// standalone SpMM).
+template <typename T, int W>
+__device__ __forceinline__ c2_t<T> row_gather_global(const int* __restrict__ pp, const void* __restrict__ pk, int i,
+                                                     const c2_t<T>* __restrict__ xl)
 {
-    using V = c2_t<T>;
-    int s[R], e[R], len = 0;
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-        s[q] = row[q] >= 0 ? __ldg(ia + row[q]) : 0;
-        e[q] = row[q] >= 0 ? __ldg(ia + row[q] + 1) : 0;
-        len = max(len, e[q] - s[q]);
-        ax[q] = cmk<V>(T(0), T(0));
-        ap[q] = cmk<V>(T(0), T(0));
-    }
-    for (int t = 0; t < len; ++t) {
-        V xv[R], pv[R];
-        T av[R];
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const bool ok = s[q] + t < e[q];
-            int j = 0;
-            T aa = T(0);
-            if (ok) load_pk<T>(pk, s[q] + t, j, aa);
-            av[q] = aa;
-            xv[q] = ok ? __ldg(x + (size_t)j * W + cl) : cmk<V>(T(0), T(0));
-            if (UPD) pv[q] = (ok && use_p) ? __ldg(p + (size_t)j * W + cl) : cmk<V>(T(0), T(0));
-        }
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            ax[q].x = fma(av[q], xv[q].x, ax[q].x);
-            ax[q].y = fma(av[q], xv[q].y, ax[q].y);
-            if (UPD) {
-                ap[q].x = fma(av[q], pv[q].x, ap[q].x);
-                ap[q].y = fma(av[q], pv[q].y, ap[q].y);
-            }
-        }
-    }
+    c2_t<T> ax, ap, xo, po;
+    bool own;
+    row_gather<T, W, false, false>((const int4*)pk, __ldg(pp + i), __ldg(pp + i + 1), i, xl, nullptr, false, ax, ap,
+                                   xo, po, own);
+    return ax;
 }
 
-// Block-wide reduction of NV per-thread doubles for each of the W lane
-// columns, written to part[item][cl][0..NV).  Fixed order => deterministic.
+// Stage the packed entries of rows [row0, row1) in shared memory (one
+// coalesced copy per item) together with their row offsets.  Returns the
+// entries' base (shared when they fit, else global) and whether staged.
+template <typename T>
+__device__ __forceinline__ bool stage_rows(const int* __restrict__ pp, const void* __restrict__ pk, int row0, int row1,
+                                           int* s_pp, int4* s_ent, const int4*& gent)
+{
+    constexpr int EPI = sizeof(T) == 4 ? 2 : 1;  // entries per int4
+    const int rows = row1 - row0;
+    const int c_lo = __ldg(pp + row0);
+    for (int t = threadIdx.x; t <= rows; t += kThreads) s_pp[t] = __ldg(pp + row0 + t) - c_lo;
+    __syncthreads();
+    const int cnt = s_pp[rows];
+    gent = (const int4*)pk + c_lo / EPI;
+    const bool staged = cnt <= kStageEntries;
+    if (staged)
+        for (int t = threadIdx.x; t < cnt / EPI; t += kThreads) s_ent[t] = __ldg(gent + t);
+    __syncthreads();
+    return staged;
+}
+
+// ---------------------------------------------------------------- reductions
+// Block-wide reduction of NV per-thread values for each of the W lane columns,
+// added to this CTA's slot of the group (slot[cl][0..NV)).  Fixed order.
 template <int W, int NV, typename T>
-__device__ __forceinline__ void block_partials(T (&v)[NV], double* sm, double* out)
+__device__ __forceinline__ void block_partials(T (&v)[NV], double* sm, double* slot)
 {
     constexpr int SEGS = kThreads / W;
     const int tid = threadIdx.x;
@@ -181,16 +231,16 @@ __device__ __forceinline__ void block_partials(T (&v)[NV], double* sm, double* o
 #pragma unroll
             for (int q = 0; q < NV; ++q) s[q] += sm[(g * W + tid) * NV + q];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) out[(size_t)tid * kPartStride + q] = s[q];
+        for (int q = 0; q < NV; ++q) slot[(size_t)tid * kPartStride + q] += s[q];
     }
     __syncthreads();
 }
 
-// Called by all threads of the CTA that finished the last item of a group:
-// sums the group's partials in item order.  Result in red[cl*kPartStride + q].
+// Called by all threads of the CTA that finished the group's last item: sums
+// the group's nslot CTA slots in order into red[cl*kPartStride + q] and
+// zeroes the slots for the next launch.
 template <int W, int NV>
-__device__ __forceinline__ void group_reduce(const double* part, long long item_first, int nrb, double* sm,
-                                             double* red)
+__device__ __forceinline__ void group_reduce(double* slots, int nslot, double* sm, double* red)
 {
     constexpr int SEGS = kThreads / W;
     const int tid = threadIdx.x;
@@ -198,10 +248,13 @@ __device__ __forceinline__ void group_reduce(const double* part, long long item_
     double s[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) s[q] = 0.0;
-    for (int rb = seg; rb < nrb; rb += SEGS) {
-        const double* src = part + ((size_t)(item_first + rb) * W + cl) * kPartStride;
+    for (int b = seg; b < nslot; b += SEGS) {
+        double* src = slots + ((size_t)b * W + cl) * kPartStride;
 #pragma unroll
-        for (int q = 0; q < NV; ++q) s[q] += __ldcg(src + q);
+        for (int q = 0; q < NV; ++q) {
+            s[q] += __ldcg(src + q);
+            src[q] = 0.0;
+        }
     }
 #pragma unroll
     for (int q = 0; q < NV; ++q) sm[(seg * W + cl) * NV + q] = s[q];
@@ -234,70 +287,135 @@ __device__ __forceinline__ bool arrive_group(unsigned* counter, int nrb, int* fl
     return last;
 }
 
+struct ItemInfo {
+    int pi, g, rb;
+};
+
+__device__ __forceinline__ ItemInfo item_info(const FilterArgs& a, long long item)
+{
+    ItemInfo t;
+    t.pi = a.nprob == 1 ? 0 : find_prob(a.probs, a.nprob, item);
+    const long long local = item - a.probs[t.pi].item0;
+    const int nrb = a.probs[t.pi].nrb;
+    t.g = (int)(local / nrb);
+    t.rb = (int)(local % nrb);
+    return t;
+}
+
+// Items of the streaming step use their own, larger row blocks (RBb rows).
+__device__ __forceinline__ int find_prob_b(const FiltProb* probs, int nprob, long long item)
+{
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (probs[mid].item0_b <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ ItemInfo item_info_b(const FilterArgs& a, long long item)
+{
+    ItemInfo t;
+    t.pi = a.nprob == 1 ? 0 : find_prob_b(a.probs, a.nprob, item);
+    const long long local = item - a.probs[t.pi].item0_b;
+    const int nrb = a.probs[t.pi].nrb_b;
+    t.g = (int)(local / nrb);
+    t.rb = (int)(local % nrb);
+    return t;
+}
+
+// L2 prefetch of the tile rows of `item` in up to two block vectors.
+template <typename V, int W>
+__device__ __forceinline__ void prefetch_item(const FilterArgs& a, long long item, const void* v0, const void* v1)
+{
+    if (item >= a.nitems || threadIdx.x >= 2) return;
+    const ItemInfo t = item_info(a, item);
+    const FiltProb& P = a.probs[t.pi];
+    if (a.grp_done[P.grp_off + t.g]) return;
+    const int row0 = t.rb * a.RB;
+    const int rows = min(a.RB, P.n - row0);
+    if (rows <= 0) return;
+    const size_t off = (size_t)P.vec_off + (size_t)t.g * P.n * W + (size_t)row0 * W;
+    const void* base = threadIdx.x == 0 ? v0 : v1;
+    if (base) l2_prefetch((const V*)base + off, (unsigned)(rows * W * sizeof(V)));
+}
+
 // ---------------------------------------------------------------- kernel A
-template <typename T, int W, bool HASB>
+// s = (zB - A) r_k gathered over the matrix rows; then, per own row,
+// p_k = r_k + beta_k p_{k-1}, q_k = s + beta_k q_{k-1} (= (zB - A) p_k),
+// both updated in place, and partial sums of p_k^T q_k (and ||r_0||^2 at k=0).
+// BM: 0 = B is the identity, 1 = B diagonal (values bd), 2 = general CSR B.
+template <typename T, int W, int BM>
 __global__ void __launch_bounds__(kThreads, FEAST_MINB) cocg_step_a(FilterArgs a, int k)
 {
     using V = c2_t<T>;
     constexpr int RPP = kThreads / W;  // rows per pass of the CTA
+    constexpr int STAGE4 = sizeof(T) == 4 ? kStageEntries / 2 : kStageEntries;
     __shared__ double sm[kThreads * 3];
     __shared__ double red[W * kPartStride];
     __shared__ int flag;
+    __shared__ int s_pp[kMaxRB + 1];
+    __shared__ int4 s_ent[STAGE4];
     const int tid = threadIdx.x;
-    const int cl = tid % W, sub = (tid % 32) / W, rowslot = tid / W;
-    const unsigned mask = seg_mask<W>(sub);
+    const int cl = tid % W, rowslot = tid / W;
     const bool first = (k == 0);
-    const V* pold = (const V*)((k & 1) ? a.p0 : a.p1);
-    V* pnew = (V*)((k & 1) ? a.p1 : a.p0);
 
     for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
-        const int pi = a.nprob == 1 ? 0 : find_prob(a.probs, a.nprob, item);
-        const FiltProb P = a.probs[pi];
-        const long long local = item - P.item0;
-        const int g = (int)(local / P.nrb), rb = (int)(local % P.nrb);
+        const ItemInfo it = item_info(a, item);
+        const FiltProb& P = a.probs[it.pi];
+        const int g = it.g;
         if (a.grp_done[P.grp_off + g]) continue;
         ColState* csg = a.cs + P.col_off + (size_t)g * W;
         const int active = csg[cl].active;
         const double2 zd = csg[cl].z, bd = csg[cl].beta;
         const V z = cmk<V>((T)zd.x, (T)zd.y), beta = cmk<V>((T)bd.x, (T)bd.y);
         const bool use_p = !first && active;
-        const size_t tile = (size_t)P.vec_off + (size_t)g * P.n * W;
-        const V* r = (const V*)a.r + tile;
-        const V* po = pold + tile;
-        V* pn = pnew + tile;
-        T acc[3] = {T(0), T(0), T(0)};  // sigma.re, sigma.im, ||b||^2 (first); FP32 in mixed precision
-        const int row0 = rb * a.RB;
-        for (int rl = rowslot; rl < a.RB; rl += RPP * kRows) {
-            int rows[kRows];
-#pragma unroll
-            for (int q = 0; q < kRows; ++q) {
-                const int i = row0 + rl + q * RPP;
-                rows[q] = (rl + q * RPP < a.RB && i < P.n) ? i : -1;
+        const int n = P.n;
+        const size_t tile = (size_t)P.vec_off + (size_t)g * n * W;
+        const V* rl_ = (const V*)a.r + tile + cl;
+        V* pl_ = (V*)a.p0 + tile + cl;
+        V* ql_ = (V*)a.p1 + tile + cl;
+        T acc[3] = {T(0), T(0), T(0)};  // sigma.re, sigma.im, ||b||^2 (first)
+        const int row0 = it.rb * a.RB;
+        const int row1 = min(n, row0 + a.RB);
+        const int4* gent;
+        const bool staged = stage_rows<T>(P.app, P.apk, row0, row1, s_pp, s_ent, gent);
+        for (int i = row0 + rowslot; i < row1; i += RPP) {
+            // own-row streams first, so their loads overlap the gather
+            V po = cmk<V>(T(0), T(0)), qo = cmk<V>(T(0), T(0));
+            if (use_p) {
+                po = pl_[(size_t)i * W];
+                qo = ql_[(size_t)i * W];
             }
-            if (rows[0] < 0) break;
-            V ar[kRows], ap[kRows];
-            rows_gather<T, W, true, kRows>(P.ia, P.apk, rows, cl, r, po, use_p, ar, ap);
-            V br[kRows], bp[kRows];
-            if (HASB) rows_gather<T, W, true, kRows>(P.ib, P.bpk, rows, cl, r, po, use_p, br, bp);
-#pragma unroll
-            for (int q = 0; q < kRows; ++q) {
-                if (rows[q] < 0) continue;
-                const int i = rows[q];
-                V pi_ = __ldg(r + (size_t)i * W + cl);
-                if (use_p) pi_ = cfma(beta, __ldg(po + (size_t)i * W + cl), pi_);
-                const V ax = use_p ? cfma(beta, ap[q], ar[q]) : ar[q];  // A (r + beta p)
-                V bx = pi_;
-                if (HASB) bx = use_p ? cfma(beta, bp[q], br[q]) : br[q];
-                const V qv = csub(cmul(z, bx), ax);
-                pn[(size_t)i * W + cl] = pi_;
-                acc[0] = fma(pi_.x, qv.x, fma(-pi_.y, qv.y, acc[0]));
-                acc[1] = fma(pi_.x, qv.y, fma(pi_.y, qv.x, acc[1]));
-                if (first) acc[2] = fma(pi_.x, pi_.x, fma(pi_.y, pi_.y, acc[2]));
+            const int c0 = s_pp[i - row0], c1 = s_pp[i - row0 + 1];
+            V ar, unused, ri, unused2;
+            bool own;
+            if (staged) row_gather<T, W, false, true>(s_ent, c0, c1, i, rl_, nullptr, false, ar, unused, ri, unused2, own);
+            else row_gather<T, W, false, false>(gent, c0, c1, i, rl_, nullptr, false, ar, unused, ri, unused2, own);
+            if (!own) ri = __ldg(rl_ + (size_t)i * W);
+            V bx = ri;
+            if (BM == 1) {
+                const T b = ((const T*)P.bd)[i];
+                bx = cmk<V>(b * ri.x, b * ri.y);
+            } else if (BM == 2) {
+                bx = row_gather_global<T, W>(P.bpp, P.bpk, i, rl_);
             }
+            V pi_ = ri, qi = csub(cmul(z, bx), ar);  // (zB - A) r
+            if (use_p) {
+                pi_ = cfma(beta, po, pi_);
+                qi = cfma(beta, qo, qi);
+            }
+            pl_[(size_t)i * W] = pi_;
+            ql_[(size_t)i * W] = qi;
+            acc[0] = fma(pi_.x, qi.x, fma(-pi_.y, qi.y, acc[0]));
+            acc[1] = fma(pi_.x, qi.y, fma(pi_.y, qi.x, acc[1]));
+            if (first) acc[2] = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[2]));
         }
-        block_partials<W, 3>(acc, sm, a.part + (size_t)item * W * kPartStride);
+        double* slots = a.part + (size_t)(P.grp_off + g) * a.nslot * W * kPartStride;
+        block_partials<W, 3>(acc, sm, slots + (size_t)blockIdx.x * W * kPartStride);
         if (arrive_group(a.grp_count + P.grp_off + g, P.nrb, &flag)) {
-            group_reduce<W, 3>(a.part, P.item0 + (long long)g * P.nrb, P.nrb, sm, red);
+            group_reduce<W, 3>(slots, a.nslot, sm, red);
             if (tid < W) {
                 ColState cs = csg[tid];
                 if (first) {
@@ -328,8 +446,12 @@ __global__ void __launch_bounds__(kThreads, FEAST_MINB) cocg_step_a(FilterArgs a
 }
 
 // ---------------------------------------------------------------- kernel B
-template <typename T, int W, bool HASB>
-__global__ void __launch_bounds__(kThreads, FEAST_MINB) cocg_step_b(FilterArgs a, int k)
+// Pure streaming over own rows: r_{k+1} = r_k - alpha q_k, the quadrature
+// accumulator += Re(c alpha p_k) (summed over the node lanes of a column),
+// partial sums of r^T r and |r|^2; the last item of a group sets beta and
+// the columns' convergence state.
+template <typename T, int W, int BM>
+__global__ void __launch_bounds__(kThreads, FEAST_MINB_B) cocg_step_b(FilterArgs a, int k)
 {
     using V = c2_t<T>;
     constexpr int RPP = kThreads / W;
@@ -339,66 +461,64 @@ __global__ void __launch_bounds__(kThreads, FEAST_MINB) cocg_step_b(FilterArgs a
     const int tid = threadIdx.x;
     const int cl = tid % W, sub = (tid % 32) / W, rowslot = tid / W;
     const unsigned mask = seg_mask<W>(sub);
-    const V* pk = (const V*)((k & 1) ? a.p1 : a.p0);
     const int e = cl % a.nbp, mloc = cl / a.nbp;
 
-    for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
-        const int pi = a.nprob == 1 ? 0 : find_prob(a.probs, a.nprob, item);
-        const FiltProb P = a.probs[pi];
-        const long long local = item - P.item0;
-        const int g = (int)(local / P.nrb), rb = (int)(local % P.nrb);
+    for (long long item = blockIdx.x; item < a.nitems_b; item += gridDim.x) {
+        const ItemInfo it = item_info_b(a, item);
+        const FiltProb& P = a.probs[it.pi];
+        const int g = it.g;
         if (a.grp_done[P.grp_off + g]) continue;
         ColState* csg = a.cs + P.col_off + (size_t)g * W;
         const int active = csg[cl].active;
-        const double2 zd = csg[cl].z, ald = csg[cl].alpha, cad = csg[cl].ca;
-        const V z = cmk<V>((T)zd.x, (T)zd.y);
+        const double2 ald = csg[cl].alpha, cad = csg[cl].ca;
         const V alpha = cmk<V>((T)ald.x, (T)ald.y);
         const V ca = cmk<V>((T)cad.x, (T)cad.y);
-        const size_t tile = (size_t)P.vec_off + (size_t)g * P.n * W;
-        V* r = (V*)a.r + tile;
-        const V* p = pk + tile;
+        const int n = P.n;
+        const size_t tile = (size_t)P.vec_off + (size_t)g * n * W;
+        V* r = (V*)a.r + tile + cl;
+        const V* pl_ = (const V*)a.p0 + tile + cl;
+        const V* ql_ = (const V*)a.p1 + tile + cl;
         const int m = g * a.mt + mloc;
-        T* dQrow = (T*)a.dQ + P.q_off + m;
+        T* dQt = (T*)a.dQ + P.dq_off + (size_t)g * n * a.mt + mloc;  // [group][row][mt] tile
+        const bool writes_q = (e == 0 && m < P.m0);
         T acc[3] = {T(0), T(0), T(0)};  // rho.re, rho.im, ||r||^2
-        const int row0 = rb * a.RB;
-        for (int rl = rowslot; rl < a.RB; rl += RPP * kRows) {
-            int rows[kRows];
+        const int row0 = it.rb * a.RBb;
+        const int row1 = min(n, row0 + a.RBb);
+        // two rows per thread per pass, every load issued before any use
+        for (int i0 = row0 + rowslot; i0 < row1; i0 += 2 * RPP) {
+            const int ii[2] = {i0, i0 + RPP};
+            V rv[2], pv[2], qv[2];
+            T dq[2];
 #pragma unroll
-            for (int q = 0; q < kRows; ++q) {
-                const int i = row0 + rl + q * RPP;
-                rows[q] = (rl + q * RPP < a.RB && i < P.n) ? i : -1;
+            for (int u = 0; u < 2; ++u) {
+                const bool ok = ii[u] < row1;
+                const size_t o = (size_t)(ok ? ii[u] : i0) * W;
+                rv[u] = ok ? r[o] : cmk<V>(T(0), T(0));
+                pv[u] = (ok && active) ? __ldg(pl_ + o) : cmk<V>(T(0), T(0));
+                qv[u] = (ok && active) ? __ldg(ql_ + o) : cmk<V>(T(0), T(0));
+                dq[u] = (ok && writes_q) ? dQt[(size_t)(ok ? ii[u] : i0) * a.mt] : T(0);
             }
-            if (rows[0] < 0) break;
-            V ax[kRows], unused[kRows], bxs[kRows];
-            rows_gather<T, W, false, kRows>(P.ia, P.apk, rows, cl, p, nullptr, false, ax, unused);
-            if (HASB) rows_gather<T, W, false, kRows>(P.ib, P.bpk, rows, cl, p, nullptr, false, bxs, unused);
 #pragma unroll
-            for (int q = 0; q < kRows; ++q) {
-                const int i = rows[q] < 0 ? 0 : rows[q];
-                const bool ok = rows[q] >= 0;
-                V pi_ = cmk<V>(T(0), T(0)), ri = cmk<V>(T(0), T(0));
-                if (ok) {
-                    pi_ = __ldg(p + (size_t)i * W + cl);
-                    ri = r[(size_t)i * W + cl];
-                }
-                const V bx = HASB ? bxs[q] : pi_;
+            for (int u = 0; u < 2; ++u) {
+                const bool ok = ii[u] < row1;
+                V ri = rv[u];
                 T qc = T(0);
-                if (active && ok) {
-                    const V qv = csub(cmul(z, bx), ax[q]);
-                    ri = csub(ri, cmul(alpha, qv));
-                    r[(size_t)i * W + cl] = ri;
-                    qc = ca.x * pi_.x - ca.y * pi_.y;  // Re(c alpha p)
+                if (active) {
+                    ri = csub(ri, cmul(alpha, qv[u]));
+                    if (ok) r[(size_t)ii[u] * W] = ri;
+                    qc = ca.x * pv[u].x - ca.y * pv[u].y;  // Re(c alpha p)
                 }
                 for (int o = 1; o < a.nbp; o <<= 1) qc += __shfl_xor_sync(mask, qc, o, W);
-                if (ok && e == 0 && m < P.m0) dQrow[(size_t)i * P.m0] += qc;
+                if (ok && writes_q) dQt[(size_t)ii[u] * a.mt] = dq[u] + qc;
                 acc[0] = fma(ri.x, ri.x, fma(-ri.y, ri.y, acc[0]));
                 acc[1] = fma(T(2) * ri.x, ri.y, acc[1]);
                 acc[2] = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[2]));
             }
         }
-        block_partials<W, 3>(acc, sm, a.part + (size_t)item * W * kPartStride);
-        if (arrive_group(a.grp_count + P.grp_off + g, P.nrb, &flag)) {
-            group_reduce<W, 3>(a.part, P.item0 + (long long)g * P.nrb, P.nrb, sm, red);
+        double* slots = a.part + (size_t)(P.grp_off + g) * a.nslot * W * kPartStride;
+        block_partials<W, 3>(acc, sm, slots + (size_t)blockIdx.x * W * kPartStride);
+        if (arrive_group(a.grp_count + P.grp_off + g, P.nrb_b, &flag)) {
+            group_reduce<W, 3>(slots, a.nslot, sm, red);
             if (tid < 32) {
                 int still = 0;
                 if (tid < W) {
@@ -427,10 +547,10 @@ __global__ void __launch_bounds__(kThreads, FEAST_MINB) cocg_step_b(FilterArgs a
                 if (tid == 0) {
                     if (!anyv) {
                         a.grp_done[P.grp_off + g] = 1;
-                        atomicSub(a.groups_left + pi, 1);
+                        atomicSub(a.groups_left + it.pi, 1);
                     }
                     if (a.work) atomicAdd(a.work, 1ull);
-                    atomicMax(a.iter_max + pi, k + 1);
+                    atomicMax(a.iter_max + it.pi, k + 1);
                     a.grp_count[P.grp_off + g] = 0u;
                 }
             }
@@ -496,10 +616,9 @@ __global__ void __launch_bounds__(kThreads) filter_init(FilterArgs a, const doub
     const int cl = tid % W, rowslot = tid / W;
     const int e = cl % a.nbp, mloc = cl / a.nbp;
     for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
-        const int pi = a.nprob == 1 ? 0 : find_prob(a.probs, a.nprob, item);
-        const FiltProb P = a.probs[pi];
-        const long long local = item - P.item0;
-        const int g = (int)(local / P.nrb), rb = (int)(local % P.nrb);
+        const ItemInfo it = item_info(a, item);
+        const FiltProb& P = a.probs[it.pi];
+        const int g = it.g, rb = it.rb;
         const int m = g * a.mt + mloc;
         const ColState& cs = a.cs[P.col_off + (size_t)g * W + cl];
         const int live = cs.active;
@@ -515,84 +634,118 @@ __global__ void __launch_bounds__(kThreads) filter_init(FilterArgs a, const doub
             r[(size_t)i * W + cl] = cmk<V>((T)v, T(0));
             if (init_q && e == 0 && m < P.m0) {
                 a.Q[P.q_off + (size_t)i * P.m0 + m] = (rii && live) ? rq * X[P.q_off + (size_t)i * P.m0 + m] : 0.0;
-                ((T*)a.dQ)[P.q_off + (size_t)i * P.m0 + m] = T(0);
+                ((T*)a.dQ)[P.dq_off + ((size_t)g * P.n + i) * a.mt + mloc] = T(0);
             }
         }
     }
 }
 
 // ---------------------------------------------------------------- standalone shifted SpMM
-// V = (z B - A) P on the tiled layout (p0 -> r buffer is unused): reads a.p0,
-// writes a.p1.  Shifts come from the column states.
-template <typename T, int W>
+// V = (z B - A) P on the tiled layout: reads a.p0, writes a.p1.  Shifts come
+// from the column states.
+template <typename T, int W, int BM>
 __global__ void __launch_bounds__(kThreads) shifted_spmm(FilterArgs a)
 {
     using V = c2_t<T>;
     constexpr int RPP = kThreads / W;
     const int tid = threadIdx.x;
-    const int cl = tid % W, sub = (tid % 32) / W, rowslot = tid / W;
-    const unsigned mask = seg_mask<W>(sub);
+    const int cl = tid % W, rowslot = tid / W;
     for (long long item = blockIdx.x; item < a.nitems; item += gridDim.x) {
-        const int pi = a.nprob == 1 ? 0 : find_prob(a.probs, a.nprob, item);
-        const FiltProb P = a.probs[pi];
-        const long long local = item - P.item0;
-        const int g = (int)(local / P.nrb), rb = (int)(local % P.nrb);
-        const double2 zd = a.cs[P.col_off + (size_t)g * W + cl].z;
+        const ItemInfo it = item_info(a, item);
+        const FiltProb& P = a.probs[it.pi];
+        const double2 zd = a.cs[P.col_off + (size_t)it.g * W + cl].z;
         const V z = cmk<V>((T)zd.x, (T)zd.y);
-        const size_t tile = (size_t)P.vec_off + (size_t)g * P.n * W;
-        const V* x = (const V*)a.p0 + tile;
-        V* y = (V*)a.p1 + tile;
-        const int row0 = rb * a.RB;
-        for (int rl = rowslot; rl < a.RB; rl += RPP) {
-            const int i = row0 + rl;
-            if (i >= P.n) break;
-            V ax, unused, bx;
-            row_gather<T, W, false>(P.ia, P.apk, i, cl, x, nullptr, false, ax, unused);
-            if (P.ib == nullptr) bx = __ldg(x + (size_t)i * W + cl);
-            else row_gather<T, W, false>(P.ib, P.bpk, i, cl, x, nullptr, false, bx, unused);
-            y[(size_t)i * W + cl] = csub(cmul(z, bx), ax);
+        const size_t tile = (size_t)P.vec_off + (size_t)it.g * P.n * W;
+        const V* x = (const V*)a.p0 + tile + cl;
+        V* y = (V*)a.p1 + tile + cl;
+        const int row0 = it.rb * a.RB;
+        const int row1 = min(P.n, row0 + a.RB);
+        for (int i = row0 + rowslot; i < row1; i += RPP) {
+            V bx = __ldg(x + (size_t)i * W);
+            const V ax = row_gather_global<T, W>(P.app, P.apk, i, x);
+            if (BM == 1) {
+                const T b = ((const T*)P.bd)[i];
+                bx = cmk<V>(b * bx.x, b * bx.y);
+            } else if (BM == 2) {
+                bx = row_gather_global<T, W>(P.bpp, P.bpk, i, x);
+            }
+            y[(size_t)i * W] = csub(cmul(z, bx), ax);
         }
     }
 }
 
-// Q += dQ after all node batches of a pass (dQ: FP32 in mixed precision).
+// Q += dQ after all node batches of a pass (dQ: FP32 in mixed precision,
+// tiled [group][row][mt] per problem; Q row-major n x m0 per problem).
 template <typename T>
-__global__ void fold_dq(long long total, const T* dQ, double* Q)
+__global__ void fold_dq(const FiltProb* probs, int nprob, int mt, const T* dQ, double* Q)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
-        Q[i] += (double)dQ[i];
+    const FiltProb& P = probs[blockIdx.y];
+    const long long total = (long long)P.n * P.m0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / P.m0), m = (int)(t % P.m0);
+        const int g = m / mt, ml = m % mt;
+        Q[P.q_off + t] += (double)dQ[P.dq_off + ((size_t)g * P.n + i) * mt + ml];
+    }
 }
 
-// Packed (column, value) CSR entries for the uniform-load gathers.
-__global__ void pack_csr(long long nnz, const int* ja, const double* av, int fp64, void* out)
+// Packed (column, value) CSR entries padded to whole chunks: row i occupies
+// entries [pp[i], pp[i+1]) of out; entries past the row's nonzeros are
+// (i, 0).  One warp per row.
+__global__ void pack_csr(int n, const int* ia, const int* ja, const double* av, const int* pp, int fp64, void* out)
 {
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nnz; t += (long long)gridDim.x * blockDim.x) {
-        if (fp64) {
-            const double v = av[t];
-            ((int4*)out)[t] = make_int4(ja[t], 0, __double2loint(v), __double2hiint(v));
-        } else {
-            ((int2*)out)[t] = make_int2(ja[t], __float_as_int((float)av[t]));
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < n; i += nw) {
+        const int s = ia[i], len = ia[i + 1] - s, c0 = pp[i], c1 = pp[i + 1];
+        for (int t = c0 + lane; t < c1; t += 32) {
+            const int q = t - c0;
+            const int j = q < len ? ja[s + q] : i;
+            const double v = q < len ? av[s + q] : 0.0;
+            if (fp64) ((int4*)out)[t] = make_int4(j, 0, __double2loint(v), __double2hiint(v));
+            else ((int2*)out)[t] = make_int2(j, __float_as_int((float)v));
         }
     }
 }
 
-cudaError_t launch_fold_dq(long long total, const void* dQ, bool fp64, double* Q, cudaStream_t s)
+__global__ void cast_diag(int n, const int* ia, const double* av, int fp64, void* out)
 {
-    if (total <= 0) return cudaSuccess;
-    long long blocks = (total + 255) / 256;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = av[ia[i]];
+        if (fp64) ((double*)out)[i] = v;
+        else ((float*)out)[i] = (float)v;
+    }
+}
+
+cudaError_t launch_fold_dq(const FilterArgs& a, long long max_total, bool fp64, cudaStream_t s)
+{
+    if (max_total <= 0) return cudaSuccess;
+    long long blocks = (max_total + 255) / 256;
     if (blocks > (long long)num_sms() * 8) blocks = (long long)num_sms() * 8;
-    if (fp64) fold_dq<double><<<(int)blocks, 256, 0, s>>>(total, (const double*)dQ, Q);
-    else fold_dq<float><<<(int)blocks, 256, 0, s>>>(total, (const float*)dQ, Q);
+    dim3 grid((unsigned)blocks, a.nprob);
+    if (fp64) fold_dq<double><<<grid, 256, 0, s>>>(a.probs, a.nprob, a.mt, (const double*)a.dQ, a.Q);
+    else fold_dq<float><<<grid, 256, 0, s>>>(a.probs, a.nprob, a.mt, (const float*)a.dQ, a.Q);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_csr(long long nnz, const int* ja, const double* av, bool fp64, void* out, cudaStream_t s)
+cudaError_t launch_pack_csr(int n, const int* ia, const int* ja, const double* av, const int* pp, bool fp64, void* out,
+                            cudaStream_t s)
 {
-    if (nnz <= 0) return cudaSuccess;
-    long long blocks = (nnz + 255) / 256;
+    if (n <= 0) return cudaSuccess;
+    long long blocks = ((long long)n + 7) / 8;
     if (blocks > 4096) blocks = 4096;
-    pack_csr<<<(int)blocks, 256, 0, s>>>(nnz, ja, av, fp64 ? 1 : 0, out);
+    pack_csr<<<(int)blocks, 256, 0, s>>>(n, ia, ja, av, pp, fp64 ? 1 : 0, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cast_diag(int n, const int* ia, const double* av, bool fp64, void* out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    long long blocks = ((long long)n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    cast_diag<<<(int)blocks, 256, 0, s>>>(n, ia, av, fp64 ? 1 : 0, out);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -619,31 +772,26 @@ __global__ void cast_values(const double* src, float* dst, long long n)
         return cudaGetLastError();                                                         \
     } while (0)
 
-#define FEAST_DISPATCH_B(KERNEL, ...)                                                      \
-    do {                                                                                   \
-        if (a.hasB) {                                                                      \
-            if (fp64) {                                                                    \
-                if (a.W == 16) KERNEL<double, 16, true><<<grid, kThreads, 0, s>>>(__VA_ARGS__);      \
-                else if (a.W == 32) KERNEL<double, 32, true><<<grid, kThreads, 0, s>>>(__VA_ARGS__); \
-                else return cudaErrorInvalidValue;                                         \
-            } else {                                                                       \
-                if (a.W == 16) KERNEL<float, 16, true><<<grid, kThreads, 0, s>>>(__VA_ARGS__);       \
-                else if (a.W == 32) KERNEL<float, 32, true><<<grid, kThreads, 0, s>>>(__VA_ARGS__);  \
-                else return cudaErrorInvalidValue;                                         \
-            }                                                                              \
-        } else {                                                                           \
-            if (fp64) {                                                                    \
-                if (a.W == 16) KERNEL<double, 16, false><<<grid, kThreads, 0, s>>>(__VA_ARGS__);      \
-                else if (a.W == 32) KERNEL<double, 32, false><<<grid, kThreads, 0, s>>>(__VA_ARGS__); \
-                else return cudaErrorInvalidValue;                                         \
-            } else {                                                                       \
-                if (a.W == 16) KERNEL<float, 16, false><<<grid, kThreads, 0, s>>>(__VA_ARGS__);       \
-                else if (a.W == 32) KERNEL<float, 32, false><<<grid, kThreads, 0, s>>>(__VA_ARGS__);  \
-                else return cudaErrorInvalidValue;                                         \
-            }                                                                              \
-        }                                                                                  \
-        count_launches(1);                                                                 \
-        return cudaGetLastError();                                                         \
+#define FEAST_LAUNCH_T(KERNEL, T, BMV, ...)                                          \
+    do {                                                                             \
+        if (a.W == 16) KERNEL<T, 16, BMV><<<grid, kThreads, 0, s>>>(__VA_ARGS__);    \
+        else if (a.W == 32) KERNEL<T, 32, BMV><<<grid, kThreads, 0, s>>>(__VA_ARGS__); \
+        else return cudaErrorInvalidValue;                                           \
+    } while (0)
+
+#define FEAST_DISPATCH_B(KERNEL, ...)                                                \
+    do {                                                                             \
+        if (fp64) {                                                                  \
+            if (a.bmode == 0) FEAST_LAUNCH_T(KERNEL, double, 0, __VA_ARGS__);        \
+            else if (a.bmode == 1) FEAST_LAUNCH_T(KERNEL, double, 1, __VA_ARGS__);   \
+            else FEAST_LAUNCH_T(KERNEL, double, 2, __VA_ARGS__);                     \
+        } else {                                                                     \
+            if (a.bmode == 0) FEAST_LAUNCH_T(KERNEL, float, 0, __VA_ARGS__);         \
+            else if (a.bmode == 1) FEAST_LAUNCH_T(KERNEL, float, 1, __VA_ARGS__);    \
+            else FEAST_LAUNCH_T(KERNEL, float, 2, __VA_ARGS__);                      \
+        }                                                                            \
+        count_launches(1);                                                           \
+        return cudaGetLastError();                                                   \
     } while (0)
 
 cudaError_t launch_cocg_step_a(const FilterArgs& a, bool fp64, int k, int grid, cudaStream_t s)
@@ -672,19 +820,43 @@ cudaError_t launch_colstate_init(const FilterArgs& a, int node0, int rii, cudaSt
 
 cudaError_t launch_shifted_spmm(const FilterArgs& a, bool fp64, int grid, cudaStream_t s)
 {
-    FEAST_DISPATCH(shifted_spmm, a);
+    FEAST_DISPATCH_B(shifted_spmm, a);
+}
+
+// Persistent grid sizes of the COCG launches: SMs x resident CTAs per SM of
+// each kernel (identity-B variants; the others differ little).
+void filter_grids(bool fp64, int W, int* grid_a, int* grid_b)
+{
+    int oa = 0, ob = 0;
+    if (fp64) {
+        if (W == 16) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oa, cocg_step_a<double, 16, 0>, kThreads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, cocg_step_b<double, 16, 0>, kThreads, 0);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oa, cocg_step_a<double, 32, 0>, kThreads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, cocg_step_b<double, 32, 0>, kThreads, 0);
+        }
+    } else {
+        if (W == 16) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oa, cocg_step_a<float, 16, 0>, kThreads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, cocg_step_b<float, 16, 0>, kThreads, 0);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oa, cocg_step_a<float, 32, 0>, kThreads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, cocg_step_b<float, 32, 0>, kThreads, 0);
+        }
+    }
+    cudaGetLastError();
+    if (oa < 1) oa = 1;
+    if (ob < 1) ob = 1;
+    *grid_a = num_sms() * oa;
+    *grid_b = num_sms() * ob;
 }
 
 int filter_grid(bool fp64, int W)
 {
-    int occ = 0;
-    cudaError_t e;
-    if (fp64) e = W == 16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cocg_step_b<double, 16, false>, kThreads, 0)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cocg_step_b<double, 32, false>, kThreads, 0);
-    else e = W == 16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cocg_step_b<float, 16, false>, kThreads, 0)
-                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cocg_step_b<float, 32, false>, kThreads, 0);
-    if (e != cudaSuccess || occ < 1) occ = 1;
-    return num_sms() * occ;
+    int ga, gb;
+    filter_grids(fp64, W, &ga, &gb);
+    return ga > gb ? ga : gb;
 }
 
 cudaError_t launch_cast_values(const double* src, float* dst, long long n, cudaStream_t s)
