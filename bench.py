@@ -52,7 +52,9 @@ def parse():
 def workload(side):
     import feast_workloads as fw
 
-    return fw.laplace3d_potential(side=side, count=100, m0=150, ne=8, ratio=100, seed=1)
+    # contour: Gauss, Ne = 8, ellipse ratio fpm(18) = 200 (vertical axis twice the
+    # half-width: keeps the shifted systems better conditioned for COCG)
+    return fw.laplace3d_potential(side=side, count=100, m0=150, ne=8, ratio=200, seed=1)
 
 
 def config_dict(p, extra=None):

@@ -207,6 +207,16 @@ def filter_block(A, B, ne, emin, emax, ratio, Y, lam=None, rii=False, solver="di
     return Q
 
 
+def eig_grad(A, X, w):
+    """grad[p] = sum_k w_k X[i_p,k] X[j_p,k] over the stored entries of A."""
+    X = np.asfortranarray(X, dtype=np.float64)
+    w = _c(w, np.float64)
+    ip, ix, _ = _csr_args(A)
+    grad = np.zeros(A.nnz)
+    lib().orc_eig_grad(C.c_int(A.n), _ptr(ip), _ptr(ix), C.c_int(X.shape[1]), _ptr(X), _ptr(w), _ptr(grad))
+    return grad
+
+
 # ---------------------------------------------------------------- FEAST
 def feastinit():
     """fpm defaults of the guide's parameter table (C indexing fpm[i-1])."""

@@ -795,6 +795,22 @@ out:
     return info;
 }
 
+/* Gradient of L = sum_k w_k lambda_k with respect to the stored entries of a
+ * CSR pattern, for B-orthonormal eigenvectors X (column-major n x m):
+ * grad[p] = sum_k w_k X[i_p, k] X[j_p, k] (first-order perturbation of a
+ * simple eigenpair; for entries of B pass w_k = -g_k lambda_k). */
+void orc_eig_grad(int n, const int* ip, const int* ix, int m, const double* X, const double* w, double* grad)
+{
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i)
+        for (int p = ip[i]; p < ip[i + 1]; ++p) {
+            const int j = ix[p];
+            double s = 0.0;
+            for (int k = 0; k < m; ++k) s += w[k] * X[(size_t)k * n + i] * X[(size_t)k * n + j];
+            grad[p] = s;
+        }
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

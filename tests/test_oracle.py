@@ -282,3 +282,48 @@ def test_no_eigenvalue_in_interval():
     A = fw.laplacian_1d(50)
     r = O.feast_scsr(A, None, 5.0, 6.0, 8, Y0=fw.gaussian_block(50, 8, 1), ratio=100)
     assert r["info"] == 1 and r["M"] == 0
+
+
+def _sym_pair_indices(A, p):
+    """Stored index of the transposed entry of entry p (same index on the diagonal)."""
+    i = int(np.searchsorted(A.indptr, p, side="right") - 1)
+    j = int(A.indices[p])
+    row = slice(A.indptr[j], A.indptr[j + 1])
+    q = A.indptr[j] + int(np.nonzero(A.indices[row] == i)[0][0])
+    return i, j, q
+
+
+@pytest.mark.parametrize("gen", [False, True])
+def test_eig_grad_matches_finite_differences(gen):
+    # d(sum_k g_k lambda_k)/d(a_ij) summed over the symmetric pair (i,j),(j,i)
+    # equals the symmetric central difference of dense eigenvalues
+    rng = np.random.default_rng(11)
+    A = fw.laplace3d_potential(side=4, count=5, m0=8, seed=3).A
+    n = A.n
+    B = fw.diagonal_csr(rng.uniform(1, 2, n)) if gen else None
+    db = np.eye(n) if B is None else B.to_dense()
+    lam, X = scipy.linalg.eigh(A.to_dense(), db)
+    k = 10
+    g = rng.standard_normal(k)
+    ga = O.eig_grad(A, X[:, :k], g)
+    gb = O.eig_grad(B, X[:, :k], -g * lam[:k]) if gen else None
+    h = 1e-6
+    for p in rng.choice(A.nnz, 12, replace=False):
+        i, j, q = _sym_pair_indices(A, p)
+        E = np.zeros((n, n))
+        E[i, j] += h
+        if i != j:
+            E[j, i] += h
+        lp = scipy.linalg.eigh(A.to_dense() + E, db, eigvals_only=True)[:k]
+        lm = scipy.linalg.eigh(A.to_dense() - E, db, eigvals_only=True)[:k]
+        fd = np.dot(g, lp - lm) / (2 * h)
+        an = ga[p] + (ga[q] if q != p else 0.0)
+        assert abs(fd - an) < 1e-6 + 1e-6 * abs(fd), (p, fd, an)
+    if gen:
+        for i in rng.choice(n, 6, replace=False):
+            E = np.zeros((n, n))
+            E[i, i] = h
+            lp = scipy.linalg.eigh(A.to_dense(), db + E, eigvals_only=True)[:k]
+            lm = scipy.linalg.eigh(A.to_dense(), db - E, eigvals_only=True)[:k]
+            fd = np.dot(g, lp - lm) / (2 * h)
+            assert abs(fd - gb[i]) < 1e-6 + 1e-6 * abs(fd)
