@@ -260,24 +260,103 @@ def stencil27_generalized(side: int = 96, count: int = 200, m0: int = 300, ne: i
                    m0, ne, ratio, seed, {"target_count": count})
 
 
+def count_below(A: CSR, sigma: float) -> int:
+    """Number of eigenvalues of the symmetric A below sigma, by Sylvester's law
+    of inertia: negative pivots of a sparse symmetric LDL^T of A - sigma I
+    (SuperLU with a symmetric ordering and diagonal pivots; a library
+    factorisation used only to place search intervals)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as sla
+
+    M = sp.csc_matrix((A.data, A.indices, A.indptr), shape=(A.n, A.n)) - sigma * sp.identity(A.n, format="csc")
+    lu = sla.splu(M.tocsc(), permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0,
+                  options={"SymmetricMode": True})
+    return int(np.sum(lu.U.diagonal() < 0))
+
+
+def _place_interval(A: CSR, k: int, e_est: float):
+    """Emax with count_below(A, Emax) within [max(8, 3k/4), min(64, 5k/4)]:
+    Illinois regula falsi on the count, bracketed below by 0 (all eigenvalues
+    are positive) and above by the closed-form estimate (doubled if short)."""
+    lo_c, hi_c = max(8, (3 * k) // 4), min(64, (5 * k + 3) // 4)
+    target = 0.5 * (lo_c + hi_c)
+    e_hi, c_hi = e_est, count_below(A, e_est)
+    if lo_c <= c_hi <= hi_c:
+        return e_hi, c_hi
+    e_lo, c_lo = 0.0, 0
+    while c_hi < lo_c:
+        e_lo, c_lo = e_hi, c_hi
+        e_hi *= 2.0
+        c_hi = count_below(A, e_hi)
+    if lo_c <= c_hi <= hi_c:
+        return e_hi, c_hi
+    side = 0
+    e, c = e_hi, c_hi
+    for _ in range(60):
+        e = e_lo + (target - c_lo) * (e_hi - e_lo) / max(c_hi - c_lo, 1)
+        c = count_below(A, e)
+        if lo_c <= c <= hi_c:
+            break
+        if c > hi_c:
+            e_hi, c_hi = e, c
+            if side == -1:
+                c_lo = c_lo + (target - c_lo) * 0.5  # Illinois: halve the stale end's weight
+            side = -1
+        else:
+            e_lo, c_lo = e, c
+            if side == 1:
+                c_hi = c_hi - (c_hi - target) * 0.5
+            side = 1
+    return e, c
+
+
+def _laplace2d_problem(args):
+    p, seed, ne, ratio, side_lo, side_hi = args
+    rng = np.random.default_rng([seed, p])
+    side = int(math.floor(math.exp(rng.uniform(math.log(side_lo), math.log(side_hi)))))
+    side = max(side_lo, min(side_hi, side))
+    k = int(rng.integers(8, 65))
+    pot = rng.uniform(0.0, 1.0, size=(side, side))
+    A = laplacian_2d(side, pot)
+    emax, c = _place_interval(A, k, interval_estimate(side, 2, k, 0.5))
+    # lower end just below the lowest eigenvalue: bisect the last energy with
+    # an empty count, then leave a margin of 5% of the occupied width
+    lam_lap = 2.0 * (2.0 - 2.0 * math.cos(math.pi / (side + 1)))  # lowest Laplacian eigenvalue
+    lo, hi = lam_lap + float(pot.min()), emax  # Weyl: no eigenvalue below lo
+    for _ in range(7):
+        mid = 0.5 * (lo + hi)
+        if count_below(A, mid) == 0:
+            lo = mid
+        else:
+            hi = mid
+    emin = max(0.0, lo - 0.05 * (emax - lo))
+    m0 = int(math.ceil(1.5 * c))
+    return Problem(f"laplace2d_{p}_{side}^2", A, None, emin, emax, m0, ne, ratio, 1000 * seed + p,
+                   {"target_count": k, "count": c})
+
+
 def batched_laplace2d(count: int = 512, seed: int = 3, ne: int = 8, ratio: int = 100,
-                      side_lo: int = 32, side_hi: int = 256) -> list[Problem]:
+                      side_lo: int = 32, side_hi: int = 256, workers: int | None = None) -> list[Problem]:
     """Independent 2D 5-point Laplacians with V ~ U[0,1]; grid side log-uniform in
-    [side_lo, side_hi]; each with k ~ U{8..64} wanted eigenvalues, M0 = ceil(1.5k).
-    Problem p draws from the PCG64 stream seeded by (seed, p)."""
-    out = []
-    for p in range(count):
-        rng = np.random.default_rng([seed, p])
-        side = int(math.floor(math.exp(rng.uniform(math.log(side_lo), math.log(side_hi)))))
-        side = max(side_lo, min(side_hi, side))
-        k = int(rng.integers(8, 65))
-        pot = rng.uniform(0.0, 1.0, size=(side, side))
-        A = laplacian_2d(side, pot)
-        emax = interval_estimate(side, 2, k, 0.5)
-        m0 = int(math.ceil(1.5 * k))
-        out.append(Problem(f"laplace2d_{p}_{side}^2", A, None, 0.0, emax, m0, ne, ratio,
-                           1000 * seed + p, {"target_count": k}))
-    return out
+    [side_lo, side_hi]; each problem draws a wanted count k ~ U{8..64}.  A
+    random potential this strong pulls many more eigenvalues below the
+    closed-form estimate on large grids, so Emax is placed by measured counts
+    (count_below) until the interval holds about k of them (within
+    [max(8, 3k/4), min(64, 5k/4)]), and Emin just below the lowest eigenvalue
+    (so the contour is not much wider than the part of the spectrum it
+    encloses); M0 = ceil(1.5 count).  Problem p draws from
+    the PCG64 stream seeded by (seed, p).  Large batches are built by a pool of
+    spawned worker processes."""
+    args = [(p, seed, ne, ratio, side_lo, side_hi) for p in range(count)]
+    if count < 32:
+        return [_laplace2d_problem(a) for a in args]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+
+    nw = workers or min(32, os.cpu_count() or 4)
+    with cf.ProcessPoolExecutor(max_workers=nw, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_laplace2d_problem, args, chunksize=4))
 
 
 def laplace3d_grad(side: int = 48, count: int = 64, m0: int = 96, ne: int = 8,

@@ -114,6 +114,49 @@ int feast_scsr_solve(char uplo, int n, const double* a, const int* ia, const int
                      const int* ib, const int* jb, int* fpm, double emin, double emax, int* m0, double* e,
                      double* x, int* m, double* res, double* epsout, int* loop, int* info);
 
+/* One problem of a batch (host memory, caller-owned).  CSR in full storage,
+ * base ia[0] in {0,1}; b/ib/jb all NULL for B = I (then for every problem of
+ * the batch).  x0: column-major n x m0 start subspace, or NULL for a random
+ * block.  1 <= m0 <= min(n, 128). */
+typedef struct feast_problem {
+    int n;
+    const double* a;
+    const int* ia;
+    const int* ja;
+    const double* b;
+    const int* ib;
+    const int* jb;
+    double emin, emax;
+    int m0;
+    const double* x0;
+} feast_problem;
+
+/* Result of one problem (host memory, caller-allocated arrays): e[m0],
+ * x[n*m0] (column-major eigenvectors), res[m0]; info as in the guide's info
+ * table; m eigenvalues found in the interval; loop refinement loops; m0 the
+ * live subspace size; epsout the relative trace change. */
+typedef struct feast_result {
+    int info, m, loop, m0;
+    double epsout;
+    double* e;
+    double* x;
+    double* res;
+} feast_result;
+
+/* Many independent problems of uneven size and interval solved together (the
+ * guide's first level of parallelism, Sec. 2.2: separate search intervals).
+ * One set of filter launches serves all unfinished problems; the COCG steps
+ * and the batched Rayleigh-Ritz sequence replay as captured CUDA graphs; the
+ * rows per work item of the gathering step are picked by timing a few
+ * choices on the batch (cached per size class) unless fpm(51) sets them.
+ * The contour nodes come from fpm(2), fpm(18) and each problem's interval;
+ * fpm(50) defaults to one node per batch.  Each problem starts with a
+ * Rayleigh-Ritz step on its start block.  Returns 0 when every problem ran
+ * (see out[p].info), -101..-104 for a bad argument (-102: problem p invalid,
+ * its out[p].info says why, or some problems have B and others not), -4 on a
+ * CUDA error. */
+int feast_scsr_solve_batched(int np, const feast_problem* probs, int* fpm, feast_result* out);
+
 /* Device workspace, in bytes, that feast_scsr_solve_dev needs for this
  * problem size and these parameters (fpm(2), fpm(42), fpm(50), fpm(51)). */
 size_t feast_scsr_workspace_bytes(int n, int nnz_a, int nnz_b, int m0, const int* fpm);

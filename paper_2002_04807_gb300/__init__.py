@@ -25,6 +25,7 @@ from ._lib import (  # noqa: F401
     feast_reduced_eig_dev,
     feast_residual_dev,
     feast_scsr_solve,
+    feast_scsr_solve_batched,
     feast_scsr_solve_dev,
     feast_scsr_workspace_bytes,
     feast_shifted_spmm_dev,

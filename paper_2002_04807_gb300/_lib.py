@@ -38,7 +38,18 @@ _SIGS = {
     "feast_eig_grad_dev": (_i, [_i, _p, _p, _i, _p, _p, _p, _p]),
     "feast_last_profile": (_i, [_p]),
     "feast_gram_noalloc_dev": (_i, [_i, _i, _p, _p, _p, _p]),
+    "feast_scsr_solve_batched": (_i, [_i, _p, _p, _p]),
 }
+
+
+class _Problem(C.Structure):
+    _fields_ = [("n", _i), ("a", _p), ("ia", _p), ("ja", _p), ("b", _p), ("ib", _p), ("jb", _p),
+                ("emin", _d), ("emax", _d), ("m0", _i), ("x0", _p)]
+
+
+class _Result(C.Structure):
+    _fields_ = [("info", _i), ("m", _i), ("loop", _i), ("m0", _i), ("epsout", _d), ("e", _p), ("x", _p),
+                ("res", _p)]
 
 
 class FeastError(RuntimeError):
@@ -221,6 +232,44 @@ def feast_scsr_solve_dev(n: int, ia, ja, a, ib=None, jb=None, b=None, fpm=None, 
         raise FeastError("feast_scsr_solve_dev: " + feast_last_error())
     k = mm.value
     return FeastResult(info.value, E[:k].copy(), x, res[:k].copy(), M.value, loop.value, eps.value, k, f)
+
+
+def feast_scsr_solve_batched(problems, fpm=None):
+    """Solve many independent problems together.
+
+    problems: list of dicts with keys n, a, ia, ja (CSR, numpy), optional b, ib,
+    jb, emin, emax, m0 and optional x0 (n x m0).  Returns (status, [FeastResult])."""
+    f = _fpm(fpm)
+    keep = []
+    P = (_Problem * len(problems))()
+    R = (_Result * len(problems))()
+    outs = []
+    for k, q in enumerate(problems):
+        n, m0 = int(q["n"]), int(q["m0"])
+        arrs = [np.ascontiguousarray(q["a"], dtype=np.float64), np.ascontiguousarray(q["ia"], dtype=np.int32),
+                np.ascontiguousarray(q["ja"], dtype=np.int32)]
+        if q.get("b") is not None:
+            arrs += [np.ascontiguousarray(q["b"], dtype=np.float64), np.ascontiguousarray(q["ib"], dtype=np.int32),
+                     np.ascontiguousarray(q["jb"], dtype=np.int32)]
+        else:
+            arrs += [None, None, None]
+        x0 = None if q.get("x0") is None else np.asfortranarray(q["x0"], dtype=np.float64)
+        E, X, res = np.zeros(m0), np.zeros((n, m0), order="F"), np.zeros(m0)
+        keep += arrs + [x0, E, X, res]
+        P[k] = _Problem(n, _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]), _ptr(arrs[3]), _ptr(arrs[4]), _ptr(arrs[5]),
+                        float(q["emin"]), float(q["emax"]), m0, _ptr(x0))
+        R[k] = _Result(0, 0, 0, m0, 0.0, _ptr(E), _ptr(X), _ptr(res))
+        outs.append((E, X, res))
+    st = library().feast_scsr_solve_batched(len(problems), C.cast(P, C.c_void_p), _ptr(f), C.cast(R, C.c_void_p))
+    if st == -4:
+        raise FeastError("feast_scsr_solve_batched: " + feast_last_error())
+    results = []
+    for k, (E, X, res) in enumerate(outs):
+        r = R[k]
+        km = r.m0
+        results.append(FeastResult(r.info, E[:km].copy(), np.asfortranarray(X[:, :km]), res[:km].copy(), r.m, r.loop,
+                                    r.epsout, km, f))
+    return st, results
 
 
 # ---------------------------------------------------------------- kernel-level entry points

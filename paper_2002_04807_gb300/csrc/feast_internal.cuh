@@ -53,6 +53,7 @@ struct FiltProb {
     const double* lam;  // Ritz values of the previous Rayleigh-Ritz step [m0]
     const int* mk;      // live subspace columns (device), or nullptr for m0
     int ne;             // number of contour nodes
+    int active;         // 0: problem finished, its items are skipped
 };
 
 // Per-column COCG state (FP64 for stability of the scalar recurrences).
@@ -97,6 +98,7 @@ struct FilterArgs {
     int* iter_max;  // per-problem max iteration reached
     int* groups_left;  // per-problem number of groups still iterating
     unsigned long long* work;  // group-iterations done (one per group per COCG step)
+    const int* kdev;  // if set, the COCG step index is read from here (graph replay)
 };
 
 // ---------------------------------------------------------------- launchers (k_filter.cu)
@@ -107,6 +109,7 @@ cudaError_t launch_filter_init(const FilterArgs& a, bool fp64, const double* R, 
 cudaError_t launch_colstate_init(const FilterArgs& a, int node0, int rii, cudaStream_t s);
 cudaError_t launch_shifted_spmm(const FilterArgs& a, bool fp64, int grid, cudaStream_t s);
 cudaError_t launch_cast_values(const double* src, float* dst, long long n, cudaStream_t s);
+cudaError_t launch_advance(int* kdev, cudaStream_t s);
 cudaError_t launch_fold_dq(const FilterArgs& a, long long max_total, bool fp64, cudaStream_t s);
 cudaError_t launch_pack_csr(int n, const int* ia, const int* ja, const double* av, const int* pp, bool fp64, void* out,
                             cudaStream_t s);
@@ -151,6 +154,38 @@ int reduced_gev_dev(int m, const double* Aq, const double* Bq, double* lam, doub
 // ---------------------------------------------------------------- gradient (k_grad.cu)
 cudaError_t launch_eig_grad(int n, const int* ia, const int* ja, int m, const double* Xr,
                             const double* gw, double* grad, cudaStream_t s);
+
+// ---------------------------------------------------------------- batched Rayleigh-Ritz (k_batch.cu)
+// One entry per problem of a batch; all pointers device; offsets in doubles.
+struct BProb {
+    int n, m;             // rows, subspace columns
+    long long row0;       // first row in the flattened row space of the batch
+    long long q_off;      // offset of the problem's n x m FP64 blocks (row-major)
+    long long c_off;      // offset of its m x m blocks
+    long long gpart_off;  // offset of its Gram split-K partials (gram_ks x m x m)
+    long long w_off;      // offset of its reduced-solver work (6 m*m + 4 m)
+    int l_off;            // offset of its m-vectors (Ritz values, residuals)
+    const int* ia;
+    const int* ja;
+    const double* av;
+    const int* ib;        // B or nullptr for B = I
+    const int* jb;
+    const double* bv;
+    int gram_b0, gram_ks, gram_T;  // Gram blocks: first block, row splits, 64-wide tiles per side
+    int gemm_b0;          // first block of the Ritz-vector product
+    int res_b0;           // first 256-row block of the residual kernel
+    double alpha;         // residual normalisation max(|Emin|, |Emax|)
+    int active;           // 0 once the problem has converged
+};
+cudaError_t launch_b_spmm(const BProb* pr, int np, long long rows, const double* X, double* Y, int useB, cudaStream_t s);
+cudaError_t launch_b_gram(const BProb* pr, int np, int nblocks, int maxm, const double* X, const double* Y, double* part,
+                          double* C, cudaStream_t s);
+cudaError_t launch_b_gemm(const BProb* pr, int np, int nblocks, const double* A, const double* V, double* Out,
+                          cudaStream_t s);
+cudaError_t launch_b_residual(const BProb* pr, int np, int nblocks, const double* X, const double* lam, double* R,
+                              double* part, double* res, cudaStream_t s);
+cudaError_t launch_b_reduced(const BProb* pr, int np, const double* Aq, const double* Bq, double* lam, double* V,
+                             int* mk, double* work, cudaStream_t s);
 
 int num_sms();
 // kernel launches issued by this library (all threads), for launch accounting

@@ -347,8 +347,9 @@ __device__ __forceinline__ void prefetch_item(const FilterArgs& a, long long ite
 // both updated in place, and partial sums of p_k^T q_k (and ||r_0||^2 at k=0).
 // BM: 0 = B is the identity, 1 = B diagonal (values bd), 2 = general CSR B.
 template <typename T, int W, int BM>
-__global__ void __launch_bounds__(kThreads, FEAST_MINB) cocg_step_a(FilterArgs a, int k)
+__global__ void __launch_bounds__(kThreads, FEAST_MINB) cocg_step_a(FilterArgs a, int kk)
 {
+    const int k = a.kdev ? *a.kdev : kk;  // step index (read from the device when replayed in a graph)
     using V = c2_t<T>;
     constexpr int RPP = kThreads / W;  // rows per pass of the CTA
     constexpr int STAGE4 = sizeof(T) == 4 ? kStageEntries / 2 : kStageEntries;
@@ -451,8 +452,9 @@ __global__ void __launch_bounds__(kThreads, FEAST_MINB) cocg_step_a(FilterArgs a
 // partial sums of r^T r and |r|^2; the last item of a group sets beta and
 // the columns' convergence state.
 template <typename T, int W, int BM>
-__global__ void __launch_bounds__(kThreads, FEAST_MINB_B) cocg_step_b(FilterArgs a, int k)
+__global__ void __launch_bounds__(kThreads, FEAST_MINB_B) cocg_step_b(FilterArgs a, int kk)
 {
+    const int k = a.kdev ? *a.kdev : kk;
     using V = c2_t<T>;
     constexpr int RPP = kThreads / W;
     __shared__ double sm[kThreads * 3];
@@ -619,6 +621,7 @@ __global__ void __launch_bounds__(kThreads) filter_init(FilterArgs a, const doub
         const ItemInfo it = item_info(a, item);
         const FiltProb& P = a.probs[it.pi];
         const int g = it.g, rb = it.rb;
+        if (!P.active) continue;
         const int m = g * a.mt + mloc;
         const ColState& cs = a.cs[P.col_off + (size_t)g * W + cl];
         const int live = cs.active;
@@ -674,12 +677,23 @@ __global__ void __launch_bounds__(kThreads) shifted_spmm(FilterArgs a)
     }
 }
 
+// Step counter of graph-replayed COCG chunks: one thread adds one.
+__global__ void k_advance(int* kdev) { *kdev += 1; }
+
+cudaError_t launch_advance(int* kdev, cudaStream_t s)
+{
+    k_advance<<<1, 1, 0, s>>>(kdev);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 // Q += dQ after all node batches of a pass (dQ: FP32 in mixed precision,
 // tiled [group][row][mt] per problem; Q row-major n x m0 per problem).
 template <typename T>
 __global__ void fold_dq(const FiltProb* probs, int nprob, int mt, const T* dQ, double* Q)
 {
     const FiltProb& P = probs[blockIdx.y];
+    if (!P.active) return;
     const long long total = (long long)P.n * P.m0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(t / P.m0), m = (int)(t % P.m0);
