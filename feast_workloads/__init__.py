@@ -8,7 +8,7 @@ Every generator is deterministic: random numbers come from numpy's PCG64
 (``numpy.random.default_rng(seed)``).  Matrices are returned as 0-based CSR
 triples ``(indptr int32, indices int32, data float64)`` with sorted, duplicate
 free rows.  The paper's own test matrix (the 4x4 "helloworld" system of the
-FEAST v4.0 user guide, Sec. 2.3 and its IFEAST variant in Sec. 5) is the only
+FEAST v4.0 user guide, Sec. 2.4 and its IFEAST variant in Sec. 3.5) is the only
 matrix taken from the paper; it stands in for the missing example data sets.
 """
 from __future__ import annotations
@@ -152,7 +152,7 @@ def stencil27_spd(side: int, rng: np.random.Generator) -> CSR:
 
 
 def helloworld_dense() -> np.ndarray:
-    """The 4x4 real symmetric example of the FEAST v4.0 guide (Sec. 2.3),
+    """The 4x4 real symmetric example of the FEAST v4.0 guide (Sec. 2.4),
     eigenvalues {0, 2, 4, 4}."""
     return np.array([[2.0, -1.0, -1.0, 0.0],
                      [-1.0, 3.0, -1.0, -1.0],
@@ -162,7 +162,7 @@ def helloworld_dense() -> np.ndarray:
 
 def helloworld_csr_1based():
     """The same matrix in the guide's 1-based CSR encoding (IFEAST example,
-    Sec. 5): returns (sA, IA, JA) exactly as printed there."""
+    Sec. 3.5): returns (sA, IA, JA) exactly as printed there."""
     sA = np.array([2.0, -1.0, -1.0, -1.0, 3.0, -1.0, -1.0, -1.0, -1.0, 3.0, -1.0, -1.0, -1.0, 2.0])
     IA = np.array([1, 4, 8, 12, 15], dtype=np.int32)
     JA = np.array([1, 2, 3, 1, 2, 3, 4, 1, 2, 3, 4, 2, 3, 4], dtype=np.int32)

@@ -3,18 +3,18 @@
  * for real symmetric sparse problems  A x = lambda B x  (B symmetric positive
  * definite; B = I when no B is given).
  *
- * Method: FEAST v4.0 user guide (Polizzi et al.), Sec. 1.2 "The FEAST
+ * Method: FEAST v4.0 user guide (Polizzi et al.), Sec. 1.1 "The FEAST
  * Algorithm": a subspace iteration that filters a block of M0 vectors with the
  * quadrature of the spectral projector along a half contour around
  * [Emin, Emax] (one shifted solve (z_e B - A) Y_e = RHS per node z_e), then
- * does a Rayleigh-Ritz step on the filtered block.  Sec. 2.2 (tips) describes
+ * does a Rayleigh-Ritz step on the filtered block.  Sec. 3.1 (tips) describes
  * the residual inverse iteration that lets the shifted solves run in single
- * precision; Sec. 3.1 gives the driver arguments; Sec. 5 (IFEAST) the
- * iterative inner solver.  Sec. 5.2 describes the CSR storage.
+ * precision; Sec. 3.2 gives the driver arguments; Sec. 3.5 (IFEAST) the
+ * iterative inner solver.  Sec. 4.1 describes the CSR storage.
  *
  * Conventions shared by every entry point:
  *  - fpm is the 64-entry parameter array of the guide's parameter table
- *    (Sec. 2.2), C indexing fpm[i-1] = fpm(i).  Used entries:
+ *    (Sec. 3.1), C indexing fpm[i-1] = fpm(i).  Used entries:
  *      fpm(1)  0 silent, 1 per-iteration log on stdout, n<0 append to feast<|n|>.log
  *      fpm(2)  Ne, number of half-contour nodes (1..20, 24, 32, 40, 48, 56)
  *      fpm(3)  stopping tolerance 10^-fpm(3) on the relative residual (0..16)
@@ -32,7 +32,7 @@
  *      inner-solver work item; fpm(52) seed of the random start block;
  *      fpm(53) 1 = record per-kernel timings (see feast_last_profile).
  *  - Return value = info (also stored in *info where that argument exists),
- *    codes of the guide's info table (Sec. 2.2): 0 success; warnings 1 (no
+ *    codes of the guide's info table (Sec. 3.1): 0 success; warnings 1 (no
  *    eigenvalue in the interval), 2 (no convergence within fpm(4) loops),
  *    3 (M0 too small: all Ritz values inside); errors 200 (Emin >= Emax),
  *    201 (bad M0), 202 (bad N), 100+i (bad fpm(i)), -(100+i) (bad i-th
@@ -58,7 +58,7 @@
 extern "C" {
 #endif
 
-/* Fill fpm[0..63] with the defaults of the guide's parameter table (Sec. 2.2,
+/* Fill fpm[0..63] with the defaults of the guide's parameter table (Sec. 3.1,
  * "feastinit").  Returns 0. */
 int feast_init(int* fpm);
 
@@ -66,7 +66,7 @@ int feast_init(int* fpm);
  * (empty when none).  The pointer stays valid until the next call. */
 const char* feast_last_error(void);
 
-/* Half-contour Gauss-Legendre nodes and weights (guide Sec. 5.3 "Search
+/* Half-contour Gauss-Legendre nodes and weights (guide Sec. 4.2 "Search
  * contour", fpm(16)=0): z_e = c + r cos(t_e) + i a r sin(t_e),
  * w_e = (omega_e r / 2)(a cos(t_e) + i sin(t_e)), t_e = (pi/2)(1 - x_e),
  * c = (Emin+Emax)/2, r = (Emax-Emin)/2, a = ratio_pct/100, (x_e, omega_e)
@@ -90,10 +90,10 @@ int feast_last_profile(double* out);
 
 /* ---------------------------------------------------------------- drivers */
 
-/* FEAST for a real symmetric CSR problem (guide Sec. 3.1, dfeast_scsrev /
+/* FEAST for a real symmetric CSR problem (guide Sec. 3.2, dfeast_scsrev /
  * dfeast_scsrgv).  All arrays are host memory; the library copies them to the
  * device, runs the whole iteration there and copies the results back.
- *   uplo      'F' full, 'L' lower or 'U' upper triangle stored (Sec. 5.2)
+ *   uplo      'F' full, 'L' lower or 'U' upper triangle stored (Sec. 4.1)
  *   n         order of A and B (> 0)
  *   a, ia, ja CSR of A; ia[0] is the index base (1 as in the guide, or 0);
  *             nnz = ia[n] - ia[0]
@@ -144,7 +144,7 @@ typedef struct feast_result {
 } feast_result;
 
 /* Many independent problems of uneven size and interval solved together (the
- * guide's first level of parallelism, Sec. 2.2: separate search intervals).
+ * guide's first level of parallelism, Sec. 1.1: separate search intervals).
  * One set of filter launches serves all unfinished problems; the COCG steps
  * and the batched Rayleigh-Ritz sequence replay as captured CUDA graphs; the
  * rows per work item of the gathering step are picked by timing a few
@@ -198,7 +198,7 @@ int feast_shifted_spmm_dev(int n, int nnz_a, const int* ia, const int* ja, const
                            const int* ib, const int* jb, const double* b, int nb, const double* z, int m,
                            int fp64, const void* P, void* V, void* stream);
 
-/* One filter pass over all ne nodes (guide Sec. 1.2 quadrature; Sec. 2.2
+/* One filter pass over all ne nodes (guide Sec. 1.1 quadrature; Sec. 3.1
  * residual inverse form):
  *   rii = 0:  Q = sum_e Re(w_e Y_e),                  (z_e B - A) Y_e = R
  *   rii = 1:  Q = X diag(rho(lam)) + sum_e Re(w_e/(z_e - lam_j) Y_e[:,j]),

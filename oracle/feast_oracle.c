@@ -7,18 +7,18 @@
  * not part of the product path, shares no code with it, and must only be called
  * from tests/, from __graft_entry__.smoke() and from bench.py's CPU-baseline leg.
  *
- * The FEAST v4.0 guide describes the method in prose (Sec. 1.2 "The FEAST
- * Algorithm", the fpm table of Sec. 2.2, the argument table of Sec. 3.1 and the
- * tips on residual inverse iteration in Sec. 2.2).  It prints no formulas, so
+ * The FEAST v4.0 guide describes the method in prose (Sec. 1.1 "The FEAST
+ * Algorithm", the fpm table of Sec. 3.1, the argument table of Sec. 3.2 and the
+ * tips on residual inverse iteration in Sec. 3.1).  It prints no formulas, so
  * the steps below are written from the mathematics the guide refers to:
  *   - the spectral projector P = (1/2 pi i) \oint (zB - A)^{-1} B dz over an
  *     ellipse through Emin/Emax (fpm(18) = ratio), symmetric about the real axis,
- *     so only the upper half contour is integrated (guide Sec. 5.3, "Search
+ *     so only the upper half contour is integrated (guide Sec. 4.2, "Search
  *     contour");
  *   - Gauss-Legendre quadrature on that half contour (fpm(16)=0);
  *   - Rayleigh-Ritz on Q = P_quad Y, a dense reduced generalized eigenproblem,
  *     Ritz vectors X = Q V and residuals ||A x - lambda B x|| / ||alpha B x||,
- *     alpha = max(|Emin|,|Emax|) (guide Sec. 3.1, argument `res`);
+ *     alpha = max(|Emin|,|Emax|) (guide Sec. 3.2, argument `res`);
  *   - stop when the largest residual of the pairs inside [Emin,Emax] is below
  *     10^-fpm(3) (fpm(6)=1).
  * Shifted solves are either a banded complex-symmetric LDL^T (no pivoting; the
@@ -541,7 +541,7 @@ long orc_count_below(int n, const int* ip, const int* ix, const double* av,
 
 /* ------------------------------------------------------------------------ */
 /* Relative residuals res_j = ||A x_j - lambda_j B x_j|| / ||alpha B x_j||,
- * alpha = max(|Emin|, |Emax|) (guide Sec. 3.1, argument res). */
+ * alpha = max(|Emin|, |Emax|) (guide Sec. 3.2, argument res). */
 void orc_residuals(int n, const int* ip, const int* ix, const double* av,
                    const int* bip, const int* bix, const double* bv,
                    int m, const double* X, const double* lam, double emin, double emax, double* res)

@@ -1,9 +1,9 @@
 // Host side of libfeast_gb300: argument checks, contour nodes, the device
 // memory plan and the FEAST subspace iteration that drives the kernels.
 //
-// FEAST v4.0 guide: Sec. 1.2 (algorithm), Sec. 2.2 (fpm and info tables,
-// residual inverse iteration and mixed precision tips), Sec. 3.1 (driver
-// arguments), Sec. 5.2 (CSR storage), Sec. 5.3 (search contour).
+// FEAST v4.0 guide: Sec. 1.1 (algorithm), Sec. 3.1 (fpm and info tables,
+// residual inverse iteration and mixed precision tips), Sec. 3.2 (driver
+// arguments), Sec. 4.1 (CSR storage), Sec. 4.2 (search contour).
 //
 // One iteration, all on the device:
 //   filter  : COCG over every (node, column) pair, Q accumulated in FP64

@@ -1,5 +1,5 @@
 // Batched Rayleigh-Ritz for many independent eigenproblems of uneven size
-// (FEAST v4.0 guide, Sec. 1.2: one reduced problem per search interval; the
+// (FEAST v4.0 guide, Sec. 1.1: one reduced problem per search interval; the
 // guide's parallelism level L1 runs separate intervals independently).
 //
 // Every kernel here covers all problems of a batch in one launch: rows of all

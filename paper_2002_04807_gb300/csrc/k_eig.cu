@@ -1,5 +1,5 @@
 // Reduced dense eigensolver of the Rayleigh-Ritz step (FEAST v4.0 guide,
-// Sec. 1.2: the reduced problem is a small dense generalized symmetric
+// Sec. 1.1: the reduced problem is a small dense generalized symmetric
 // eigenproblem A_Q v = lambda B_Q v, solved in FP64).
 //
 // Symmetric eigen-decomposition: two-sided cyclic Jacobi with the

@@ -2,7 +2,7 @@
 // COCG for the complex symmetric systems (z_e B - A) y = rhs, and the fused
 // accumulation of the quadrature sum into the FP64 subspace block Q.
 //
-// Method (FEAST v4.0 guide, Sec. 1.2 and the tips of Sec. 2.2): for the Ne
+// Method (FEAST v4.0 guide, Sec. 1.1 and the tips of Sec. 3.1): for the Ne
 // half-contour nodes z_e with weights w_e, the filter is
 //   Q = sum_e Re( w_e (z_e B - A)^{-1} B Y )                       (first pass)
 // and, in the residual-inverse form used by every later pass,

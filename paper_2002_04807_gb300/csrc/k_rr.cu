@@ -1,5 +1,5 @@
-// Rayleigh-Ritz kernels, all FP64 (FEAST v4.0 guide Sec. 1.2: the reduced
-// problem is built from the filtered subspace; Sec. 3.1: residuals
+// Rayleigh-Ritz kernels, all FP64 (FEAST v4.0 guide Sec. 1.1: the reduced
+// problem is built from the filtered subspace; Sec. 3.2: residuals
 // ||A x - lambda B x|| / ||alpha B x||, alpha = max(|Emin|, |Emax|)).
 //
 // Blocks of vectors are row-major n x m (each row's m values contiguous), so a
