@@ -18,6 +18,7 @@
 //   b_reduced     the reduced generalized eigenproblem of one problem per CTA
 //                 (m <= 128): two cyclic Jacobi decompositions in shared and
 //                 global memory, rounds synchronised with __syncthreads
+#include "chol.cuh"
 #include "feast_internal.cuh"
 
 namespace feast {
@@ -401,8 +402,10 @@ __device__ void cta_jacobi(int m, double* A, double* V, CtaRot& R)
 }
 
 // Reduced generalized problem of one problem per CTA (m <= 128): scale by
-// diag(B_Q)^{-1/2}, Jacobi on B~, keep d > 1e-14 max d, S = D U_k d_k^{-1/2},
-// C = S^T A~ S (sentinel on dropped directions), Jacobi on C, V = S W; lam
+// D = diag(B_Q)^{-1/2}; S = D L^{-T} from B~ = L L^T when the Cholesky
+// factor is accepted, else Jacobi on B~, keep d > 1e-14 max d,
+// S = D U_k d_k^{-1/2} (sentinel on dropped directions); C = S^T A~ S,
+// Jacobi on C, V = S W; lam
 // ascending (live values first), mk live count.  work: 6 m*m + 4 m doubles.
 __global__ void __launch_bounds__(kRedThreads) b_reduced(const BProb* pr, const double* __restrict__ Aq,
                                                           const double* __restrict__ Bq, double* __restrict__ lam,
@@ -433,17 +436,30 @@ __global__ void __launch_bounds__(kRedThreads) b_reduced(const BProb* pr, const 
         At[idx] = 0.5 * (aq[i * m + j] + aq[j * m + i]);
         if (j == 0) dsc[i] = di;
     }
+    for (int idx = threadIdx.x; idx < (int)mm; idx += blockDim.x) U[idx] = Bt[idx];
     __syncthreads();
-    cta_jacobi(m, Bt, U, R);
-    __syncthreads();
-    double dmax = 0.0;
-    for (int i = 0; i < m; ++i) dmax = fmax(dmax, Bt[i * m + i]);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) d[i] = Bt[i * m + i];
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < (int)mm; idx += blockDim.x) {
-        const int r = idx / m, c = idx % m;
-        const bool keep = dmax > 0.0 && d[c] > 1e-14 * dmax;
-        S[idx] = keep ? dsc[r] * U[idx] / sqrt(d[c]) : 0.0;
+    double* xd = d + m;
+    const bool chol = cta_chol_inv(m, U, xd, d + 2 * m, R.red);
+    int live = m;
+    if (chol) {  // S = D L^{-T}
+        for (int idx = threadIdx.x; idx < (int)mm; idx += blockDim.x) {
+            const int r = idx / m, c = idx % m;
+            S[idx] = c > r ? dsc[r] * U[idx] : (c == r ? dsc[r] * xd[r] : 0.0);
+        }
+    } else {
+        cta_jacobi(m, Bt, U, R);
+        __syncthreads();
+        double dmax = 0.0;
+        for (int i = 0; i < m; ++i) dmax = fmax(dmax, Bt[i * m + i]);
+        for (int i = threadIdx.x; i < m; i += blockDim.x) d[i] = Bt[i * m + i];
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < (int)mm; idx += blockDim.x) {
+            const int r = idx / m, c = idx % m;
+            const bool keep = dmax > 0.0 && d[c] > 1e-14 * dmax;
+            S[idx] = keep ? dsc[r] * U[idx] / sqrt(d[c]) : 0.0;
+        }
+        live = 0;
+        for (int c = 0; c < m; ++c) live += (dmax > 0.0 && d[c] > 1e-14 * dmax);
     }
     __syncthreads();
     // T = A~ S into U, then C = S^T T
@@ -463,10 +479,12 @@ __global__ void __launch_bounds__(kRedThreads) b_reduced(const BProb* pr, const 
         C[c * m + r] = s;
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < m; c += blockDim.x) {
-        bool zero = true;
-        for (int r = 0; r < m && zero; ++r) zero = S[r * m + c] == 0.0;
-        if (zero) C[c * m + c] = kSentinelB;
+    if (!chol) {
+        for (int c = threadIdx.x; c < m; c += blockDim.x) {
+            bool zero = true;
+            for (int r = 0; r < m && zero; ++r) zero = S[r * m + c] == 0.0;
+            if (zero) C[c * m + c] = kSentinelB;
+        }
     }
     __syncthreads();
     cta_jacobi(m, C, Wv, R);
@@ -488,11 +506,7 @@ __global__ void __launch_bounds__(kRedThreads) b_reduced(const BProb* pr, const 
             vo[r * m + rank] = s;
         }
     }
-    if (threadIdx.x == 0) {
-        int k = 0;
-        for (int c = 0; c < m; ++c) k += (dmax > 0.0 && d[c] > 1e-14 * dmax);
-        mk[blockIdx.x] = k;
-    }
+    if (threadIdx.x == 0) mk[blockIdx.x] = live;
 }
 
 // ---------------------------------------------------------------- launchers

@@ -210,19 +210,42 @@ def test_sym_eig_degenerate_and_diagonal(pkg):
     assert sw <= 1 and np.array_equal(lam2.cpu().numpy(), np.sort(d))
 
 
-def test_reduced_eig_matches_oracle(pkg):
-    rng = np.random.default_rng(3)
-    m = 40
+def _reduced_case(kind, m, rng):
     a = rng.standard_normal((m, m)); a = a + a.T
-    g = rng.standard_normal((m, m)); b = g @ g.T + 0.5 * np.eye(m)
+    if kind == "random":
+        g = rng.standard_normal((m, m)); b = g @ g.T + 0.5 * np.eye(m)
+    elif kind == "near_identity":  # a filtered subspace after a few loops: B_Q = D (I + E) D
+        e = 1e-3 * rng.standard_normal((m, m)); e = e + e.T
+        dg = rng.uniform(1e-4, 1.0, m)
+        b = dg[:, None] * (np.eye(m) + e) * dg[None, :]
+        a = dg[:, None] * (np.diag(np.sort(rng.uniform(-1, 1, m))) + 1e-3 * a) * dg[None, :]
+    else:  # full rank, condition 1e9: the Cholesky factor is rejected (||L^-1||_F^2 >= 1e9)
+        qm, _ = np.linalg.qr(rng.standard_normal((m, m)))
+        b = qm @ np.diag(np.logspace(0, -9, m)) @ qm.T
+        b = 0.5 * (b + b.T)
+    return a, b
+
+
+@pytest.mark.parametrize("kind,m", [("random", 40), ("random", 150), ("random", 200), ("near_identity", 150),
+                                    ("near_identity", 200), ("ill", 60)])
+def test_reduced_eig_matches_oracle(pkg, kind, m):
+    """Both routes of the reduced generalized solver (Cholesky factor in
+    shared or global memory; Jacobi on B~ when the factor is rejected)."""
+    rng = np.random.default_rng(3 + m)
+    a, b = _reduced_case(kind, m, rng)
     lam = torch.zeros(m, dtype=torch.float64, device="cuda")
     V = torch.zeros((m, m), dtype=torch.float64, device="cuda")
     mk = pkg.feast_reduced_eig_dev(m, dev(a), dev(b), lam, V)
     info, lo, Vo = O.reduced_gev(a, b)
     assert mk == len(lo) == m
-    assert np.abs(lam.cpu().numpy() - lo).max() < 1e-11 * np.abs(lo).max()
+    lg = lam.cpu().numpy()
     Vg = V.cpu().numpy()
+    if kind == "ill":  # eigenvalue perturbations of order eps * cond(B) = 2e-7 of the largest
+        assert np.abs(lg - lo).max() < 1e-6 * np.abs(lo).max()
+        return
+    assert np.abs(lg - lo).max() < 1e-11 * np.abs(lo).max()
     assert np.abs(Vg.T @ b @ Vg - np.eye(m)).max() < 1e-11
+    assert np.abs(a @ Vg - (b @ Vg) * lg).max() < 1e-11 * np.abs(lo).max() * np.abs(b).max()
 
 
 def test_reduced_eig_rank_deficient(pkg):
