@@ -33,11 +33,8 @@
 // for two extra streams is faster even though it moves more bytes.
 // Rows of a CSR matrix are stored as packed (column, value) entries padded to
 // chunks of 8 with zero-weight entries on the diagonal, so a row is gathered
-// with unpredicated, fully unrolled loads: 8 (or 16) independent row-segment
-// loads in flight per thread.  Before working on an item, a CTA asks the TMA
-// engine to prefetch into L2 the tile rows of the item it will take next
-// (cp.async.bulk.prefetch), so the gathers of the current item hit L2 instead
-// of waiting on DRAM row by row.
+// with unpredicated, fully unrolled loads; step A gathers two rows per pass,
+// 16 independent row-segment loads in flight per thread.
 // Reductions are deterministic: fixed per-thread order, fixed block order;
 // each CTA accumulates its items of a group into its own slot, and whichever
 // CTA finishes the group's last item sums the slots in CTA order.
@@ -50,14 +47,14 @@ static constexpr int kPartStride = 4;
 static constexpr int kChunk = 8;  // padded CSR chunk (entries)
 static constexpr int kStageEntries = 2048;  // packed entries of one item staged in shared memory
 static constexpr int kMaxRB = 512;  // rows per work item, at most
-#ifndef FEAST_PREFETCH
-#define FEAST_PREFETCH 1
-#endif
 #ifndef FEAST_MINB
-#define FEAST_MINB 4
+#define FEAST_MINB 3
 #endif
 #ifndef FEAST_MINB_B
 #define FEAST_MINB_B 6
+#endif
+#ifndef FEAST_A_ROWS2
+#define FEAST_A_ROWS2 1
 #endif
 
 __device__ __forceinline__ int find_prob(const FiltProb* probs, int nprob, long long item)
@@ -75,13 +72,6 @@ template <int W>
 __device__ __forceinline__ unsigned seg_mask(int sub)
 {
     return W == 32 ? 0xffffffffu : (((1u << W) - 1u) << (sub * W));
-}
-
-// TMA bulk prefetch of a contiguous range into L2 (16-byte aligned, size a
-// multiple of 16 bytes).
-__device__ __forceinline__ void l2_prefetch(const void* ptr, unsigned bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ptr), "r"(bytes) : "memory");
 }
 
 // ---------------------------------------------------------------- padded CSR chunks
@@ -132,6 +122,35 @@ template <> __device__ __forceinline__ void load_chunk<double, false>(const int4
     }
 }
 
+// Column indices and values of a shared-memory chunk, read separately.  The
+// value read is volatile so that it is not merged with the index read and
+// issued before the gathers that the indices feed.
+template <typename T> __device__ __forceinline__ void load_cols(const int4* ent, int c, int (&j)[kChunk]);
+template <> __device__ __forceinline__ void load_cols<float>(const int4* ent, int c, int (&j)[kChunk])
+{
+    const int2* q = (const int2*)ent + c;
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) j[u] = q[u].x;
+}
+template <> __device__ __forceinline__ void load_cols<double>(const int4* ent, int c, int (&j)[kChunk])
+{
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) j[u] = ent[c + u].x;
+}
+template <typename T> __device__ __forceinline__ void load_vals(const int4* ent, int c, T (&a)[kChunk]);
+template <> __device__ __forceinline__ void load_vals<float>(const int4* ent, int c, float (&a)[kChunk])
+{
+    const volatile int2* q = (const volatile int2*)ent + c;
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) a[u] = __int_as_float(q[u].y);
+}
+template <> __device__ __forceinline__ void load_vals<double>(const int4* ent, int c, double (&a)[kChunk])
+{
+    const volatile int4* q = (const volatile int4*)ent + c;
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u) a[u] = __hiloint2double(q[u].w, q[u].z);
+}
+
 // ax = sum a_k x[j_k] (and with UPD ap = sum a_k p[j_k]) over the padded row
 // entries [c0, c1) of ent.  The row's own values x[i] (and p[i]) come out of
 // the same loads when the row has an entry in column i (its diagonal, or a
@@ -172,6 +191,53 @@ __device__ __forceinline__ void row_gather(const int4* __restrict__ ent, int c0,
                 ap.x = fma(av[u], pv[u].x, ap.x);
                 ap.y = fma(av[u], pv[u].y, ap.y);
                 if (j[u] == i) po = pv[u];
+            }
+        }
+    }
+}
+
+// Two rows a and b gathered together from shared-memory entries: the chunks
+// of both rows are loaded before either is used, so each thread keeps twice
+// the row segments in flight.  Row b is absent when nb == 0.  The column
+// indices are dead once the loads are issued (the caller reads the rows' own
+// values separately, from L1).
+template <typename T, int W>
+__device__ __forceinline__ void row_gather2(const int4* ent, int ca, int na, int cb, int nb,
+                                            const c2_t<T>* __restrict__ xl, c2_t<T>& axa, c2_t<T>& axb)
+{
+    using V = c2_t<T>;
+    axa = cmk<V>(T(0), T(0));
+    axb = cmk<V>(T(0), T(0));
+    const int nmax = na > nb ? na : nb;
+    for (int off = 0; off < nmax; off += kChunk) {
+        const bool ha = off < na, hb = off < nb;
+        V xa[kChunk], xb[kChunk];
+        {
+            int ja[kChunk], jb[kChunk];
+            if (ha) load_cols<T>(ent, ca + off, ja);
+            if (hb) load_cols<T>(ent, cb + off, jb);
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u) xa[u] = ha ? __ldg(xl + (size_t)ja[u] * W) : cmk<V>(T(0), T(0));
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u) xb[u] = hb ? __ldg(xl + (size_t)jb[u] * W) : cmk<V>(T(0), T(0));
+        }
+        // the values are read after the loads are issued, so they need no
+        // registers while the loads are in flight
+        T aa[kChunk], ab[kChunk];
+        if (ha) {
+            load_vals<T>(ent, ca + off, aa);
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u) {
+                axa.x = fma(aa[u], xa[u].x, axa.x);
+                axa.y = fma(aa[u], xa[u].y, axa.y);
+            }
+        }
+        if (hb) {
+            load_vals<T>(ent, cb + off, ab);
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u) {
+                axb.x = fma(ab[u], xb[u].x, axb.x);
+                axb.y = fma(ab[u], xb[u].y, axb.y);
             }
         }
     }
@@ -237,18 +303,37 @@ __device__ __forceinline__ void block_partials(T (&v)[NV], double* sm, double* s
 }
 
 // Called by all threads of the CTA that finished the group's last item: sums
-// the group's nslot CTA slots in order into red[cl*kPartStride + q] and
-// zeroes the slots for the next launch.
+// the slots of this launch's CTAs (slot b belongs to CTA b, b < gridDim.x <=
+// nslot) in order into red[cl*kPartStride + q] and zeroes them for the next
+// launch.  Eight slots' loads are issued before any is summed or zeroed, so
+// the pass over the slots costs a few L2 round trips, not one per slot.
 template <int W, int NV>
 __device__ __forceinline__ void group_reduce(double* slots, int nslot, double* sm, double* red)
 {
     constexpr int SEGS = kThreads / W;
+    constexpr int U = 8;
     const int tid = threadIdx.x;
     const int cl = tid % W, seg = tid / W;
+    const int nb = min(nslot, (int)gridDim.x);
     double s[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) s[q] = 0.0;
-    for (int b = seg; b < nslot; b += SEGS) {
+    int b = seg;
+    for (; b + (U - 1) * SEGS < nb; b += U * SEGS) {
+        double v[U][NV];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) v[u][q] = __ldcg(slots + ((size_t)(b + u * SEGS) * W + cl) * kPartStride + q);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                s[q] += v[u][q];
+                slots[((size_t)(b + u * SEGS) * W + cl) * kPartStride + q] = 0.0;
+            }
+    }
+    for (; b < nb; b += SEGS) {
         double* src = slots + ((size_t)b * W + cl) * kPartStride;
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
@@ -325,22 +410,6 @@ __device__ __forceinline__ ItemInfo item_info_b(const FilterArgs& a, long long i
     return t;
 }
 
-// L2 prefetch of the tile rows of `item` in up to two block vectors.
-template <typename V, int W>
-__device__ __forceinline__ void prefetch_item(const FilterArgs& a, long long item, const void* v0, const void* v1)
-{
-    if (item >= a.nitems || threadIdx.x >= 2) return;
-    const ItemInfo t = item_info(a, item);
-    const FiltProb& P = a.probs[t.pi];
-    if (a.grp_done[P.grp_off + t.g]) return;
-    const int row0 = t.rb * a.RB;
-    const int rows = min(a.RB, P.n - row0);
-    if (rows <= 0) return;
-    const size_t off = (size_t)P.vec_off + (size_t)t.g * P.n * W + (size_t)row0 * W;
-    const void* base = threadIdx.x == 0 ? v0 : v1;
-    if (base) l2_prefetch((const V*)base + off, (unsigned)(rows * W * sizeof(V)));
-}
-
 // ---------------------------------------------------------------- kernel A
 // s = (zB - A) r_k gathered over the matrix rows; then, per own row,
 // p_k = r_k + beta_k p_{k-1}, q_k = s + beta_k q_{k-1} (= (zB - A) p_k),
@@ -382,19 +451,9 @@ __global__ void __launch_bounds__(kThreads, FEAST_MINB) cocg_step_a(FilterArgs a
         const int row1 = min(n, row0 + a.RB);
         const int4* gent;
         const bool staged = stage_rows<T>(P.app, P.apk, row0, row1, s_pp, s_ent, gent);
-        for (int i = row0 + rowslot; i < row1; i += RPP) {
-            // own-row streams first, so their loads overlap the gather
-            V po = cmk<V>(T(0), T(0)), qo = cmk<V>(T(0), T(0));
-            if (use_p) {
-                po = pl_[(size_t)i * W];
-                qo = ql_[(size_t)i * W];
-            }
-            const int c0 = s_pp[i - row0], c1 = s_pp[i - row0 + 1];
-            V ar, unused, ri, unused2;
-            bool own;
-            if (staged) row_gather<T, W, false, true>(s_ent, c0, c1, i, rl_, nullptr, false, ar, unused, ri, unused2, own);
-            else row_gather<T, W, false, false>(gent, c0, c1, i, rl_, nullptr, false, ar, unused, ri, unused2, own);
-            if (!own) ri = __ldg(rl_ + (size_t)i * W);
+        // p_k, q_k of row i from the gathered s = A r, the own value r_i and
+        // the previous p, q of the row
+        auto finish = [&](int i, V ri, V ar, V po, V qo) {
             V bx = ri;
             if (BM == 1) {
                 const T b = ((const T*)P.bd)[i];
@@ -412,6 +471,46 @@ __global__ void __launch_bounds__(kThreads, FEAST_MINB) cocg_step_a(FilterArgs a
             acc[0] = fma(pi_.x, qi.x, fma(-pi_.y, qi.y, acc[0]));
             acc[1] = fma(pi_.x, qi.y, fma(pi_.y, qi.x, acc[1]));
             if (first) acc[2] = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[2]));
+        };
+        const V zero = cmk<V>(T(0), T(0));
+        if (FEAST_A_ROWS2 && staged) {
+            // two rows per pass, every load of both issued before any use
+            for (int i0 = row0 + rowslot; i0 < row1; i0 += 2 * RPP) {
+                const int i1 = i0 + RPP;
+                const bool ok1 = i1 < row1;
+                V po0 = zero, qo0 = zero, po1 = zero, qo1 = zero;
+                if (use_p) {
+                    po0 = pl_[(size_t)i0 * W];
+                    qo0 = ql_[(size_t)i0 * W];
+                    if (ok1) {
+                        po1 = pl_[(size_t)i1 * W];
+                        qo1 = ql_[(size_t)i1 * W];
+                    }
+                }
+                const int ca = s_pp[i0 - row0], na = s_pp[i0 - row0 + 1] - ca;
+                const int cb = ok1 ? s_pp[i1 - row0] : 0, nb = ok1 ? s_pp[i1 - row0 + 1] - cb : 0;
+                V ar0, ar1;
+                row_gather2<T, W>(s_ent, ca, na, cb, nb, rl_, ar0, ar1);
+                const V ri0 = __ldg(rl_ + (size_t)i0 * W);
+                const V ri1 = ok1 ? __ldg(rl_ + (size_t)i1 * W) : zero;
+                finish(i0, ri0, ar0, po0, qo0);
+                if (ok1) finish(i1, ri1, ar1, po1, qo1);
+            }
+        } else {
+            for (int i = row0 + rowslot; i < row1; i += RPP) {
+                V po = zero, qo = zero;
+                if (use_p) {
+                    po = pl_[(size_t)i * W];
+                    qo = ql_[(size_t)i * W];
+                }
+                const int c0 = s_pp[i - row0], c1 = s_pp[i - row0 + 1];
+                V ar, unused, ri = zero, unused2;
+                bool own;
+                if (staged) row_gather<T, W, false, true>(s_ent, c0, c1, i, rl_, nullptr, false, ar, unused, ri, unused2, own);
+                else row_gather<T, W, false, false>(gent, c0, c1, i, rl_, nullptr, false, ar, unused, ri, unused2, own);
+                if (!own) ri = __ldg(rl_ + (size_t)i * W);
+                finish(i, ri, ar, po, qo);
+            }
         }
         double* slots = a.part + (size_t)(P.grp_off + g) * a.nslot * W * kPartStride;
         block_partials<W, 3>(acc, sm, slots + (size_t)blockIdx.x * W * kPartStride);
