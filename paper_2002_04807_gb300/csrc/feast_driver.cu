@@ -176,7 +176,8 @@ struct Plan {
     bool fp64 = false, hasB = false;
     int nnzA = 0, nnzB = 0;
     int ksplit = 1;
-    int nslot = 1;  // upper bound of the COCG grid (partial-sum slots per group)
+    int nslot = 1;  // partial-sum slots per group (item slots + bucket slots)
+    int nbk = 1;    // bucket counters per group
     size_t gpart = 0, rpart = 0;
 };
 
@@ -185,6 +186,7 @@ struct Bufs {
     ColState* cs = nullptr;
     double* part = nullptr;
     unsigned* grp_count = nullptr;
+    unsigned* bk_count = nullptr;
     int* grp_done = nullptr;
     int* iter_max = nullptr;  // [nbatch]
     int* groups_left = nullptr;
@@ -226,12 +228,13 @@ Plan make_plan(int n, int nnzA, int nnzB, int m0, const int* fpm, bool filter_on
     }
     P.nbatch = (P.ne + P.nbp - 1) / P.nbp;
     P.RB = fpm[50] > 0 ? std::min(fpm[50], 512) : 128;
-    P.nslot = num_sms() * 8;
     P.nrb = (n + P.RB - 1) / P.RB;
     P.nitems = (long long)P.G * P.nrb;
     P.RBb = 512;
     P.nrb_b = (n + P.RBb - 1) / P.RBb;
     P.nitems_b = (long long)P.G * P.nrb_b;
+    P.nslot = std::max(part_slots(P.nrb), part_slots(P.nrb_b));
+    P.nbk = std::max(part_buckets(P.nrb), part_buckets(P.nrb_b));
     if (!filter_only) {
         P.gpart = gram_partial_doubles(n, m0, &P.ksplit, num_sms());
         P.rpart = residual_partial_doubles(n, m0);
@@ -263,6 +266,7 @@ size_t carve(const Plan& P, void* base, Bufs& B, bool filter_only = false)
     B.cs = c.take<ColState>((size_t)P.G * P.W);
     B.part = c.take<double>((size_t)P.G * P.nslot * P.W * 4);
     B.grp_count = c.take<unsigned>(P.G);
+    B.bk_count = c.take<unsigned>((size_t)P.G * P.nbk);
     B.grp_done = c.take<int>(P.G);
     B.iter_max = c.take<int>(P.nbatch);
     B.groups_left = c.take<int>(1);
@@ -425,6 +429,8 @@ int filter_pass(const Plan& P, Bufs& B, int rii, const double* R, const double* 
     fa.cs = B.cs;
     fa.part = B.part;
     fa.grp_count = B.grp_count;
+    fa.bk_count = B.bk_count;
+    fa.nbk = P.nbk;
     fa.grp_done = B.grp_done;
     fa.Q = B.Q;
     fa.dQ = B.dQ;
@@ -433,17 +439,17 @@ int filter_pass(const Plan& P, Bufs& B, int rii, const double* R, const double* 
     fa.work = B.work;
     int grid_a = 1, grid_b = 1;
     filter_grids(P.fp64, P.W, &grid_a, &grid_b);
-    grid_a = (int)std::min<long long>(std::min(grid_a, P.nslot), P.nitems);
-    grid_b = (int)std::min<long long>(std::min(grid_b, P.nslot), P.nitems_b);
+    grid_a = (int)std::min<long long>(grid_a, P.nitems);
+    grid_b = (int)std::min<long long>(grid_b, P.nitems_b);
     const int grid = std::max(grid_a, grid_b);  // filter_init
-    fa.nslot = grid;
+    fa.nslot = P.nslot;
     CK(cudaMemsetAsync(B.iter_max, 0, sizeof(int) * P.nbatch, s));
     int left = P.G;
     for (int b = 0; b < P.nbatch; ++b) {
         fa.iter_max = B.iter_max + b;
         CK(cudaMemsetAsync(B.grp_count, 0, sizeof(unsigned) * P.G, s));
+        CK(cudaMemsetAsync(B.bk_count, 0, sizeof(unsigned) * (size_t)P.G * P.nbk, s));
         CK(cudaMemsetAsync(B.grp_done, 0, sizeof(int) * P.G, s));
-        CK(cudaMemsetAsync(B.part, 0, sizeof(double) * (size_t)P.G * grid * P.W * 4, s));
         CK(cudaMemcpyAsync(B.groups_left, &left, sizeof(int), cudaMemcpyHostToDevice, s));
         CK(launch_colstate_init(fa, b * P.nbp, rii, s));
         CK(launch_filter_init(fa, P.fp64, R, X, rii, b == 0, grid, s));
@@ -1310,7 +1316,14 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
     }
     int ga = 1, gb = 1;
     filter_grids(fp64, W, &ga, &gb);
-    const int nslot = std::max(ga, gb);
+    // partial-sum slots for the smallest row block the tuner may pick
+    const int rb_min = fpm[50] > 0 ? std::min(fpm[50], 512) : 64;
+    int nslot = 1, nbk = 1;
+    for (int p = 0; p < np; ++p) {
+        const int nrb_max = (probs[p].n + rb_min - 1) / rb_min;
+        nslot = std::max(nslot, std::max(part_slots(nrb_max), part_slots(fpv[p].nrb_b)));
+        nbk = std::max(nbk, std::max(part_buckets(nrb_max), part_buckets(fpv[p].nrb_b)));
+    }
     // ---- device memory: one allocation carved in place
     DevMem dm;
     Bump bump;
@@ -1334,6 +1347,7 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
         (void)bump.take<char>(vec * csz * 3);
         (void)bump.take<ColState>(colo);
         (void)bump.take<double>((size_t)grpo * nslot * W * 4);
+        (void)bump.take<unsigned>((size_t)grpo * nbk);
         (void)bump.take<unsigned>(grpo);
         (void)bump.take<int>(grpo);
         (void)bump.take<int>((size_t)nbatch * np);
@@ -1375,6 +1389,7 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
     char* d_vec = bump.take<char>(vec * csz * 3);
     ColState* d_cs = bump.take<ColState>(colo);
     double* d_part = bump.take<double>((size_t)grpo * nslot * W * 4);
+    unsigned* d_bkcount = bump.take<unsigned>((size_t)grpo * nbk);
     unsigned* d_gcount = bump.take<unsigned>(grpo);
     int* d_gdone = bump.take<int>(grpo);
     int* d_itmax = bump.take<int>((size_t)nbatch * np);
@@ -1522,6 +1537,9 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
     fa.cs = d_cs;
     fa.part = d_part;
     fa.grp_count = d_gcount;
+    fa.bk_count = d_bkcount;
+    fa.nbk = nbk;
+    fa.nslot = nslot;
     fa.grp_done = d_gdone;
     fa.Q = d_Q;
     fa.dQ = d_dq;
@@ -1539,7 +1557,6 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
         fa.nitems = nitems;
         fa.nitems_b = nitems_b;
         fa.RB = RB;
-        fa.nslot = g_i;
     };
     std::vector<int> gdone(grpo), gleft(np);
     std::vector<char> done(np, 0);
@@ -1595,8 +1612,8 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
         }
         if (!cached) {
             { const int sg = set_groups(); if (sg) return sg; }
-            CK(cudaMemsetAsync(d_part, 0, sizeof(double) * (size_t)grpo * nslot * W * 4, s));
             CK(cudaMemsetAsync(d_gcount, 0, sizeof(unsigned) * grpo, s));
+            CK(cudaMemsetAsync(d_bkcount, 0, sizeof(unsigned) * (size_t)grpo * nbk, s));
             CK(launch_colstate_init(fa, 0, 0, s));
             float best = 1e30f;
             int best_rb = 128;
@@ -1706,7 +1723,7 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
         grids(g_a, g_b, g_i);
         for (int bt = 0; bt < nbatch; ++bt) {
             CK(cudaMemsetAsync(d_gcount, 0, sizeof(unsigned) * grpo, s));
-            CK(cudaMemsetAsync(d_part, 0, sizeof(double) * (size_t)grpo * g_i * W * 4, s));
+            CK(cudaMemsetAsync(d_bkcount, 0, sizeof(unsigned) * (size_t)grpo * nbk, s));
             { const int sg = set_groups(); if (sg) return sg; }
             CK(cudaMemsetAsync(d_k, 0, sizeof(int), s));
             CK(launch_colstate_init(fa, bt * nbp, 1, s));

@@ -72,6 +72,14 @@ struct ColState {
     int status;     // 0 ok, 1 converged, 2 breakdown
 };
 
+// Partial sums of the COCG dot products: every work item writes its own slot
+// of kPartStride x W doubles; buckets of kPartBucket consecutive items are
+// summed by the CTA that completes the bucket, and the group total by the CTA
+// that completes the last bucket, always in item order (deterministic).
+constexpr int kPartBucket = 32;
+__host__ __device__ inline int part_buckets(int nrb) { return (nrb + kPartBucket - 1) / kPartBucket; }
+__host__ __device__ inline int part_slots(int nrb) { return nrb + part_buckets(nrb); }
+
 struct FilterArgs {
     const FiltProb* probs;
     int nprob;
@@ -84,13 +92,15 @@ struct FilterArgs {
     long long nitems_b;  // work items of the streaming step
     int hasB;       // 1 when the problems have a B matrix (all or none)
     int bmode;      // 0: B = I, 1: B diagonal, 2: general B (same for all problems)
-    int nslot;      // partial-sum slots per group = grid size of the COCG launches
+    int nslot;      // partial-sum slots per group, >= part_slots(nrb) and part_slots(nrb_b) of every problem
+    int nbk;        // bucket counters per group, >= part_buckets(nrb) and part_buckets(nrb_b)
     void* r;        // residual block vectors (complex T)
     void* p0;       // search directions, ping
     void* p1;       // search directions, pong
     ColState* cs;   // per-column state
-    double* part;   // partial sums, [group][nslot][W][4], zero between launches
-    unsigned* grp_count;  // per-group finished-item counters
+    double* part;   // partial sums, [group][nslot][4][W]: item slots, then bucket slots
+    unsigned* bk_count;   // per-group, per-bucket finished-item counters [group][nbk], zero between launches
+    unsigned* grp_count;  // per-group finished-bucket counters, zero between launches
     int* grp_done;  // per-group "no active column" flags
     double* Q;      // FP64 filter accumulator (row-major n x m0 per problem)
     void* dQ;       // per-pass accumulator of the quadrature sum, filter precision, [group][row][mt] tiles

@@ -36,8 +36,11 @@
 // with unpredicated, fully unrolled loads; step A gathers two rows per pass,
 // 16 independent row-segment loads in flight per thread.
 // Reductions are deterministic: fixed per-thread order, fixed block order;
-// each CTA accumulates its items of a group into its own slot, and whichever
-// CTA finishes the group's last item sums the slots in CTA order.
+// every work item writes its own partial-sum slot, the CTA that completes a
+// bucket of 32 consecutive items sums them into a bucket slot, and the CTA
+// that completes a group's last bucket sums the bucket slots, each in item
+// order.  No CTA has to read more than 64 slots, so no single CTA carries a
+// long reduction at the end of a launch.
 #include "feast_internal.cuh"
 
 namespace feast {
@@ -51,7 +54,7 @@ static constexpr int kMaxRB = 512;  // rows per work item, at most
 #define FEAST_MINB 3
 #endif
 #ifndef FEAST_MINB_B
-#define FEAST_MINB_B 6
+#define FEAST_MINB_B 5
 #endif
 #ifndef FEAST_A_ROWS2
 #define FEAST_A_ROWS2 1
@@ -279,9 +282,11 @@ __device__ __forceinline__ bool stage_rows(const int* __restrict__ pp, const voi
 
 // ---------------------------------------------------------------- reductions
 // Block-wide reduction of NV per-thread values for each of the W lane columns,
-// added to this CTA's slot of the group (slot[cl][0..NV)).  Fixed order.
+// written to the work item's slot.  A slot holds kPartStride rows of W
+// doubles (slot[q * W + cl]), so one value of every lane is one coalesced
+// row.  Fixed order.
 template <int W, int NV, typename T>
-__device__ __forceinline__ void block_partials(T (&v)[NV], double* sm, double* slot)
+__device__ __forceinline__ void item_partials(T (&v)[NV], double* sm, double* slot)
 {
     constexpr int SEGS = kThreads / W;
     const int tid = threadIdx.x;
@@ -297,50 +302,26 @@ __device__ __forceinline__ void block_partials(T (&v)[NV], double* sm, double* s
 #pragma unroll
             for (int q = 0; q < NV; ++q) s[q] += sm[(g * W + tid) * NV + q];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) slot[(size_t)tid * kPartStride + q] += s[q];
+        for (int q = 0; q < NV; ++q) slot[(size_t)q * W + tid] = s[q];
     }
     __syncthreads();
 }
 
-// Called by all threads of the CTA that finished the group's last item: sums
-// the slots of this launch's CTAs (slot b belongs to CTA b, b < gridDim.x <=
-// nslot) in order into red[cl*kPartStride + q] and zeroes them for the next
-// launch.  Eight slots' loads are issued before any is summed or zeroed, so
-// the pass over the slots costs a few L2 round trips, not one per slot.
+// Sum of `count` consecutive slots starting at `base`, per lane, in a fixed
+// order, into red[cl * kPartStride + q] (shared).  All threads of the CTA.
 template <int W, int NV>
-__device__ __forceinline__ void group_reduce(double* slots, int nslot, double* sm, double* red)
+__device__ __forceinline__ void sum_slots(const double* base, int count, double* sm, double* red)
 {
     constexpr int SEGS = kThreads / W;
-    constexpr int U = 8;
     const int tid = threadIdx.x;
     const int cl = tid % W, seg = tid / W;
-    const int nb = min(nslot, (int)gridDim.x);
     double s[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) s[q] = 0.0;
-    int b = seg;
-    for (; b + (U - 1) * SEGS < nb; b += U * SEGS) {
-        double v[U][NV];
+#pragma unroll 4
+    for (int b = seg; b < count; b += SEGS)
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int q = 0; q < NV; ++q) v[u][q] = __ldcg(slots + ((size_t)(b + u * SEGS) * W + cl) * kPartStride + q);
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                s[q] += v[u][q];
-                slots[((size_t)(b + u * SEGS) * W + cl) * kPartStride + q] = 0.0;
-            }
-    }
-    for (; b < nb; b += SEGS) {
-        double* src = slots + ((size_t)b * W + cl) * kPartStride;
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            s[q] += __ldcg(src + q);
-            src[q] = 0.0;
-        }
-    }
+        for (int q = 0; q < NV; ++q) s[q] += __ldcg(base + ((size_t)b * kPartStride + q) * W + cl);
 #pragma unroll
     for (int q = 0; q < NV; ++q) sm[(seg * W + cl) * NV + q] = s[q];
     __syncthreads();
@@ -357,19 +338,44 @@ __device__ __forceinline__ void group_reduce(double* slots, int nslot, double* s
     __syncthreads();
 }
 
-// Returns true in every thread of the CTA that completed the group's last item.
-__device__ __forceinline__ bool arrive_group(unsigned* counter, int nrb, int* flag_sm)
+// Returns true in every thread of the CTA whose arrival is the total-th.
+__device__ __forceinline__ bool arrive_count(unsigned* counter, int total, int* flag_sm)
 {
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned prev = atomicAdd(counter, 1u);
-        *flag_sm = (prev == (unsigned)(nrb - 1));
+        *flag_sm = (prev == (unsigned)(total - 1));
     }
     __syncthreads();
     const bool last = *flag_sm != 0;
     if (last) __threadfence();
     return last;
+}
+
+// After an item wrote its slot: the CTA completing the item's bucket sums the
+// bucket into its bucket slot; the CTA completing the group's last bucket sums
+// the bucket slots into red[] and returns true (all its threads).  Counters
+// are reset by the CTA that completes them.
+template <int W, int NV>
+__device__ __forceinline__ bool tree_arrive(double* gslots, int nrb, int rb, unsigned* bk_count, unsigned* grp_count,
+                                            double* sm, double* red, int* flag_sm)
+{
+    const int nbk = part_buckets(nrb);
+    const int bk = rb / kPartBucket;
+    const int bsz = min(kPartBucket, nrb - bk * kPartBucket);
+    if (!arrive_count(bk_count + bk, bsz, flag_sm)) return false;
+    sum_slots<W, NV>(gslots + (size_t)bk * kPartBucket * kPartStride * W, bsz, sm, red);
+    if (threadIdx.x < W) {
+        double* bs = gslots + ((size_t)nrb + bk) * kPartStride * W;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) bs[(size_t)q * W + threadIdx.x] = red[threadIdx.x * kPartStride + q];
+    }
+    if (threadIdx.x == 0) bk_count[bk] = 0u;
+    if (!arrive_count(grp_count, nbk, flag_sm)) return false;
+    sum_slots<W, NV>(gslots + (size_t)nrb * kPartStride * W, nbk, sm, red);
+    if (threadIdx.x == 0) *grp_count = 0u;
+    return true;
 }
 
 struct ItemInfo {
@@ -408,6 +414,83 @@ __device__ __forceinline__ ItemInfo item_info_b(const FilterArgs& a, long long i
     t.g = (int)(local / nrb);
     t.rb = (int)(local % nrb);
     return t;
+}
+
+// ---------------------------------------------------------------- group finish
+// Run by the CTA that completed a group's last item.  Kept out of line so
+// that their FP64 scalar work does not raise the register count of the
+// streaming loops.  Step A: sigma = p^T q, alpha = rho / sigma, c alpha.
+template <int W>
+__device__ __noinline__ void finish_group_a(ColState* csg, bool first, const double* red)
+{
+    const int tid = threadIdx.x;
+    if (tid < W) {
+        ColState cs = csg[tid];
+        if (first) {
+            cs.bn2 = red[tid * kPartStride + 2];
+            cs.rho = make_double2(cs.bn2, 0.0);  // the right-hand side is real
+            cs.rn2 = cs.bn2;
+            if (!(cs.bn2 > 0.0)) { cs.active = 0; cs.status = 1; }
+        }
+        double2 sig = make_double2(red[tid * kPartStride], red[tid * kPartStride + 1]);
+        double2 al = make_double2(0.0, 0.0);
+        if (cs.active) {
+            const double d = sig.x * sig.x + sig.y * sig.y;
+            if (!(d > 0.0) || !isfinite(d)) {
+                cs.active = 0;
+                cs.status = 2;
+            } else {  // alpha = rho / sigma
+                al.x = (cs.rho.x * sig.x + cs.rho.y * sig.y) / d;
+                al.y = (cs.rho.y * sig.x - cs.rho.x * sig.y) / d;
+            }
+        }
+        cs.alpha = al;
+        cs.ca = make_double2(cs.c.x * al.x - cs.c.y * al.y, cs.c.x * al.y + cs.c.y * al.x);
+        csg[tid] = cs;
+    }
+}
+
+// Step B: rho' = r^T r, beta = rho' / rho, convergence |r|^2 <= tol^2 |b|^2;
+// a group whose columns all stopped is marked done.
+template <int W>
+__device__ __noinline__ void finish_group_b(ColState* csg, int k, double tol2, int* done, int* groups_left,
+                                            int* iter_max, unsigned long long* work, const double* red)
+{
+    const int tid = threadIdx.x;
+    if (tid < 32) {
+        int still = 0;
+        if (tid < W) {
+            ColState cs = csg[tid];
+            if (cs.active) {
+                const double2 rho1 = make_double2(red[tid * kPartStride], red[tid * kPartStride + 1]);
+                cs.rn2 = red[tid * kPartStride + 2];
+                cs.iters = k + 1;
+                const double d = cs.rho.x * cs.rho.x + cs.rho.y * cs.rho.y;
+                if (cs.rn2 <= tol2 * cs.bn2) {
+                    cs.active = 0;
+                    cs.status = 1;
+                } else if (!(d > 0.0) || !isfinite(cs.rn2)) {
+                    cs.active = 0;
+                    cs.status = 2;
+                } else {  // beta = rho1 / rho
+                    cs.beta.x = (rho1.x * cs.rho.x + rho1.y * cs.rho.y) / d;
+                    cs.beta.y = (rho1.y * cs.rho.x - rho1.x * cs.rho.y) / d;
+                    cs.rho = rho1;
+                }
+                csg[tid] = cs;
+                still = cs.active;
+            }
+        }
+        const unsigned anyv = __ballot_sync(0xffffffffu, still);
+        if (tid == 0) {
+            if (!anyv) {
+                *done = 1;
+                atomicSub(groups_left, 1);
+            }
+            if (work) atomicAdd(work, 1ull);
+            atomicMax(iter_max, k + 1);
+        }
+    }
 }
 
 // ---------------------------------------------------------------- kernel A
@@ -512,36 +595,11 @@ __global__ void __launch_bounds__(kThreads, FEAST_MINB) cocg_step_a(FilterArgs a
                 finish(i, ri, ar, po, qo);
             }
         }
-        double* slots = a.part + (size_t)(P.grp_off + g) * a.nslot * W * kPartStride;
-        block_partials<W, 3>(acc, sm, slots + (size_t)blockIdx.x * W * kPartStride);
-        if (arrive_group(a.grp_count + P.grp_off + g, P.nrb, &flag)) {
-            group_reduce<W, 3>(slots, a.nslot, sm, red);
-            if (tid < W) {
-                ColState cs = csg[tid];
-                if (first) {
-                    cs.bn2 = red[tid * kPartStride + 2];
-                    cs.rho = make_double2(cs.bn2, 0.0);  // the right-hand side is real
-                    cs.rn2 = cs.bn2;
-                    if (!(cs.bn2 > 0.0)) { cs.active = 0; cs.status = 1; }
-                }
-                double2 sig = make_double2(red[tid * kPartStride], red[tid * kPartStride + 1]);
-                double2 al = make_double2(0.0, 0.0);
-                if (cs.active) {
-                    const double d = sig.x * sig.x + sig.y * sig.y;
-                    if (!(d > 0.0) || !isfinite(d)) {
-                        cs.active = 0;
-                        cs.status = 2;
-                    } else {  // alpha = rho / sigma
-                        al.x = (cs.rho.x * sig.x + cs.rho.y * sig.y) / d;
-                        al.y = (cs.rho.y * sig.x - cs.rho.x * sig.y) / d;
-                    }
-                }
-                cs.alpha = al;
-                cs.ca = make_double2(cs.c.x * al.x - cs.c.y * al.y, cs.c.x * al.y + cs.c.y * al.x);
-                csg[tid] = cs;
-            }
-            if (tid == 0) a.grp_count[P.grp_off + g] = 0u;
-        }
+        const int gi = P.grp_off + g;
+        double* gslots = a.part + (size_t)gi * a.nslot * kPartStride * W;
+        item_partials<W, 3>(acc, sm, gslots + (size_t)it.rb * kPartStride * W);
+        if (tree_arrive<W, 3>(gslots, P.nrb, it.rb, a.bk_count + (size_t)gi * a.nbk, a.grp_count + gi, sm, red, &flag))
+            finish_group_a<W>(csg, first, red);
     }
 }
 
@@ -616,46 +674,12 @@ __global__ void __launch_bounds__(kThreads, FEAST_MINB_B) cocg_step_b(FilterArgs
                 acc[2] = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[2]));
             }
         }
-        double* slots = a.part + (size_t)(P.grp_off + g) * a.nslot * W * kPartStride;
-        block_partials<W, 3>(acc, sm, slots + (size_t)blockIdx.x * W * kPartStride);
-        if (arrive_group(a.grp_count + P.grp_off + g, P.nrb_b, &flag)) {
-            group_reduce<W, 3>(slots, a.nslot, sm, red);
-            if (tid < 32) {
-                int still = 0;
-                if (tid < W) {
-                    ColState cs = csg[tid];
-                    if (cs.active) {
-                        const double2 rho1 = make_double2(red[tid * kPartStride], red[tid * kPartStride + 1]);
-                        cs.rn2 = red[tid * kPartStride + 2];
-                        cs.iters = k + 1;
-                        const double d = cs.rho.x * cs.rho.x + cs.rho.y * cs.rho.y;
-                        if (cs.rn2 <= a.tol2 * cs.bn2) {
-                            cs.active = 0;
-                            cs.status = 1;
-                        } else if (!(d > 0.0) || !isfinite(cs.rn2)) {
-                            cs.active = 0;
-                            cs.status = 2;
-                        } else {  // beta = rho1 / rho
-                            cs.beta.x = (rho1.x * cs.rho.x + rho1.y * cs.rho.y) / d;
-                            cs.beta.y = (rho1.y * cs.rho.x - rho1.x * cs.rho.y) / d;
-                            cs.rho = rho1;
-                        }
-                        csg[tid] = cs;
-                        still = cs.active;
-                    }
-                }
-                const unsigned anyv = __ballot_sync(0xffffffffu, still);
-                if (tid == 0) {
-                    if (!anyv) {
-                        a.grp_done[P.grp_off + g] = 1;
-                        atomicSub(a.groups_left + it.pi, 1);
-                    }
-                    if (a.work) atomicAdd(a.work, 1ull);
-                    atomicMax(a.iter_max + it.pi, k + 1);
-                    a.grp_count[P.grp_off + g] = 0u;
-                }
-            }
-        }
+        const int gi = P.grp_off + g;
+        double* gslots = a.part + (size_t)gi * a.nslot * kPartStride * W;
+        item_partials<W, 3>(acc, sm, gslots + (size_t)it.rb * kPartStride * W);
+        if (tree_arrive<W, 3>(gslots, P.nrb_b, it.rb, a.bk_count + (size_t)gi * a.nbk, a.grp_count + gi, sm, red,
+                              &flag))
+            finish_group_b<W>(csg, k, a.tol2, a.grp_done + gi, a.groups_left + it.pi, a.iter_max + it.pi, a.work, red);
     }
 }
 
