@@ -227,7 +227,7 @@ Plan make_plan(int n, int nnzA, int nnzB, int m0, const int* fpm, bool filter_on
         nb = (nb + 1) / 2;
     }
     P.nbatch = (P.ne + P.nbp - 1) / P.nbp;
-    P.RB = fpm[50] > 0 ? std::min(fpm[50], 512) : 128;
+    P.RB = fpm[50] > 0 ? std::min(fpm[50], 512) : 256;
     P.nrb = (n + P.RB - 1) / P.RB;
     P.nitems = (long long)P.G * P.nrb;
     P.RBb = 512;
@@ -1317,7 +1317,7 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
     int ga = 1, gb = 1;
     filter_grids(fp64, W, &ga, &gb);
     // partial-sum slots for the smallest row block the tuner may pick
-    const int rb_min = fpm[50] > 0 ? std::min(fpm[50], 512) : 64;
+    const int rb_min = fpm[50] > 0 ? std::min(fpm[50], 512) : 128;
     int nslot = 1, nbk = 1;
     for (int p = 0; p < np; ++p) {
         const int nrb_max = (probs[p].n + rb_min - 1) / rb_min;
@@ -1548,7 +1548,7 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
     fa.work = d_work;
     fa.kdev = d_k;
     fa.iter_max = d_itmax;
-    int st = build_tables(fpm[50] > 0 ? std::min(fpm[50], 512) : 128);
+    int st = build_tables(fpm[50] > 0 ? std::min(fpm[50], 512) : 256);
     if (st) return st;
     auto grids = [&](int& g_a, int& g_b, int& g_i) {
         g_a = (int)std::min<long long>(ga, std::max(1LL, nitems));
@@ -1616,11 +1616,11 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
             CK(cudaMemsetAsync(d_bkcount, 0, sizeof(unsigned) * (size_t)grpo * nbk, s));
             CK(launch_colstate_init(fa, 0, 0, s));
             float best = 1e30f;
-            int best_rb = 128;
+            int best_rb = 256;
             cudaEvent_t e0, e1;
             CK(cudaEventCreate(&e0));
             CK(cudaEventCreate(&e1));
-            for (int cand : {64, 128, 256}) {
+            for (int cand : {128, 256, 512}) {
                 build_tables(cand);
                 int g_a, g_b, g_i;
                 grids(g_a, g_b, g_i);

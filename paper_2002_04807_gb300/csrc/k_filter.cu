@@ -31,10 +31,10 @@
 // a gather of a wide 3D stencil moves data at roughly half the rate of a
 // plain stream (far neighbours come through L2), so trading a second gather
 // for two extra streams is faster even though it moves more bytes.
-// Rows of a CSR matrix are stored as packed (column, value) entries padded to
-// chunks of 8 with zero-weight entries on the diagonal, so a row is gathered
-// with unpredicated, fully unrolled loads; step A gathers two rows per pass,
-// 16 independent row-segment loads in flight per thread.
+// Rows of a CSR matrix are stored as packed (column, value) entries, the
+// diagonal entry first, padded to chunks of 8 with column -1 entries that
+// issue no load, so a row is gathered with fully unrolled loads and its own
+// value comes out of its first load.
 // Reductions are deterministic: fixed per-thread order, fixed block order;
 // every work item writes its own partial-sum slot, the CTA that completes a
 // bucket of 32 consecutive items sums them into a bucket slot, and the CTA
@@ -48,16 +48,15 @@ namespace feast {
 static constexpr int kThreads = 256;
 static constexpr int kPartStride = 4;
 static constexpr int kChunk = 8;  // padded CSR chunk (entries)
-static constexpr int kStageEntries = 2048;  // packed entries of one item staged in shared memory
+// Packed entries of one item staged in shared memory.  Kept small: shared
+// memory comes out of the L1 capacity that caches the gathered neighbours.
+static constexpr int kStageEntries = 2048;
 static constexpr int kMaxRB = 512;  // rows per work item, at most
 #ifndef FEAST_MINB
-#define FEAST_MINB 3
+#define FEAST_MINB 5
 #endif
 #ifndef FEAST_MINB_B
 #define FEAST_MINB_B 5
-#endif
-#ifndef FEAST_A_ROWS2
-#define FEAST_A_ROWS2 1
 #endif
 
 __device__ __forceinline__ int find_prob(const FiltProb* probs, int nprob, long long item)
@@ -125,60 +124,23 @@ template <> __device__ __forceinline__ void load_chunk<double, false>(const int4
     }
 }
 
-// Column indices and values of a shared-memory chunk, read separately.  The
-// value read is volatile so that it is not merged with the index read and
-// issued before the gathers that the indices feed.
-template <typename T> __device__ __forceinline__ void load_cols(const int4* ent, int c, int (&j)[kChunk]);
-template <> __device__ __forceinline__ void load_cols<float>(const int4* ent, int c, int (&j)[kChunk])
-{
-    const int2* q = (const int2*)ent + c;
-#pragma unroll
-    for (int u = 0; u < kChunk; ++u) j[u] = q[u].x;
-}
-template <> __device__ __forceinline__ void load_cols<double>(const int4* ent, int c, int (&j)[kChunk])
-{
-#pragma unroll
-    for (int u = 0; u < kChunk; ++u) j[u] = ent[c + u].x;
-}
-template <typename T> __device__ __forceinline__ void load_vals(const int4* ent, int c, T (&a)[kChunk]);
-template <> __device__ __forceinline__ void load_vals<float>(const int4* ent, int c, float (&a)[kChunk])
-{
-    const volatile int2* q = (const volatile int2*)ent + c;
-#pragma unroll
-    for (int u = 0; u < kChunk; ++u) a[u] = __int_as_float(q[u].y);
-}
-template <> __device__ __forceinline__ void load_vals<double>(const int4* ent, int c, double (&a)[kChunk])
-{
-    const volatile int4* q = (const volatile int4*)ent + c;
-#pragma unroll
-    for (int u = 0; u < kChunk; ++u) a[u] = __hiloint2double(q[u].w, q[u].z);
-}
-
-// ax = sum a_k x[j_k] (and with UPD ap = sum a_k p[j_k]) over the padded row
-// entries [c0, c1) of ent.  The row's own values x[i] (and p[i]) come out of
-// the same loads when the row has an entry in column i (its diagonal, or a
-// zero-weight padding entry); *own says whether they did.
-template <typename T, int W, bool UPD, bool SH>
+// ax = sum a_k x[j_k] over the padded row entries [c0, c1) of ent (padding
+// entries have column -1 and issue no load).  The row's own value x[i] comes
+// out of the same loads when the row stores column i; *own says whether it did.
+template <typename T, int W, bool SH>
 __device__ __forceinline__ void row_gather(const int4* __restrict__ ent, int c0, int c1, int i,
-                                           const c2_t<T>* __restrict__ xl, const c2_t<T>* __restrict__ pl,
-                                           bool use_p, c2_t<T>& ax, c2_t<T>& ap, c2_t<T>& xo, c2_t<T>& po,
-                                           bool& own)
+                                           const c2_t<T>* __restrict__ xl, c2_t<T>& ax, c2_t<T>& xo, bool& own)
 {
     using V = c2_t<T>;
     ax = cmk<V>(T(0), T(0));
-    ap = cmk<V>(T(0), T(0));
     own = false;
     for (int c = c0; c < c1; c += kChunk) {
         int j[kChunk];
         T av[kChunk];
         load_chunk<T, SH>(ent, c, j, av);
-        V xv[kChunk], pv[kChunk];
+        V xv[kChunk];
 #pragma unroll
-        for (int u = 0; u < kChunk; ++u) xv[u] = __ldg(xl + (size_t)j[u] * W);
-        if (UPD && use_p) {
-#pragma unroll
-            for (int u = 0; u < kChunk; ++u) pv[u] = __ldg(pl + (size_t)j[u] * W);
-        }
+        for (int u = 0; u < kChunk; ++u) xv[u] = j[u] >= 0 ? __ldg(xl + (size_t)j[u] * W) : cmk<V>(T(0), T(0));
 #pragma unroll
         for (int u = 0; u < kChunk; ++u) {
             ax.x = fma(av[u], xv[u].x, ax.x);
@@ -186,61 +148,6 @@ __device__ __forceinline__ void row_gather(const int4* __restrict__ ent, int c0,
             if (j[u] == i) {
                 xo = xv[u];
                 own = true;
-            }
-        }
-        if (UPD && use_p) {
-#pragma unroll
-            for (int u = 0; u < kChunk; ++u) {
-                ap.x = fma(av[u], pv[u].x, ap.x);
-                ap.y = fma(av[u], pv[u].y, ap.y);
-                if (j[u] == i) po = pv[u];
-            }
-        }
-    }
-}
-
-// Two rows a and b gathered together from shared-memory entries: the chunks
-// of both rows are loaded before either is used, so each thread keeps twice
-// the row segments in flight.  Row b is absent when nb == 0.  The column
-// indices are dead once the loads are issued (the caller reads the rows' own
-// values separately, from L1).
-template <typename T, int W>
-__device__ __forceinline__ void row_gather2(const int4* ent, int ca, int na, int cb, int nb,
-                                            const c2_t<T>* __restrict__ xl, c2_t<T>& axa, c2_t<T>& axb)
-{
-    using V = c2_t<T>;
-    axa = cmk<V>(T(0), T(0));
-    axb = cmk<V>(T(0), T(0));
-    const int nmax = na > nb ? na : nb;
-    for (int off = 0; off < nmax; off += kChunk) {
-        const bool ha = off < na, hb = off < nb;
-        V xa[kChunk], xb[kChunk];
-        {
-            int ja[kChunk], jb[kChunk];
-            if (ha) load_cols<T>(ent, ca + off, ja);
-            if (hb) load_cols<T>(ent, cb + off, jb);
-#pragma unroll
-            for (int u = 0; u < kChunk; ++u) xa[u] = ha ? __ldg(xl + (size_t)ja[u] * W) : cmk<V>(T(0), T(0));
-#pragma unroll
-            for (int u = 0; u < kChunk; ++u) xb[u] = hb ? __ldg(xl + (size_t)jb[u] * W) : cmk<V>(T(0), T(0));
-        }
-        // the values are read after the loads are issued, so they need no
-        // registers while the loads are in flight
-        T aa[kChunk], ab[kChunk];
-        if (ha) {
-            load_vals<T>(ent, ca + off, aa);
-#pragma unroll
-            for (int u = 0; u < kChunk; ++u) {
-                axa.x = fma(aa[u], xa[u].x, axa.x);
-                axa.y = fma(aa[u], xa[u].y, axa.y);
-            }
-        }
-        if (hb) {
-            load_vals<T>(ent, cb + off, ab);
-#pragma unroll
-            for (int u = 0; u < kChunk; ++u) {
-                axb.x = fma(ab[u], xb[u].x, axb.x);
-                axb.y = fma(ab[u], xb[u].y, axb.y);
             }
         }
     }
@@ -252,10 +159,9 @@ template <typename T, int W>
 __device__ __forceinline__ c2_t<T> row_gather_global(const int* __restrict__ pp, const void* __restrict__ pk, int i,
                                                      const c2_t<T>* __restrict__ xl)
 {
-    c2_t<T> ax, ap, xo, po;
+    c2_t<T> ax, xo;
     bool own;
-    row_gather<T, W, false, false>((const int4*)pk, __ldg(pp + i), __ldg(pp + i + 1), i, xl, nullptr, false, ax, ap,
-                                   xo, po, own);
+    row_gather<T, W, false>((const int4*)pk, __ldg(pp + i), __ldg(pp + i + 1), i, xl, ax, xo, own);
     return ax;
 }
 
@@ -534,9 +440,20 @@ __global__ void __launch_bounds__(kThreads, FEAST_MINB) cocg_step_a(FilterArgs a
         const int row1 = min(n, row0 + a.RB);
         const int4* gent;
         const bool staged = stage_rows<T>(P.app, P.apk, row0, row1, s_pp, s_ent, gent);
-        // p_k, q_k of row i from the gathered s = A r, the own value r_i and
-        // the previous p, q of the row
-        auto finish = [&](int i, V ri, V ar, V po, V qo) {
+        const V zero = cmk<V>(T(0), T(0));
+        for (int i = row0 + rowslot; i < row1; i += RPP) {
+            // own-row streams first, so their loads overlap the gather
+            V po = zero, qo = zero;
+            if (use_p) {
+                po = pl_[(size_t)i * W];
+                qo = ql_[(size_t)i * W];
+            }
+            const int c0 = s_pp[i - row0], c1 = s_pp[i - row0 + 1];
+            V ar, ri = zero;
+            bool own;
+            if (staged) row_gather<T, W, true>(s_ent, c0, c1, i, rl_, ar, ri, own);
+            else row_gather<T, W, false>(gent, c0, c1, i, rl_, ar, ri, own);
+            if (!own) ri = __ldg(rl_ + (size_t)i * W);
             V bx = ri;
             if (BM == 1) {
                 const T b = ((const T*)P.bd)[i];
@@ -554,46 +471,6 @@ __global__ void __launch_bounds__(kThreads, FEAST_MINB) cocg_step_a(FilterArgs a
             acc[0] = fma(pi_.x, qi.x, fma(-pi_.y, qi.y, acc[0]));
             acc[1] = fma(pi_.x, qi.y, fma(pi_.y, qi.x, acc[1]));
             if (first) acc[2] = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[2]));
-        };
-        const V zero = cmk<V>(T(0), T(0));
-        if (FEAST_A_ROWS2 && staged) {
-            // two rows per pass, every load of both issued before any use
-            for (int i0 = row0 + rowslot; i0 < row1; i0 += 2 * RPP) {
-                const int i1 = i0 + RPP;
-                const bool ok1 = i1 < row1;
-                V po0 = zero, qo0 = zero, po1 = zero, qo1 = zero;
-                if (use_p) {
-                    po0 = pl_[(size_t)i0 * W];
-                    qo0 = ql_[(size_t)i0 * W];
-                    if (ok1) {
-                        po1 = pl_[(size_t)i1 * W];
-                        qo1 = ql_[(size_t)i1 * W];
-                    }
-                }
-                const int ca = s_pp[i0 - row0], na = s_pp[i0 - row0 + 1] - ca;
-                const int cb = ok1 ? s_pp[i1 - row0] : 0, nb = ok1 ? s_pp[i1 - row0 + 1] - cb : 0;
-                V ar0, ar1;
-                row_gather2<T, W>(s_ent, ca, na, cb, nb, rl_, ar0, ar1);
-                const V ri0 = __ldg(rl_ + (size_t)i0 * W);
-                const V ri1 = ok1 ? __ldg(rl_ + (size_t)i1 * W) : zero;
-                finish(i0, ri0, ar0, po0, qo0);
-                if (ok1) finish(i1, ri1, ar1, po1, qo1);
-            }
-        } else {
-            for (int i = row0 + rowslot; i < row1; i += RPP) {
-                V po = zero, qo = zero;
-                if (use_p) {
-                    po = pl_[(size_t)i * W];
-                    qo = ql_[(size_t)i * W];
-                }
-                const int c0 = s_pp[i - row0], c1 = s_pp[i - row0 + 1];
-                V ar, unused, ri = zero, unused2;
-                bool own;
-                if (staged) row_gather<T, W, false, true>(s_ent, c0, c1, i, rl_, nullptr, false, ar, unused, ri, unused2, own);
-                else row_gather<T, W, false, false>(gent, c0, c1, i, rl_, nullptr, false, ar, unused, ri, unused2, own);
-                if (!own) ri = __ldg(rl_ + (size_t)i * W);
-                finish(i, ri, ar, po, qo);
-            }
         }
         const int gi = P.grp_off + g;
         double* gslots = a.part + (size_t)gi * a.nslot * kPartStride * W;
@@ -826,8 +703,9 @@ __global__ void fold_dq(const FiltProb* probs, int nprob, int mt, const T* dQ, d
 }
 
 // Packed (column, value) CSR entries padded to whole chunks: row i occupies
-// entries [pp[i], pp[i+1]) of out; entries past the row's nonzeros are
-// (i, 0).  One warp per row.
+// entries [pp[i], pp[i+1]) of out, its (first) diagonal entry first, then the
+// other stored entries in order; entries past the row's nonzeros are (-1, 0).
+// One warp per row.
 __global__ void pack_csr(int n, const int* ia, const int* ja, const double* av, const int* pp, int fp64, void* out)
 {
     const int lane = threadIdx.x & 31;
@@ -835,10 +713,23 @@ __global__ void pack_csr(int n, const int* ia, const int* ja, const double* av, 
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int i = warp; i < n; i += nw) {
         const int s = ia[i], len = ia[i + 1] - s, c0 = pp[i], c1 = pp[i + 1];
+        // position of the row's (first) diagonal entry, -1 if it has none
+        int dpos = -1;
+        for (int base = 0; base < len; base += 32) {
+            const int t = base + lane;
+            const unsigned b = __ballot_sync(0xffffffffu, t < len && ja[s + t] == i);
+            if (b) {
+                dpos = base + __ffs(b) - 1;
+                break;
+            }
+        }
         for (int t = c0 + lane; t < c1; t += 32) {
             const int q = t - c0;
-            const int j = q < len ? ja[s + q] : i;
-            const double v = q < len ? av[s + q] : 0.0;
+            // diagonal first, then the other entries in their stored order
+            int src = -1;
+            if (q < len) src = dpos < 0 ? q : (q == 0 ? dpos : (q - 1 < dpos ? q - 1 : q));
+            const int j = src >= 0 ? ja[s + src] : -1;
+            const double v = src >= 0 ? av[s + src] : 0.0;
             if (fp64) ((int4*)out)[t] = make_int4(j, 0, __double2loint(v), __double2hiint(v));
             else ((int2*)out)[t] = make_int2(j, __float_as_int((float)v));
         }
