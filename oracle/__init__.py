@@ -207,6 +207,25 @@ def filter_block(A, B, ne, emin, emax, ratio, Y, lam=None, rii=False, solver="di
     return Q
 
 
+def stochastic_count(A, B, ne, emin, emax, ratio, Y, solver="direct", solve_tol=1e-13):
+    """Stochastic estimate of the eigenvalue count inside the contour (fpm(14)=2;
+    ratio = ellipse axis ratio, fpm(18)/100):
+    mean over the probe columns of Y of y^T rho(B^{-1}A) y, with its standard
+    error.  Returns (estimate, standard_error)."""
+    Y = np.asfortranarray(Y, dtype=np.float64)
+    n, m = Y.shape
+    ip, ix, v = _csr_args(A)
+    bip, bix, bv = _csr_args(B)
+    est, sem = C.c_double(0.0), C.c_double(0.0)
+    st = lib().orc_stochastic_count(C.c_int(n), _ptr(ip), _ptr(ix), _ptr(v), _ptr(bip), _ptr(bix), _ptr(bv),
+                                    C.c_int(ne), C.c_double(emin), C.c_double(emax), C.c_double(ratio),
+                                    C.c_int(m), _ptr(Y), C.c_int(0 if solver == "direct" else 1),
+                                    C.c_double(solve_tol), C.byref(est), C.byref(sem))
+    if st:
+        raise RuntimeError("oracle stochastic count failed")
+    return est.value, sem.value
+
+
 def eig_grad(A, X, w):
     """grad[p] = sum_k w_k X[i_p,k] X[j_p,k] over the stored entries of A."""
     X = np.asfortranarray(X, dtype=np.float64)

@@ -672,6 +672,39 @@ int orc_filter(int n, const int* ip, const int* ix, const double* av,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Stochastic estimate of the number of eigenvalues inside the contour
+ * (fpm(14)=2; the guide cites Di Napoli, Polizzi and Saad for the method).
+ * The quadrature filter applied to a vector is rho(B^{-1}A) y, and
+ * trace(rho(B^{-1}A)) = sum_i rho(lambda_i), which counts the eigenvalues
+ * inside (rho ~ 1) and ignores those far outside (rho ~ 0).  For probes with
+ * E[y y^T] = I, E[y^T rho(B^{-1}A) y] is that trace, so the estimate is the
+ * mean over the m columns of Y (column-major n x m) of y_j^T Q_j with
+ * Q = sum_e Re(w_e (z_e B - A)^{-1} B Y); *sem is the standard error of that
+ * mean (sample standard deviation / sqrt(m)).  Returns 0 or -2. */
+int orc_stochastic_count(int n, const int* ip, const int* ix, const double* av,
+                         const int* bip, const int* bix, const double* bv,
+                         int ne, double emin, double emax, double ratio, int m, const double* Y,
+                         int solver, double solve_tol, double* est, double* sem)
+{
+    double* Q = (double*)malloc(sizeof(double) * (size_t)n * m);
+    int st = orc_filter(n, ip, ix, av, bip, bix, bv, ne, emin, emax, ratio, m, Y, NULL, 0, Q, solver, solve_tol);
+    if (st) { free(Q); return st; }
+    double sum = 0.0, sum2 = 0.0;
+    for (int j = 0; j < m; ++j) {
+        double t = 0.0;
+        for (int i = 0; i < n; ++i) t += Y[(size_t)j * n + i] * Q[(size_t)j * n + i];
+        sum += t;
+        sum2 += t * t;
+    }
+    const double mean = sum / m;
+    const double var = m > 1 ? (sum2 - m * mean * mean) / (m - 1) : 0.0;
+    *est = mean;
+    *sem = sqrt(var > 0.0 ? var : 0.0) / sqrt((double)m);
+    free(Q);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* FEAST for real symmetric CSR problems (dfeast_scsr{ev,gv} semantics).
  * fpm is the 64-entry parameter array, C indexing fpm[i-1] = fpm(i).
  * Used entries: fpm(2) = Ne, fpm(3) = tolerance exponent, fpm(4) = max

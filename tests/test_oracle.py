@@ -327,3 +327,45 @@ def test_eig_grad_matches_finite_differences(gen):
             lm = scipy.linalg.eigh(A.to_dense(), db - E, eigvals_only=True)[:k]
             fd = np.dot(g, lp - lm) / (2 * h)
             assert abs(fd - gb[i]) < 1e-6 + 1e-6 * abs(fd)
+
+
+# ------------------------------------------------------------------ stochastic count (fpm(14)=2)
+def _rho_dense(ne, emin, emax, ratio, lam):
+    """rho(lambda) = sum_e Re(w_e / (z_e - lambda)) from the pinned nodes."""
+    z, w = O.contour_gauss(ne, emin, emax, ratio)
+    return np.array([np.sum((w / (z - l)).real) for l in lam])
+
+
+@pytest.mark.parametrize("gen", [False, True])
+def test_stochastic_count_matches_dense_trace_formula(gen):
+    """y^T rho(B^{-1}A) y by contour solves equals the dense spectral formula
+    y^T X diag(rho(lambda)) X^T B y (X^T B X = I) for every probe."""
+    rng = np.random.default_rng(21)
+    A = fw.laplacian_2d(12, rng.uniform(0, 1, (12, 12)))
+    B = fw.diagonal_csr(rng.uniform(1, 2, A.n)) if gen else None
+    db = np.eye(A.n) if B is None else B.to_dense()
+    lam, X = scipy.linalg.eigh(A.to_dense(), db)
+    emin, emax = 0.0, 0.5 * (lam[14] + lam[15])
+    Y = rng.standard_normal((A.n, 10))
+    est, sem = O.stochastic_count(A, B, 8, emin, emax, 1.0, Y)
+    r = _rho_dense(8, emin, emax, 1.0, lam)
+    t = np.einsum("ij,ij->j", Y, X @ (r[:, None] * (X.T @ (db @ Y))))
+    assert abs(est - t.mean()) < 1e-11 * abs(t.mean())
+    assert abs(sem - t.std(ddof=1) / np.sqrt(10)) < 1e-9 * t.std()
+
+
+def test_stochastic_count_estimates_eigenvalue_count():
+    """With many probes and a sharp filter the estimate lands on the count of
+    eigenvalues inside (inertia), within five standard errors."""
+    rng = np.random.default_rng(22)
+    A = fw.laplacian_2d(20, rng.uniform(0, 1, (20, 20)))
+    lam = np.linalg.eigvalsh(A.to_dense())
+    emax = 0.5 * (lam[29] + lam[30])
+    cnt = O.count_below(A, None, emax)
+    assert cnt == 30
+    Y = rng.standard_normal((A.n, 400))
+    est, sem = O.stochastic_count(A, None, 32, 0.0, emax, 1.0, Y)
+    trace = np.sum(_rho_dense(32, 0.0, emax, 1.0, lam))
+    assert abs(trace - cnt) < 0.05
+    assert 0.0 < sem < 1.0
+    assert abs(est - cnt) < 5 * sem
