@@ -21,8 +21,13 @@
  *      fpm(4)  maximum number of refinement loops (>= 0)
  *      fpm(5)  1: X holds the start subspace on entry; 0: a random start block
  *      fpm(6)  must be 1 (relative residual criterion)
+ *      fpm(14) 0 normal run; 1 return the block Q after one contour pass
+ *              (info 4); 2 stochastic estimate of the number of eigenvalues
+ *              inside the contour (info 5), see feast_scsr_solve
  *      fpm(16) must be 0 (Gauss-Legendre nodes)
  *      fpm(18) ellipse ratio in percent (> 0)
+ *      fpm(40) 0 search interval given (feast_scsr_solve*); -1 / +1 search
+ *              the M0/2 lowest / largest eigenpairs (feast_scsr_extreme*)
  *      fpm(42) 1: complex FP32 shifted solves (mixed precision), 0: complex FP64
  *      fpm(45) inner solver tolerance 10^-fpm(45) (0..16)
  *      fpm(46) inner solver iteration cap (>= 1)
@@ -34,7 +39,10 @@
  *  - Return value = info (also stored in *info where that argument exists),
  *    codes of the guide's info table (Sec. 3.1): 0 success; warnings 1 (no
  *    eigenvalue in the interval), 2 (no convergence within fpm(4) loops),
- *    3 (M0 too small: all Ritz values inside); errors 200 (Emin >= Emax),
+ *    3 (M0 too small: all Ritz values inside), 4 (only the filtered
+ *    subspace returned, fpm(14)=1), 5 (only the stochastic eigenvalue count
+ *    returned, fpm(14)=2), 7 (the search for extreme eigenvalues failed; the
+ *    interval must be given); errors 200 (Emin >= Emax),
  *    201 (bad M0), 202 (bad N), 100+i (bad fpm(i)), -(100+i) (bad i-th
  *    argument, e.g. CSR indices out of range, non-finite values), -2 (inner
  *    solver failure), -3 (reduced eigensolver failure, e.g. B not positive
@@ -109,10 +117,43 @@ int feast_last_profile(double* out);
  *   res       [m0] out: ||A x - e B x|| / ||alpha B x||, alpha = max(|emin|,|emax|)
  *   epsout    out: relative trace change of the last loop
  *   loop      out: refinement loops done
- *   info      out: as the return value */
+ *   info      out: as the return value
+ * One-pass modes (guide Sec. 3.1, fpm(14); the guide cites Di Napoli, Polizzi
+ * and Saad for the estimate): the M0 columns of the start block (X when
+ * fpm(5)=1, else seeded normal random vectors) go through one contour pass
+ * Q = sum_e Re(w_e (z_e B - A)^{-1} B Y) and no Rayleigh-Ritz step follows.
+ * fpm(14)=1 returns Q in x (info 4).  fpm(14)=2 returns in m the nearest
+ * integer to the estimate (1/M0) sum_j y_j^T Q_j of trace(rho(B^{-1}A)), the
+ * number of eigenvalues inside the contour (rho ~ 1 inside, ~ 0 far
+ * outside), with e[0] = the estimate and e[1] = its standard error (sample
+ * standard deviation / sqrt(M0), M0 >= 2); x is not changed (info 5).
+ * fpm(40) must be 0 here (-> 140); feast_scsr_extreme takes +-1. */
 int feast_scsr_solve(char uplo, int n, const double* a, const int* ia, const int* ja, const double* b,
                      const int* ib, const int* jb, int* fpm, double emin, double emax, int* m0, double* e,
                      double* x, int* m, double* res, double* epsout, int* loop, int* info);
+
+/* Extreme-eigenvalue mode (guide Sec. 3.1, fpm(40) = -1 / +1, and Sec. 3.2:
+ * the sparse drivers search the M0/2 lowest or largest eigenpairs and return
+ * the search interval).  Arguments as feast_scsr_solve, except:
+ *   fpm(40)   -1 lowest, +1 largest (anything else -> 140); fpm(14) must be 0
+ *   emin,emax host, out: an interval holding exactly the k = M0/2 wanted
+ *             eigenvalues (ignored on entry)
+ *   m0        in: 2k (2..n); out: live subspace size
+ *   e, x, res the k wanted pairs first (e ascending), then the other Ritz pairs
+ *   m         out: k
+ * The guide does not give the search; this library's: Gershgorin bounds of
+ * the pencil (of A for B = I, of D^{-1/2} A D^{-1/2} for B = D diagonal, else
+ * A's bounds divided by B's, which must be positive), an interval grown from
+ * the low (high) end guided by stochastic counts (fpm(14)=2 with min(M0, 32)
+ * probes, seed fpm(52)) until it holds about 1.15k..1.5k eigenvalues, then
+ * normal FEAST runs with M0 = 2k on it, widened or narrowed and restarted
+ * from the current Ritz vectors until at least k eigenvalues converge inside.
+ * Returns 0 (or 2 if the last run did not converge within fpm(4) loops), 7
+ * when no interval could be found, or the error codes above; -110/-111 for
+ * NULL emin/emax. */
+int feast_scsr_extreme(char uplo, int n, const double* a, const int* ia, const int* ja, const double* b,
+                       const int* ib, const int* jb, int* fpm, double* emin, double* emax, int* m0, double* e,
+                       double* x, int* m, double* res, double* epsout, int* loop, int* info);
 
 /* One problem of a batch (host memory, caller-owned).  CSR in full storage,
  * base ia[0] in {0,1}; b/ib/jb all NULL for B = I (then for every problem of
@@ -174,6 +215,15 @@ int feast_scsr_solve_dev(int n, int nnz_a, const int* d_ia, const int* d_ja, con
                          double emax, int* m0, double* e, double* d_x, int* m, double* res,
                          double* epsout, int* loop, int* info, void* d_work, size_t work_bytes,
                          void* stream);
+
+/* feast_scsr_extreme with the matrices and X on the device, arguments as
+ * feast_scsr_solve_dev; emin and emax are host pointers (out).  d_work: at
+ * least feast_scsr_workspace_bytes(...) bytes for this fpm (fpm(40) != 0 adds
+ * room for -A, diag(B) and the Gershgorin partials). */
+int feast_scsr_extreme_dev(int n, int nnz_a, const int* d_ia, const int* d_ja, const double* d_a, int nnz_b,
+                           const int* d_ib, const int* d_jb, const double* d_b, int* fpm, double* emin,
+                           double* emax, int* m0, double* e, double* d_x, int* m, double* res, double* epsout,
+                           int* loop, int* info, void* d_work, size_t work_bytes, void* stream);
 
 /* ---------------------------------------------------------------- kernels
  * Device-pointer entry points of the individual steps, for testing and for

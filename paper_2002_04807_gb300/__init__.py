@@ -27,6 +27,8 @@ from ._lib import (  # noqa: F401
     feast_scsr_solve,
     feast_scsr_solve_batched,
     feast_scsr_solve_dev,
+    feast_scsr_extreme,
+    feast_scsr_extreme_dev,
     feast_scsr_workspace_bytes,
     feast_shifted_spmm_dev,
     feast_sym_eig_dev,

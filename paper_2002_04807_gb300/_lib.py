@@ -39,6 +39,10 @@ _SIGS = {
     "feast_last_profile": (_i, [_p]),
     "feast_gram_noalloc_dev": (_i, [_i, _i, _p, _p, _p, _p]),
     "feast_scsr_solve_batched": (_i, [_i, _p, _p, _p]),
+    "feast_scsr_extreme": (_i, [C.c_char, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p,
+                                _p]),
+    "feast_scsr_extreme_dev": (_i, [_i, _i, _p, _p, _p, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p,
+                                    _p, _p, _p, C.c_size_t, _p]),
 }
 
 
@@ -157,6 +161,8 @@ class FeastResult:
     epsout: float
     m0: int
     fpm: np.ndarray
+    emin: float = float("nan")  # interval found by the extreme-eigenvalue search
+    emax: float = float("nan")
 
 
 def _fpm(fpm):
@@ -232,6 +238,69 @@ def feast_scsr_solve_dev(n: int, ia, ja, a, ib=None, jb=None, b=None, fpm=None, 
         raise FeastError("feast_scsr_solve_dev: " + feast_last_error())
     k = mm.value
     return FeastResult(info.value, E[:k].copy(), x, res[:k].copy(), M.value, loop.value, eps.value, k, f)
+
+
+def feast_scsr_extreme(uplo: str, n: int, a, ia, ja, b=None, ib=None, jb=None, fpm=None, m0: int = 2,
+                       x0=None) -> FeastResult:
+    """Host driver of the extreme-eigenvalue mode: fpm(40) = -1 (lowest) or +1
+    (largest) selects the m0/2 wanted pairs; the returned FeastResult carries
+    the interval found in emin/emax."""
+    f = _fpm(fpm)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    ia = np.ascontiguousarray(ia, dtype=np.int32)
+    ja = np.ascontiguousarray(ja, dtype=np.int32)
+    if b is not None:
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        ib = np.ascontiguousarray(ib, dtype=np.int32)
+        jb = np.ascontiguousarray(jb, dtype=np.int32)
+    x = np.zeros((n, m0), order="F")
+    if x0 is not None:
+        x[:] = x0
+    E = np.zeros(m0)
+    res = np.zeros(m0)
+    M, loop, info, mm = _i(0), _i(0), _i(0), _i(m0)
+    eps, lo, hi = _d(0), _d(0), _d(0)
+    library().feast_scsr_extreme(uplo.encode(), n, _ptr(a), _ptr(ia), _ptr(ja), _ptr(b), _ptr(ib), _ptr(jb),
+                                 _ptr(f), C.byref(lo), C.byref(hi), C.byref(mm), _ptr(E), _ptr(x), C.byref(M),
+                                 _ptr(res), C.byref(eps), C.byref(loop), C.byref(info))
+    k = mm.value
+    if info.value == -4:
+        raise FeastError("feast_scsr_extreme: " + feast_last_error())
+    return FeastResult(info.value, E[:k].copy(), np.asfortranarray(x[:, :k]), res[:k].copy(), M.value,
+                       loop.value, eps.value, k, f, lo.value, hi.value)
+
+
+def feast_scsr_extreme_dev(n: int, ia, ja, a, ib=None, jb=None, b=None, fpm=None, m0: int = 2, x=None,
+                           work=None, stream=None) -> FeastResult:
+    """Device driver of the extreme-eigenvalue mode (tensors as for
+    feast_scsr_solve_dev); the interval found is in emin/emax."""
+    import torch
+
+    f = _fpm(fpm)
+    ia, ja, a = _dev(ia, torch.int32), _dev(ja, torch.int32), _dev(a, torch.float64)
+    nnzb = 0
+    if b is not None:
+        ib, jb, b = _dev(ib, torch.int32), _dev(jb, torch.int32), _dev(b, torch.float64)
+        nnzb = b.numel()
+    if x is None:
+        x = torch.zeros((m0, n), dtype=torch.float64, device=a.device)
+    x = _dev(x, torch.float64)
+    need = feast_scsr_workspace_bytes(n, a.numel(), nnzb, m0, f)
+    if work is None or work.numel() < need:
+        work = torch.empty(need, dtype=torch.uint8, device=a.device)
+    E = np.zeros(m0)
+    res = np.zeros(m0)
+    M, loop, info, mm = _i(0), _i(0), _i(0), _i(m0)
+    eps, lo, hi = _d(0), _d(0), _d(0)
+    library().feast_scsr_extreme_dev(n, a.numel(), _ptr(ia), _ptr(ja), _ptr(a), nnzb, _ptr(ib), _ptr(jb),
+                                     _ptr(b), _ptr(f), C.byref(lo), C.byref(hi), C.byref(mm), _ptr(E), _ptr(x),
+                                     C.byref(M), _ptr(res), C.byref(eps), C.byref(loop), C.byref(info),
+                                     _ptr(work), work.numel(), _stream(stream))
+    if info.value == -4:
+        raise FeastError("feast_scsr_extreme_dev: " + feast_last_error())
+    k = mm.value
+    return FeastResult(info.value, E[:k].copy(), x, res[:k].copy(), M.value, loop.value, eps.value, k, f,
+                       lo.value, hi.value)
 
 
 def feast_scsr_solve_batched(problems, fpm=None):

@@ -75,8 +75,10 @@ static int check_fpm(const int* fpm)
     if (fpm[3] < 0) return 104;
     if (fpm[4] != 0 && fpm[4] != 1) return 105;
     if (fpm[5] != 0 && fpm[5] != 1) return 106;
+    if (fpm[13] < 0 || fpm[13] > 2) return 114;
     if (fpm[15] != 0) return 116;
     if (fpm[17] <= 0) return 118;
+    if (fpm[39] < -1 || fpm[39] > 1) return 140;
     if (fpm[41] != 0 && fpm[41] != 1) return 142;
     if (fpm[44] < 0 || fpm[44] > 16) return 145;
     if (fpm[45] < 1) return 146;
@@ -347,6 +349,81 @@ __global__ void k_random_block(long long total, unsigned long long seed, double*
     }
 }
 
+// ---------------------------------------------------------------- extreme-eigenvalue search kernels
+// Diagonal of a CSR matrix; *offdiag is set when a row stores a nonzero
+// off-diagonal value.
+__global__ void k_csr_diag(int n, const int* ia, const int* ja, const double* v, double* d, int* offdiag)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double di = 0.0;
+        bool off = false;
+        for (int p = ia[i]; p < ia[i + 1]; ++p) {
+            if (ja[p] == i) di += v[p];
+            else if (v[p] != 0.0) off = true;
+        }
+        d[i] = di;
+        if (off) *offdiag = 1;
+    }
+}
+
+// Gershgorin discs of the rows: centre m_ii, radius sum_{j != i} |m_ij|, of
+// M itself (scale == NULL) or of S^{-1/2} M S^{-1/2} with S = diag(scale).
+// Per block: part[2 b] = min(centre - radius), part[2 b + 1] = max(centre + radius).
+__global__ void __launch_bounds__(256) k_gersh(int n, const int* ia, const int* ja, const double* v,
+                                               const double* scale, double* part)
+{
+    __shared__ double slo[256], shi[256];
+    double lo = INFINITY, hi = -INFINITY;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double si = scale ? scale[i] : 1.0;
+        double c = 0.0, r = 0.0;
+        for (int p = ia[i]; p < ia[i + 1]; ++p) {
+            const int j = ja[p];
+            if (j == i) c += v[p];
+            else r += scale ? fabs(v[p]) / sqrt(si * scale[j]) : fabs(v[p]);
+        }
+        if (scale) c /= si;
+        lo = fmin(lo, c - r);
+        hi = fmax(hi, c + r);
+    }
+    slo[threadIdx.x] = lo;
+    shi[threadIdx.x] = hi;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + o]);
+            shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = slo[0];
+        part[2 * blockIdx.x + 1] = shi[0];
+    }
+}
+
+__global__ void k_negate(long long total, const double* a, double* b)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x)
+        b[i] = -a[i];
+}
+
+// Reverse the order of the columns c0 .. c1-1 of a column-major n-row block.
+__global__ void k_reverse_cols(int n, int c0, int c1, double* x)
+{
+    const long long half = (c1 - c0) / 2;
+    const long long total = half * n;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int c = c0 + (int)(idx / n), i = (int)(idx % n);
+        const int o = c1 - 1 - (c - c0);
+        const double t = x[(size_t)c * n + i];
+        x[(size_t)c * n + i] = x[(size_t)o * n + i];
+        x[(size_t)o * n + i] = t;
+    }
+}
+
 // Optional per-kernel timing (fpm(53) = 1): CUDA events recorded on the
 // solve's stream around every COCG launch and every Rayleigh-Ritz phase.
 struct Prof {
@@ -606,7 +683,8 @@ int run_feast(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, int* fpm, dou
     }
     CK(cudaGetLastError());
     size_t ph0 = 0;
-    if (fpm[4] == 1) {
+    const int mode14 = fpm[13];  // 1: return the filtered block, 2: stochastic count
+    if (fpm[4] == 1 && mode14 == 0) {
         // a given subspace is tested by Rayleigh-Ritz before any filtering, so
         // a converged subspace (e.g. a previous solution) returns at loop 0
         CK(cudaMemcpyAsync(B.Q, B.Y, sizeof(double) * blk, cudaMemcpyDeviceToDevice, s));
@@ -625,6 +703,45 @@ int run_feast(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, int* fpm, dou
     std::vector<int> itmax(P.nbatch);
     long long total_iters = 0;
     CK(cudaMemcpyAsync(itmax.data(), B.iter_max, sizeof(int) * P.nbatch, cudaMemcpyDeviceToHost, s));
+    if (mode14 != 0) {
+        // one contour pass only (fpm(14) = 1 or 2): no Rayleigh-Ritz
+        CK(cudaStreamSynchronize(s));
+        for (int b = 0; b < P.nbatch; ++b) total_iters += itmax[b];
+        fpm[59] = (int)std::min<long long>(total_iters, 2147483647LL);
+        for (int c = 0; c < m0; ++c) { e_host[c] = 0.0; res_host[c] = 0.0; }
+        *M_out = 0;
+        *loop_out = 0;
+        *epsout = 0.0;
+        if (mode14 == 1) {
+            // the filtered block Q, column-major, into X (guide info 4)
+            std::vector<int> id(m0);
+            for (int c = 0; c < m0; ++c) id[c] = c;
+            CK(cudaMemcpyAsync(B.perm, id.data(), sizeof(int) * m0, cudaMemcpyHostToDevice, s));
+            k_gather_cols<<<grid_for(blk), 256, 0, s>>>(n, m0, m0, B.Q, B.perm, x_dev);
+            count_launches(1);
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(s));
+            return 4;
+        }
+        // stochastic count (guide info 5): the probes are the columns of Y
+        // (E[y y^T] = I), Q = rho(B^{-1}A) Y, and the mean of y_j^T Q_j
+        // estimates trace(rho(B^{-1}A)), the number of eigenvalues inside
+        CK(launch_coldot_f64(n, m0, B.Y, B.Q, B.rpart, B.res, s));
+        std::vector<double> t(m0);
+        CK(cudaMemcpyAsync(t.data(), B.res, sizeof(double) * m0, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        double sum = 0.0, sum2 = 0.0;
+        for (int c = 0; c < m0; ++c) {
+            sum += t[c];
+            sum2 += t[c] * t[c];
+        }
+        const double mean = sum / m0;
+        const double var = m0 > 1 ? (sum2 - m0 * mean * mean) / (m0 - 1) : 0.0;
+        e_host[0] = mean;
+        if (m0 > 1) e_host[1] = std::sqrt(std::max(var, 0.0) / m0);
+        *M_out = (int)std::max(0.0, std::floor(mean + 0.5));
+        return 5;
+    }
 
     std::vector<double> lam(m0), res(m0);
     int mk = m0, M = 0, info = 0, k = 0;
@@ -737,12 +854,259 @@ int run_feast(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, int* fpm, dou
 }  // namespace
 
 // ---------------------------------------------------------------- device driver
+// ---------------------------------------------------------------- extreme-eigenvalue search (fpm(40) = -1 / +1)
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+static constexpr int kGershBlocks = 1024;
+
+// Workspace beyond the solver's own: -A (largest mode), diag(B), Gershgorin
+// partials and a flag.
+static size_t extreme_extra_bytes(int n, int nnz_a)
+{
+    return al256((size_t)nnz_a * sizeof(double)) + al256((size_t)n * sizeof(double)) +
+           al256(2 * kGershBlocks * sizeof(double)) + 512;
+}
+
 extern "C" size_t feast_scsr_workspace_bytes(int n, int nnz_a, int nnz_b, int m0, const int* fpm)
 {
     if (n <= 0 || m0 <= 0 || !fpm) return 0;
     Plan P = make_plan(n, nnz_a, nnz_b, m0, fpm);
     Bufs B;
-    return carve(P, nullptr, B);
+    const size_t base = carve(P, nullptr, B);
+    return fpm[39] != 0 ? al256(base) + extreme_extra_bytes(n, nnz_a) : base;
+}
+
+// Smallest and largest Gershgorin bound over the rows (scaled by diag(scale)
+// when given).  Synchronises the stream.
+static int gersh_bounds(const int* ia, const int* ja, const double* v, int n, const double* scale, double* part,
+                        cudaStream_t s, double* lo, double* hi)
+{
+    const int blocks = std::max(1, std::min(kGershBlocks, (n + 255) / 256));
+    k_gersh<<<blocks, 256, 0, s>>>(n, ia, ja, v, scale, part);
+    count_launches(1);
+    CK(cudaGetLastError());
+    std::vector<double> h(2 * (size_t)blocks);
+    CK(cudaMemcpyAsync(h.data(), part, sizeof(double) * 2 * blocks, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *lo = INFINITY;
+    *hi = -INFINITY;
+    for (int b = 0; b < blocks; ++b) {
+        *lo = std::min(*lo, h[2 * b]);
+        *hi = std::max(*hi, h[2 * b + 1]);
+    }
+    return 0;
+}
+
+// Bounds [lo, hi] of the spectrum of the pencil (A, B): Gershgorin discs of A
+// (B = I), of D^{-1/2} A D^{-1/2} (B = D diagonal), or, for a general B whose
+// Gershgorin interval is [bl, bu] with bl > 0, the bounds of the quotient
+// x^T A x / x^T B x from A's interval [al, au]: [min(al/bl, al/bu),
+// max(au/bl, au/bu)].  Returns 0, 7 when B cannot be shown positive definite
+// this way, -4 on a CUDA error.
+static int pencil_bounds(const Csr& A, const Csr& Bm, double* bdiag, int* flag, double* part, cudaStream_t s,
+                         double* lo, double* hi)
+{
+    const int n = A.n;
+    if (!Bm.v) return gersh_bounds(A.ia, A.ja, A.v, n, nullptr, part, s, lo, hi);
+    CK(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    k_csr_diag<<<grid_for(n), 256, 0, s>>>(n, Bm.ia, Bm.ja, Bm.v, bdiag, flag);
+    count_launches(1);
+    CK(cudaGetLastError());
+    int offdiag = 0;
+    CK(cudaMemcpyAsync(&offdiag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    double bl = 0.0, bu = 0.0;
+    int r = gersh_bounds(Bm.ia, Bm.ja, Bm.v, n, nullptr, part, s, &bl, &bu);  // synchronises
+    if (r) return r;
+    if (!(bl > 0.0)) return 7;
+    if (!offdiag) return gersh_bounds(A.ia, A.ja, A.v, n, bdiag, part, s, lo, hi);
+    double al = 0.0, au = 0.0;
+    r = gersh_bounds(A.ia, A.ja, A.v, n, nullptr, part, s, &al, &au);
+    if (r) return r;
+    *lo = std::min(al / bl, al / bu);
+    *hi = std::max(au / bl, au / bu);
+    return 0;
+}
+
+// The k = M0/2 lowest eigenpairs of (A, B) (fpm(40) = -1), or the k largest
+// (fpm(40) = +1, the lowest of (-A, B) with the signs turned back).
+//  1. Emin just below the Gershgorin lower bound of the pencil.
+//  2. Emax by a search on the stochastic count (fpm(14) = 2 machinery, up to
+//     32 seeded probes, the solver's contour settings) for an interval that
+//     holds between 1.15 k and 1.5 k eigenvalues: grow the interval until the
+//     count passes 1.15 k, then interpolate a power law count ~ span^p
+//     between the bracketing spans (bisection of the log span as a fallback).
+//  3. A normal solve on [Emin, Emax] with M0 = 2k; if it finds fewer than k
+//     eigenvalues inside the interval grows by 35 %, if the subspace is too
+//     small it shrinks by 20 %, each retry starting from the Ritz vectors just
+//     found.
+//  4. Output: M = k, E[0..k-1] the wanted eigenvalues ascending, the other
+//     Ritz values after them, and the interval [emin, emax] that holds
+//     exactly the k wanted eigenvalues (emax midway between the k-th and the
+//     next Ritz value inside the searched interval when one was found).
+// Returns the solver's info (0, or 2 when the last solve did not converge),
+// 7 when no suitable interval was found, or an error code.
+static int extreme_solve(int n, int nnz_a, const int* d_ia, const int* d_ja, const double* d_a, int nnz_b,
+                         const int* d_ib, const int* d_jb, const double* d_b, int* fpm, double* emin_io,
+                         double* emax_io, int* m0, double* e, double* d_x, int* m, double* res, double* epsout,
+                         int* loop, void* d_work, size_t work_bytes, cudaStream_t s)
+{
+    const int M0 = *m0, k = M0 / 2, sign = fpm[39];
+    Plan Pm = make_plan(n, nnz_a, d_b ? nnz_b : 0, M0, fpm);
+    Bufs Bw;
+    const size_t need = carve(Pm, nullptr, Bw);
+    if (!d_work || work_bytes < al256(need) + extreme_extra_bytes(n, nnz_a)) return -120;
+    char* xp = (char*)d_work + al256(need);
+    double* negA = (double*)xp;
+    xp += al256((size_t)nnz_a * sizeof(double));
+    double* bdiag = (double*)xp;
+    xp += al256((size_t)n * sizeof(double));
+    double* part = (double*)xp;
+    xp += al256(2 * kGershBlocks * sizeof(double));
+    int* flag = (int*)xp;
+    const double* av = d_a;
+    if (sign > 0) {
+        k_negate<<<grid_for(nnz_a), 256, 0, s>>>(nnz_a, d_a, negA);
+        count_launches(1);
+        CK(cudaGetLastError());
+        av = negA;
+    }
+    Csr A{n, nnz_a, d_ia, d_ja, av}, Bm{n, d_b ? nnz_b : 0, d_ib, d_jb, d_b};
+    double lo = 0.0, hi = 0.0;
+    int r = pencil_bounds(A, Bm, bdiag, flag, part, s, &lo, &hi);
+    if (r) return r;
+    char line[256];
+    const double width = std::max(hi - lo, 1e-9 * std::max(1.0, std::fabs(lo)));
+    const double Emin = lo - 0.01 * width;
+    const double span_max = hi + 0.01 * width - Emin;
+    snprintf(line, sizeof(line), "extreme search: spectrum bounds [%.10E, %.10E], Emin %.10E\n", lo, hi, Emin);
+    log_line(fpm[0], line);
+
+    // ---- interval search on stochastic counts
+    int fpc[64];
+    memcpy(fpc, fpm, sizeof(fpc));
+    fpc[13] = 2;
+    fpc[4] = 0;
+    fpc[39] = 0;
+    fpc[0] = 0;
+    const int sp = std::max(2, std::min(M0, 32));
+    const Plan Pc = make_plan(n, nnz_a, Bm.nnz, sp, fpc);
+    auto count = [&](double E, double* est) -> int {
+        Bufs Bc;
+        carve(Pc, d_work, Bc);
+        int mm = sp, Mi = 0, lp = 0;
+        double eo = 0.0;
+        std::vector<double> et(sp), rt(sp);
+        CK(cudaMemsetAsync(Bc.work, 0, sizeof(unsigned long long), s));
+        const int rr = run_feast(Pc, Bc, A, Bm, fpc, Emin, E, &mm, et.data(), d_x, &Mi, rt.data(), &eo, &lp, s);
+        if (rr != 5) return rr < 0 ? rr : -2;
+        *est = et[0];
+        return 0;
+    };
+    const double t_lo = 1.15 * k, t_hi = 1.5 * k, t_mid = 1.3 * k;
+    double d = std::min(span_max, width * std::min(1.0, t_mid / n));
+    double dl = 0.0, nl = 0.0, dh = 0.0, nh = 0.0;
+    bool have_l = false, have_h = false, found = false;
+    for (int it = 0; it < 40; ++it) {
+        d = std::min(d, span_max);
+        double nu = 0.0;
+        r = count(Emin + d, &nu);
+        if (r) return r;
+        snprintf(line, sizeof(line), "extreme search: Emax %.10E  estimated count %.2f\n", Emin + d, nu);
+        log_line(fpm[0], line);
+        if ((nu >= t_lo && nu <= t_hi) || (nu < t_lo && d >= span_max)) {
+            found = true;
+            break;
+        }
+        if (nu < t_lo) { dl = d; nl = nu; have_l = true; }
+        else { dh = d; nh = nu; have_h = true; }
+        double dn;
+        if (!have_h) dn = d * std::min(8.0, std::max(1.25, nu > 0.5 ? t_mid / nu : 8.0));
+        else if (!have_l) dn = d * std::max(0.125, std::min(0.8, t_mid / nu));
+        else {
+            dn = std::sqrt(dl * dh);
+            if (nl > 0.5) {
+                const double pw = std::log(nh / nl) / std::log(dh / dl);
+                const double di = dl * std::pow(t_mid / nl, 1.0 / pw);
+                if (pw > 0.0 && di > dl && di < dh) dn = di;
+            }
+        }
+        d = dn;
+    }
+    if (!found) return 7;
+    double E = Emin + d;
+
+    // ---- solves on [Emin, E]
+    int fps[64];
+    memcpy(fps, fpm, sizeof(fps));
+    fps[39] = 0;
+    fps[13] = 0;
+    int info = 7, mk = M0;
+    for (int attempt = 0; attempt < 5; ++attempt) {
+        carve(Pm, d_work, Bw);
+        CK(cudaMemsetAsync(Bw.work, 0, sizeof(unsigned long long), s));
+        mk = M0;
+        r = run_feast(Pm, Bw, A, Bm, fps, Emin, E, &mk, e, d_x, m, res, epsout, loop, s);
+        if (r < 0) return r;
+        snprintf(line, sizeof(line), "extreme search: solve on [%.10E, %.10E]: info %d, %d inside\n", Emin, E, r, *m);
+        log_line(fpm[0], line);
+        if ((r == 0 || r == 2) && *m >= k) {
+            info = r;
+            break;
+        }
+        if (r == 3) E = Emin + 0.8 * (E - Emin);
+        else E = Emin + 1.35 * (E - Emin);
+        fps[4] = 1;  // start again from the Ritz vectors just found
+    }
+    fpm[59] = fps[59];
+    *m0 = mk;
+    if (info == 7) return 7;
+    const double Eout = *m > k ? 0.5 * (e[k - 1] + e[k]) : E;
+    *m = k;
+    if (sign > 0) {
+        for (int c = 0; c < mk; ++c) e[c] = -e[c];
+        std::reverse(e, e + k);
+        std::reverse(res, res + k);
+        std::reverse(e + k, e + mk);
+        std::reverse(res + k, res + mk);
+        k_reverse_cols<<<grid_for((long long)n * k), 256, 0, s>>>(n, 0, k, d_x);
+        k_reverse_cols<<<grid_for((long long)n * (mk - k + 1)), 256, 0, s>>>(n, k, mk, d_x);
+        count_launches(2);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(s));
+        *emin_io = -Eout;
+        *emax_io = -Emin;
+    } else {
+        *emin_io = Emin;
+        *emax_io = Eout;
+    }
+    return info;
+}
+
+extern "C" int feast_scsr_extreme_dev(int n, int nnz_a, const int* d_ia, const int* d_ja, const double* d_a,
+                                      int nnz_b, const int* d_ib, const int* d_jb, const double* d_b, int* fpm,
+                                      double* emin, double* emax, int* m0, double* e, double* d_x, int* m,
+                                      double* res, double* epsout, int* loop, int* info, void* d_work,
+                                      size_t work_bytes, void* stream)
+{
+    int inf = 0;
+    auto ret = [&](int v) { if (info) *info = v; return v; };
+    if (!fpm) return ret(-109);
+    if (n <= 0) return ret(202);
+    if (!m0 || *m0 < 2 || *m0 > n) return ret(201);
+    if ((inf = check_fpm(fpm))) return ret(inf);
+    if (fpm[39] != -1 && fpm[39] != 1) return ret(140);
+    if (fpm[13] != 0) return ret(114);
+    if (!d_ia || !d_ja || !d_a || nnz_a < 0) return ret(-103);
+    if (d_b && (!d_ib || !d_jb || nnz_b <= 0)) return ret(-106);
+    if (!emin) return ret(-110);
+    if (!emax) return ret(-111);
+    if (!e || !d_x || !m || !res || !epsout || !loop) return ret(-113);
+    g_err.clear();
+    g_prof.reset(fpm[52] == 1);
+    const long long l0 = launch_count();
+    inf = extreme_solve(n, nnz_a, d_ia, d_ja, d_a, nnz_b, d_ib, d_jb, d_b, fpm, emin, emax, m0, e, d_x, m, res,
+                        epsout, loop, d_work, work_bytes, (cudaStream_t)stream);
+    g_prof.out[15] = (double)(launch_count() - l0);
+    return ret(inf);
 }
 
 extern "C" int feast_scsr_solve_dev(int n, int nnz_a, const int* d_ia, const int* d_ja, const double* d_a,
@@ -758,6 +1122,7 @@ extern "C" int feast_scsr_solve_dev(int n, int nnz_a, const int* d_ia, const int
     if (!m0 || *m0 <= 0 || *m0 > n) return ret(201);
     if (!(emin < emax)) return ret(200);
     if ((inf = check_fpm(fpm))) return ret(inf);
+    if (fpm[39] != 0) return ret(140);  // extreme-eigenvalue search: feast_scsr_extreme_dev
     if (!d_ia || !d_ja || !d_a || nnz_a < 0) return ret(-103);
     if (d_b && (!d_ib || !d_jb || nnz_b <= 0)) return ret(-106);
     if (!e || !d_x || !m || !res || !epsout || !loop) return ret(-113);
@@ -840,9 +1205,13 @@ struct DevMem {
 
 }  // namespace
 
-extern "C" int feast_scsr_solve(char uplo, int n, const double* a, const int* ia, const int* ja, const double* b,
-                                const int* ib, const int* jb, int* fpm, double emin, double emax, int* m0,
-                                double* e, double* x, int* m, double* res, double* epsout, int* loop, int* info)
+// Host-memory driver shared by feast_scsr_solve (extreme = false: the
+// interval is an input) and feast_scsr_extreme (the interval is found and
+// returned): validates and expands the CSR, copies it to the device, runs the
+// device entry point and copies X back.
+static int host_driver(bool extreme, char uplo, int n, const double* a, const int* ia, const int* ja,
+                       const double* b, const int* ib, const int* jb, int* fpm, double* emin_io, double* emax_io,
+                       int* m0, double* e, double* x, int* m, double* res, double* epsout, int* loop, int* info)
 {
     auto ret = [&](int v) { if (info) *info = v; return v; };
     if (uplo != 'F' && uplo != 'L' && uplo != 'U') return ret(-101);
@@ -850,8 +1219,11 @@ extern "C" int feast_scsr_solve(char uplo, int n, const double* a, const int* ia
     if (!fpm) return ret(-109);
     int inf = check_fpm(fpm);
     if (inf) return ret(inf);
-    if (!(emin < emax)) return ret(200);
-    if (!m0 || *m0 <= 0 || *m0 > n) return ret(201);
+    if (!extreme && fpm[39] != 0) return ret(140);  // extreme-eigenvalue search: feast_scsr_extreme
+    if (extreme && fpm[39] != -1 && fpm[39] != 1) return ret(140);
+    if (extreme && fpm[13] != 0) return ret(114);
+    if (!extreme && !(*emin_io < *emax_io)) return ret(200);
+    if (!m0 || *m0 <= (extreme ? 1 : 0) || *m0 > n) return ret(201);
     if (!e) return ret(-113);
     if (!x) return ret(-114);
     if (!m) return ret(-115);
@@ -897,12 +1269,33 @@ extern "C" int feast_scsr_solve(char uplo, int n, const double* a, const int* ia
         HK(cudaMemcpy(d_b, bv.data(), sizeof(double) * bv.size(), cudaMemcpyHostToDevice));
     }
     if (fpm[4] == 1) HK(cudaMemcpy(d_x, x, sizeof(double) * (size_t)n * mm0, cudaMemcpyHostToDevice));
-    inf = feast_scsr_solve_dev(n, (int)aja.size(), d_ia, d_ja, d_a, hasB ? (int)bja.size() : 0, d_ib, d_jb, d_b,
-                               fpm, emin, emax, m0, e, d_x, m, res, epsout, loop, info, d_work, wb, s);
-    if (inf >= 0 || inf == -3 || inf == -2)
+    if (extreme)
+        inf = feast_scsr_extreme_dev(n, (int)aja.size(), d_ia, d_ja, d_a, hasB ? (int)bja.size() : 0, d_ib, d_jb,
+                                     d_b, fpm, emin_io, emax_io, m0, e, d_x, m, res, epsout, loop, info, d_work, wb, s);
+    else
+        inf = feast_scsr_solve_dev(n, (int)aja.size(), d_ia, d_ja, d_a, hasB ? (int)bja.size() : 0, d_ib, d_jb, d_b,
+                                   fpm, *emin_io, *emax_io, m0, e, d_x, m, res, epsout, loop, info, d_work, wb, s);
+    if ((inf >= 0 && inf != 5) || inf == -3 || inf == -2)  // info 5 (count only) leaves X alone
         HK(cudaMemcpy(x, d_x, sizeof(double) * (size_t)n * mm0, cudaMemcpyDeviceToHost));
 #undef HK
     return ret(inf);
+}
+
+extern "C" int feast_scsr_solve(char uplo, int n, const double* a, const int* ia, const int* ja, const double* b,
+                                const int* ib, const int* jb, int* fpm, double emin, double emax, int* m0,
+                                double* e, double* x, int* m, double* res, double* epsout, int* loop, int* info)
+{
+    return host_driver(false, uplo, n, a, ia, ja, b, ib, jb, fpm, &emin, &emax, m0, e, x, m, res, epsout, loop,
+                       info);
+}
+
+extern "C" int feast_scsr_extreme(char uplo, int n, const double* a, const int* ia, const int* ja, const double* b,
+                                  const int* ib, const int* jb, int* fpm, double* emin, double* emax, int* m0,
+                                  double* e, double* x, int* m, double* res, double* epsout, int* loop, int* info)
+{
+    if (!emin) { if (info) *info = -110; return -110; }
+    if (!emax) { if (info) *info = -111; return -111; }
+    return host_driver(true, uplo, n, a, ia, ja, b, ib, jb, fpm, emin, emax, m0, e, x, m, res, epsout, loop, info);
 }
 
 // ---------------------------------------------------------------- kernel-level entry points
@@ -1210,6 +1603,8 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
     if (!out) return -104;
     int inf = check_fpm(fpm);
     if (inf) return inf;
+    if (fpm[13] != 0) return 114;  // one-pass modes are single-problem only
+    if (fpm[39] != 0) return 140;
     g_err.clear();
     const int ne = fpm[1];
     const bool fp64 = fpm[41] == 0;

@@ -146,6 +146,9 @@ cudaError_t launch_residual_f64(int n, int m, const int* ia, const int* ja, cons
                                 const double* lam, double* R, double* part, unsigned* counter,
                                 double* res, double alpha, cudaStream_t s);
 size_t residual_partial_doubles(int n, int m);
+// t[c] = sum_i X[i][c] Y[i][c] (row-major n x m), deterministic; part as for the residuals
+cudaError_t launch_coldot_f64(int n, int m, const double* X, const double* Y, double* part, double* t,
+                              cudaStream_t s);
 
 // ---------------------------------------------------------------- reduced eigensolver (k_eig.cu)
 // Symmetric eigen-decomposition of the m x m row-major matrix A (destroyed):

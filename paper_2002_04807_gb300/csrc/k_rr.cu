@@ -392,4 +392,62 @@ cudaError_t launch_residual_f64(int n, int m, const int* ia, const int* ja, cons
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- column dots
+// t[c] = sum_i X[i][c] Y[i][c] over row-major n x m blocks (the probe terms
+// y_c^T Q_c of the stochastic eigenvalue count).  Pass 1: per row block of
+// RR_RB rows, one warp-row sweep per 32 columns, fixed-order partials
+// part[rb][c]; pass 2: fixed-order sum over the row blocks.
+__global__ void __launch_bounds__(256) coldot_rows(int n, int m, const double* __restrict__ X,
+                                                   const double* __restrict__ Y, double* __restrict__ part)
+{
+    __shared__ double sh[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nrb = (n + RR_RB - 1) / RR_RB;
+    const int nchunk = (m + 31) / 32;
+    for (int it = blockIdx.x; it < nrb * nchunk; it += gridDim.x) {
+        const int rb = it / nchunk, ch = it % nchunk;
+        const int c = ch * 32 + lane;
+        double acc = 0.0;
+        if (c < m)
+            for (int i = rb * RR_RB + warp; i < min(n, (rb + 1) * RR_RB); i += 8)
+                acc = fma(X[(size_t)i * m + c], Y[(size_t)i * m + c], acc);
+        sh[warp][lane] = acc;
+        __syncthreads();
+        if (warp == 0 && c < m) {
+            double t = 0.0;
+            for (int w = 0; w < 8; ++w) t += sh[w][lane];
+            part[(size_t)rb * m + c] = t;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void coldot_cols(int n, int m, const double* __restrict__ part, double* __restrict__ t)
+{
+    const int nrb = (n + RR_RB - 1) / RR_RB;
+    const int c = blockIdx.x;
+    __shared__ double sh[256];
+    double a = 0.0;
+    for (int rb = threadIdx.x; rb < nrb; rb += blockDim.x) a += part[(size_t)rb * m + c];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) t[c] = sh[0];
+}
+
+// part: at least residual_partial_doubles(n, m) / 2 doubles.
+cudaError_t launch_coldot_f64(int n, int m, const double* X, const double* Y, double* part, double* t, cudaStream_t s)
+{
+    if (n <= 0 || m <= 0) return cudaSuccess;
+    const long long items = (long long)((n + RR_RB - 1) / RR_RB) * ((m + 31) / 32);
+    const long long cap = (long long)num_sms() * 8;
+    coldot_rows<<<(int)(items < cap ? items : cap), 256, 0, s>>>(n, m, X, Y, part);
+    coldot_cols<<<m, 256, 0, s>>>(n, m, part, t);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
 }  // namespace feast

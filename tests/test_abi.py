@@ -114,6 +114,54 @@ def test_argument_errors_are_host_side(pkg):
     assert run(uplo="L") == -105
 
 
+def test_one_pass_and_extreme_mode_argument_checks(pkg):
+    """fpm(14) and fpm(40) validation of the solve and extreme-mode entry
+    points (guide parameter table: fpm(14) in {0,1,2}, fpm(40) in {-1,0,1})."""
+    A = fw.laplacian_1d(20)
+    base = dict(uplo="F", n=20, a=A.data, ia=A.indptr, ja=A.indices)
+    f = pkg.feast_init()
+    f[13] = 3
+    assert pkg.feast_scsr_solve(**base, fpm=f, emin=0.0, emax=0.5, m0=6).info == 114
+    f = pkg.feast_init()
+    f[39] = -1  # the interval-search mode has its own entry point
+    assert pkg.feast_scsr_solve(**base, fpm=f, emin=0.0, emax=0.5, m0=6).info == 140
+    f[39] = 2
+    assert pkg.feast_scsr_extreme(**base, fpm=f, m0=6).info == 140
+    f[39] = 0
+    assert pkg.feast_scsr_extreme(**base, fpm=f, m0=6).info == 140
+    f[39] = 1
+    assert pkg.feast_scsr_extreme(**base, fpm=f, m0=1).info == 201
+    f[13] = 2
+    assert pkg.feast_scsr_extreme(**base, fpm=f, m0=6).info == 114
+    lib = pkg.library()
+    fz = pkg.feast_init()
+    fz[39] = -1
+    # NULL interval pointers
+    import ctypes as C
+
+    E, X, R = np.zeros(6), np.zeros((20, 6)), np.zeros(6)
+    M, L, I, m0 = C.c_int(0), C.c_int(0), C.c_int(0), C.c_int(6)
+    eps = C.c_double(0)
+    ia, ja, a = (np.ascontiguousarray(A.indptr, np.int32), np.ascontiguousarray(A.indices, np.int32),
+                 np.ascontiguousarray(A.data))
+    p = lambda v: v.ctypes.data_as(C.c_void_p)
+    r = lib.feast_scsr_extreme(b"F", 20, p(a), p(ia), p(ja), None, None, None, p(fz), None, None, C.byref(m0),
+                               p(E), p(X), C.byref(M), p(R), C.byref(eps), C.byref(L), C.byref(I))
+    assert r == -110
+    lo = C.c_double(0)
+    r = lib.feast_scsr_extreme(b"F", 20, p(a), p(ia), p(ja), None, None, None, p(fz), C.byref(lo), None,
+                               C.byref(m0), p(E), p(X), C.byref(M), p(R), C.byref(eps), C.byref(L), C.byref(I))
+    assert r == -111
+
+
+def test_extreme_workspace_includes_search_buffers(pkg):
+    f = pkg.feast_init()
+    base = pkg.feast_scsr_workspace_bytes(4096, 20000, 0, 40, f)
+    f[39] = 1
+    ext = pkg.feast_scsr_workspace_bytes(4096, 20000, 0, 40, f)
+    assert ext >= base + 20000 * 8 + 4096 * 8
+
+
 def test_no_cpu_fallback_without_gpu(pkg):
     """With valid arguments the host driver goes to the GPU; without one it
     must fail with the CUDA error code, never compute on the CPU."""
