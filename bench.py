@@ -46,7 +46,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--side", type=int, default=64)
+    ap.add_argument("--side", type=int, default=None, help="grid side (default 64; 96 for --workload stencil27)")
+    ap.add_argument("--workload", default="laplace3d", choices=["laplace3d", "stencil27"],
+                    help="laplace3d: 7-point 3D Laplacian + potential, B = I (the headline line); stencil27: "
+                         "27-point generalized problem, B diagonal, lowest 200 eigenvalues, M0 = 300, Ne = 16")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -419,9 +422,143 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+# ---------------------------------------------------------------- 27-point generalized workload
+def run_stencil27(args):
+    """The 27-point generalized problem (B diagonal): the interval holding the
+    200 lowest eigenvalues comes from the library's extreme-eigenvalue mode
+    (fpm(40) = -1, M0 = 400, timed apart), then mixed and FP64 solves with
+    M0 = 300, Ne = 16 on it are timed.  The mixed result is checked on the CPU
+    in FP64: residuals, X^T B X = I, eigenvalue count; and against the FP64
+    solve."""
+    import scipy.sparse as sps
+    import torch
+
+    import feast_workloads as fw
+    import paper_2002_04807_gb300 as pkg
+    from paper_2002_04807_gb300 import build
+
+    rank, ws, local = dist_setup()
+    torch.cuda.set_device(local)
+    build.build()
+    pkg.library()
+    p = fw.stencil27_generalized(side=args.side)
+    k = p.notes["target_count"]
+    dev = torch.device("cuda", local)
+    ia, ja, av = (torch.as_tensor(p.A.indptr).to(dev), torch.as_tensor(p.A.indices).to(dev),
+                  torch.as_tensor(p.A.data).to(dev))
+    ib, jb, bv = (torch.as_tensor(p.B.indptr).to(dev), torch.as_tensor(p.B.indices).to(dev),
+                  torch.as_tensor(p.B.data).to(dev))
+    stream = torch.cuda.Stream(device=dev)
+    # interval: the k lowest eigenpairs by the extreme-eigenvalue search
+    fx = fpm_for(pkg, p, True, False)
+    fx[4], fx[39] = 0, -1
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        t0 = time.time()
+        rx = pkg.feast_scsr_extreme_dev(p.n, ia, ja, av, ib=ib, jb=jb, b=bv, fpm=fx, m0=2 * k, stream=stream)
+        torch.cuda.synchronize()
+        t_search = time.time() - t0
+    if rx.info != 0:
+        raise RuntimeError(f"extreme-eigenvalue search info {rx.info}")
+    # the searched interval holds exactly the k lowest eigenvalues; its lower
+    # end (the Gershgorin bound of the scaled pencil) lies well below the
+    # spectrum, which makes the contour taller and the inexact shifted solves
+    # far better conditioned than Emin = 0 would (8 loops instead of 30)
+    emin, emax = rx.emin, rx.emax
+    del rx
+    torch.cuda.empty_cache()
+    y0 = torch.as_tensor(np.ascontiguousarray(p.y0().T)).to(dev)
+    x = torch.empty_like(y0)
+
+    def solve(f):
+        x.copy_(y0)
+        r = pkg.feast_scsr_solve_dev(p.n, ia, ja, av, ib=ib, jb=jb, b=bv, fpm=f, emin=emin, emax=emax, m0=p.m0,
+                                     x=x, stream=stream)
+        if r.info != 0:
+            raise RuntimeError(f"FEAST info {r.info}")
+        return r, int(np.sum(r.res[: r.M] <= RES_TOL))
+
+    def timed(f, steps, warmup):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                solve(f)
+            torch.cuda.synchronize()
+            barrier(ws)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            conv, prof = 0, None
+            for _ in range(steps):
+                r, c = solve(f)
+                conv += c
+                pr = pkg.feast_last_profile()
+                if prof is None:
+                    prof = dict(pr)
+                else:
+                    for kk in ("cocg_a_ms", "cocg_b_ms", "cocg_a_launches", "cocg_b_launches", "group_iterations",
+                               "filter_ms", "project_ms", "reduce_ms", "ritz_ms", "launches"):
+                        prof[kk] += pr[kk]
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), ws)
+        return r, throughput(conv, e0.elapsed_time(e1), ws), ms, prof
+
+    clocks = Clocks(local)
+    clocks.start()
+    r, value, ms, pr = timed(fpm_for(pkg, p, True, True), args.steps, args.warmup)
+    clk = clocks.stop()
+    M = r.M
+    E = r.E[:M].copy()
+    X = x.cpu().numpy().T[:, :M]  # column-major n x m0 block, first M columns
+    fp64 = None
+    if args.fp64_steps > 0:
+        r64, v64, ms64, _ = timed(fpm_for(pkg, p, False, False), args.fp64_steps, 0)
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps, "loops": r64.loop,
+                "M": r64.M, "mixed_over_fp64": value / v64,
+                "max_rel_eig_diff_vs_mixed": float(np.max(np.abs(r64.E[:M] - E) / np.abs(E)))}
+    # FP64 a-posteriori checks on the CPU
+    A = sps.csr_matrix((p.A.data, p.A.indices, p.A.indptr), shape=(p.n, p.n))
+    Bd = p.B.data
+    AX, BX = A @ X, Bd[:, None] * X
+    alpha = max(abs(emin), abs(emax))
+    res = np.linalg.norm(AX - BX * E[None, :], axis=0) / (alpha * np.linalg.norm(BX, axis=0))
+    checks = {"M": M, "wanted": k, "max_residual_cpu_fp64": float(res.max()),
+              "max_abs_XtBX_minus_I": float(np.abs(X.T @ BX - np.eye(M)).max())}
+    n, W, mt, sc = pr["n"], pr["W"], pr["mt"], pr["complex_bytes"]
+    live = (p.m0 * min(W / mt, p.ne)) / (pr["groups"] * W)
+    tile = n * W * sc * live
+    mat = p.A.nnz * (4 + (4 if sc == 8 else 8)) + (p.n + 1) * 4
+    gbs_a = (pr["group_iterations"] * 5 * tile + pr["cocg_a_launches"] * mat) / (pr["cocg_a_ms"] / 1e3) / 1e9
+    gbs_b = pr["group_iterations"] * (4 * tile + n * mt * 2 * 4 * live) / (pr["cocg_b_ms"] / 1e3) / 1e9
+    peak = FALLBACK_HBM_GBS
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        pass
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "c32 solves + f64 Rayleigh-Ritz",
+               "data": "synthetic (seeded generator, no dataset)",
+               "config": {"workload": f"stencil27_generalized_{args.side}^3_Bdiag_U[1,2]_seed2", "N": p.n,
+                          "nnz": p.A.nnz, "M0": p.m0, "Ne": p.ne, "contour_ratio_pct": p.ratio,
+                          "interval": [emin, emax], "B": "diagonal U[1,2]", "tol": RES_TOL,
+                          "interval_from": "feast_scsr_extreme_dev, fpm(40)=-1, M0 = 2 x 200",
+                          "interval_search_s": t_search, "loops": r.loop, "precision": "mixed fpm(42)=1"},
+               "fp64": fp64, "checks": checks, "clocks": clk,
+               "cocg_gbs": {"step_a": gbs_a, "step_b": gbs_b, "peak": peak},
+               "phases_ms_per_step": {kk: pr[kk] / args.steps for kk in ("filter_ms", "project_ms", "reduce_ms",
+                                                                          "ritz_ms")},
+               "gpu_launches": int(pr["launches"])}
+        print(json.dumps(out))
+
+
 if __name__ == "__main__":
     a = parse()
+    if a.side is None:
+        a.side = 96 if a.workload == "stencil27" else 64
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "stencil27":
+        run_stencil27(a)
     else:
         run_gpu(a)

@@ -163,6 +163,29 @@ def test_generalized_27pt(pkg, mixed):
     check_against(r, ref, emax, B=B)
 
 
+@pytest.fixture(scope="module")
+def config3_shape():
+    """The 27-point generalized workload's generator (off-diagonals -U[0.5,1.5],
+    diagonal row-abs-sum + U[0.1,1], B = diag(U[1,2])) at 12^3 with its shape
+    scaled: the 100 lowest eigenvalues, M0 = 150, Ne = 16; the oracle solves it
+    with its banded LDL^T."""
+    p = fw.stencil27_generalized(side=12, count=100, m0=150, ne=16, emax=1.0)
+    d = 1 / np.sqrt(p.B.data)
+    ev = np.linalg.eigvalsh(d[:, None] * p.A.to_dense() * d[None, :])
+    emax = 0.5 * (ev[99] + ev[100])
+    p = fw.Problem(p.name, p.A, p.B, 0.0, emax, 150, 16, 100, 2)
+    ref = O.feast_scsr(p.A, p.B, 0.0, emax, 150, Y0=p.y0(), ne=16, ratio=100, tol_exp=10)
+    assert ref["M"] == 100 == O.count_below(p.A, p.B, emax)
+    return p, ref
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_generalized_27pt_config3_shape(pkg, config3_shape, mixed):
+    p, ref = config3_shape
+    r = run_gpu(pkg, p, mixed)
+    check_against(r, ref, p.emax, B=p.B)
+
+
 def test_node_batches_agree(pkg):
     """Solving the 16 nodes in batches of 4 gives the same eigenpairs."""
     p = fw.laplace3d_potential(side=12, count=16, m0=28, ne=16, seed=9)
