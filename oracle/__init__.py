@@ -85,12 +85,21 @@ def contour_gauss(ne: int, emin: float, emax: float, ratio: float):
     return z[0::2] + 1j * z[1::2], w[0::2] + 1j * w[1::2]
 
 
-def rho(ne: int, emin: float, emax: float, ratio: float, lam):
+def contour_trapezoid(ne: int, emin: float, emax: float, ratio: float):
+    """Half-contour trapezoidal (midpoint) nodes z_e and weights w_e (fpm(16)=1)."""
+    z = np.zeros(2 * ne)
+    w = np.zeros(2 * ne)
+    lib().orc_contour_trapezoid(C.c_int(ne), C.c_double(emin), C.c_double(emax), C.c_double(ratio),
+                                _ptr(z), _ptr(w))
+    return z[0::2] + 1j * z[1::2], w[0::2] + 1j * w[1::2]
+
+
+def rho(ne: int, emin: float, emax: float, ratio: float, lam, rule: int = 0):
     z = np.zeros(2 * ne)
     w = np.zeros(2 * ne)
     L = lib()
-    L.orc_contour_gauss(C.c_int(ne), C.c_double(emin), C.c_double(emax), C.c_double(ratio),
-                        _ptr(z), _ptr(w))
+    nodes = L.orc_contour_trapezoid if rule == 1 else L.orc_contour_gauss
+    nodes(C.c_int(ne), C.c_double(emin), C.c_double(emax), C.c_double(ratio), _ptr(z), _ptr(w))
     lam = np.atleast_1d(np.asarray(lam, dtype=np.float64))
     return np.array([L.orc_rho(C.c_int(ne), _ptr(z), _ptr(w), C.c_double(v)) for v in lam])
 
@@ -188,7 +197,7 @@ def residuals(A, B, X, lam, emin, emax):
 
 
 def filter_block(A, B, ne, emin, emax, ratio, Y, lam=None, rii=False, solver="direct",
-                 solve_tol=1e-13):
+                 solve_tol=1e-13, rule=0):
     """One quadrature filter pass on the block Y (n x m): classic form
     sum_e Re(w_e (z_e B - A)^{-1} B Y), or with rii the residual-inverse form
     on (X = Y, lam).  Returns Q (n x m, column-major)."""
@@ -201,13 +210,13 @@ def filter_block(A, B, ne, emin, emax, ratio, Y, lam=None, rii=False, solver="di
     st = lib().orc_filter(C.c_int(n), _ptr(ip), _ptr(ix), _ptr(v), _ptr(bip), _ptr(bix), _ptr(bv),
                           C.c_int(ne), C.c_double(emin), C.c_double(emax), C.c_double(ratio), C.c_int(m),
                           _ptr(Y), _ptr(lam_a), C.c_int(1 if rii else 0), _ptr(Q),
-                          C.c_int(0 if solver == "direct" else 1), C.c_double(solve_tol))
+                          C.c_int(0 if solver == "direct" else 1), C.c_double(solve_tol), C.c_int(rule))
     if st:
         raise RuntimeError("oracle filter failed")
     return Q
 
 
-def stochastic_count(A, B, ne, emin, emax, ratio, Y, solver="direct", solve_tol=1e-13):
+def stochastic_count(A, B, ne, emin, emax, ratio, Y, solver="direct", solve_tol=1e-13, rule=0):
     """Stochastic estimate of the eigenvalue count inside the contour (fpm(14)=2;
     ratio = ellipse axis ratio, fpm(18)/100):
     mean over the probe columns of Y of y^T rho(B^{-1}A) y, with its standard
@@ -220,7 +229,7 @@ def stochastic_count(A, B, ne, emin, emax, ratio, Y, solver="direct", solve_tol=
     st = lib().orc_stochastic_count(C.c_int(n), _ptr(ip), _ptr(ix), _ptr(v), _ptr(bip), _ptr(bix), _ptr(bv),
                                     C.c_int(ne), C.c_double(emin), C.c_double(emax), C.c_double(ratio),
                                     C.c_int(m), _ptr(Y), C.c_int(0 if solver == "direct" else 1),
-                                    C.c_double(solve_tol), C.byref(est), C.byref(sem))
+                                    C.c_double(solve_tol), C.byref(est), C.byref(sem), C.c_int(rule))
     if st:
         raise RuntimeError("oracle stochastic count failed")
     return est.value, sem.value
@@ -248,7 +257,7 @@ def feastinit():
 
 
 def feast_scsr(A, B, emin, emax, m0, Y0=None, X0=None, ne=8, ratio=30, tol_exp=10, maxloop=20,
-               solver="direct", solve_tol=1e-13, rii=False):
+               solver="direct", solve_tol=1e-13, rii=False, rule=0):
     """Plain FP64 FEAST on a real symmetric CSR problem.
 
     Returns a dict with E (inside first, ascending), X (n x m0', column-major),
@@ -260,6 +269,7 @@ def feast_scsr(A, B, emin, emax, m0, Y0=None, X0=None, ne=8, ratio=30, tol_exp=1
     fpm[2] = tol_exp
     fpm[3] = maxloop
     fpm[17] = ratio
+    fpm[15] = rule
     X = np.zeros((n, m0), order="F")
     if X0 is not None:
         fpm[4] = 1

@@ -108,6 +108,33 @@ int orc_contour_gauss(int ne, double emin, double emax, double ratio, double* z,
     return 0;
 }
 
+/* Trapezoidal rule on the same half contour (fpm(16)=1): the midpoints
+ * theta_e = pi (e - 1/2) / ne, e = 1..ne, each with theta-weight pi/ne.  A
+ * rule with theta-nodes and weights (theta_e, v_e) gives
+ * w_e = (v_e / (i pi)) z'(theta_e) = (v_e r / pi)(a cos theta_e + i sin theta_e),
+ * here w_e = (r / ne)(a cos theta_e + i sin theta_e).  With the conjugate
+ * lower half these are the 2 ne equally spaced points of the full contour. */
+int orc_contour_trapezoid(int ne, double emin, double emax, double ratio, double* z, double* w)
+{
+    if (ne < 1) return -1;
+    double c = 0.5 * (emin + emax), r = 0.5 * (emax - emin);
+    for (int e = 0; e < ne; ++e) {
+        double th = M_PI * (e + 0.5) / ne;
+        z[2 * e] = c + r * cos(th);
+        z[2 * e + 1] = ratio * r * sin(th);
+        w[2 * e] = r * ratio * cos(th) / ne;
+        w[2 * e + 1] = r * sin(th) / ne;
+    }
+    return 0;
+}
+
+/* Nodes of the quadrature rule fpm(16): 0 Gauss-Legendre, 1 trapezoidal. */
+static int contour_nodes(int rule, int ne, double emin, double emax, double ratio, double* z, double* w)
+{
+    return rule == 1 ? orc_contour_trapezoid(ne, emin, emax, ratio, z, w)
+                     : orc_contour_gauss(ne, emin, emax, ratio, z, w);
+}
+
 /* Rational filter rho(lambda) = sum_e Re(w_e / (z_e - lambda)): the scalar the
  * quadrature applies to an eigenvector with eigenvalue lambda. */
 double orc_rho(int ne, const double* z, const double* w, double lam)
@@ -653,17 +680,18 @@ static int filter_rii(const ocsr* A, const ocsr* B, int ne, const double* z, con
 }
 
 /* Exported filter passes on a block (column-major n x m): rii = 0 applies the
- * classic quadrature to Y; rii = 1 the residual-inverse form to (X = Y, lam). */
+ * classic quadrature to Y; rii = 1 the residual-inverse form to (X = Y, lam);
+ * rule as fpm(16). */
 int orc_filter(int n, const int* ip, const int* ix, const double* av,
                const int* bip, const int* bix, const double* bv,
                int ne, double emin, double emax, double ratio, int m, const double* Y,
-               const double* lam, int rii, double* Q, int solver, double solve_tol)
+               const double* lam, int rii, double* Q, int solver, double solve_tol, int rule)
 {
     ocsr A = {n, ip, ix, av}, Bm = {n, bip, bix, bv};
     const ocsr* B = bip ? &Bm : NULL;
     double* z = (double*)malloc(sizeof(double) * 2 * ne);
     double* w = (double*)malloc(sizeof(double) * 2 * ne);
-    orc_contour_gauss(ne, emin, emax, ratio, z, w);
+    contour_nodes(rule, ne, emin, emax, ratio, z, w);
     int st = rii ? filter_rii(&A, B, ne, z, w, m, Y, lam, Q, solver, solve_tol, NULL)
                  : filter_classic(&A, B, ne, z, w, m, Y, Q, solver, solve_tol, NULL);
     free(z);
@@ -684,10 +712,11 @@ int orc_filter(int n, const int* ip, const int* ix, const double* av,
 int orc_stochastic_count(int n, const int* ip, const int* ix, const double* av,
                          const int* bip, const int* bix, const double* bv,
                          int ne, double emin, double emax, double ratio, int m, const double* Y,
-                         int solver, double solve_tol, double* est, double* sem)
+                         int solver, double solve_tol, double* est, double* sem, int rule)
 {
     double* Q = (double*)malloc(sizeof(double) * (size_t)n * m);
-    int st = orc_filter(n, ip, ix, av, bip, bix, bv, ne, emin, emax, ratio, m, Y, NULL, 0, Q, solver, solve_tol);
+    int st = orc_filter(n, ip, ix, av, bip, bix, bv, ne, emin, emax, ratio, m, Y, NULL, 0, Q, solver, solve_tol,
+                        rule);
     if (st) { free(Q); return st; }
     double sum = 0.0, sum2 = 0.0;
     for (int j = 0; j < m; ++j) {
@@ -727,6 +756,7 @@ int orc_feast_scsr(int n, const int* ip, const int* ix, const double* av,
     if (!(emin < emax)) return 200;
     int ne = fpm[1];
     if (ne < 1) return 102;
+    if (fpm[15] != 0 && fpm[15] != 1) return 116;
     ocsr A = {n, ip, ix, av}, Bm = {n, bip, bix, bv};
     const ocsr* B = bip ? &Bm : NULL;
     double ratio = fpm[17] / 100.0;
@@ -735,7 +765,7 @@ int orc_feast_scsr(int n, const int* ip, const int* ix, const double* av,
     double alpha = fmax(fabs(emin), fabs(emax));
     double* z = (double*)malloc(sizeof(double) * 2 * ne);
     double* w = (double*)malloc(sizeof(double) * 2 * ne);
-    orc_contour_gauss(ne, emin, emax, ratio, z, w);
+    contour_nodes(fpm[15], ne, emin, emax, ratio, z, w);
 
     size_t nm = (size_t)n * m0;
     double* Q = (double*)malloc(sizeof(double) * nm);

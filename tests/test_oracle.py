@@ -72,6 +72,52 @@ def test_filter_edges_and_decay():
     assert abs(rho[0]) < 1e-4 and abs(rho[-1]) < 1e-4
 
 
+@pytest.mark.parametrize("ne", [1, 2, 3, 4, 8, 16])
+def test_trapezoid_filter_closed_form_on_circle(ne):
+    """The 2 ne equally spaced midpoints of a circle are the roots of
+    t^(2 ne) = -1, and the trapezoidal sum of the resolvent is then exactly
+    rho(lambda) = 1 / (1 + t^(2 ne)), t = (lambda - c) / r."""
+    emin, emax = -1.0, 3.0
+    c, r = 1.0, 2.0
+    lam = np.linspace(-3.0, 5.0, 41)
+    t = (lam - c) / r
+    ref = 1.0 / (1.0 + t ** (2 * ne))
+    got = O.rho(ne, emin, emax, 1.0, lam, rule=1)
+    assert np.abs(got - ref).max() < 1e-13
+
+
+@pytest.mark.parametrize("ratio", [0.3, 1.0])
+def test_trapezoid_filter_converges_to_contour_integral(ratio):
+    """On an ellipse the trapezoidal sum converges (geometrically, the
+    integrand being periodic and analytic) to the same half-contour integral."""
+    emin, emax = 1.0, 3.0
+    c, r = 2.0, 1.0
+    for lam in [1.5, 2.0, 2.7, 0.0, 3.6, 10.0]:
+        f = lambda t: ((-r * math.sin(t) + 1j * ratio * r * math.cos(t))
+                       / (c + r * math.cos(t) + 1j * ratio * r * math.sin(t) - lam)).imag
+        ref = scipy.integrate.quad(f, 0.0, math.pi, limit=400, epsabs=1e-13)[0] / math.pi
+        assert abs(O.rho(400, emin, emax, ratio, lam, rule=1)[0] - ref) < 1e-6
+
+
+def test_trapezoid_weights_sum():
+    """sum_e Re(w_e) = (r a / ne) sum cos(theta_e) = 0 and sum Im(w_e) equals the
+    midpoint rule of (r/pi) int_0^pi sin = 2 r / pi up to its O(ne^-2) error."""
+    z, w = O.contour_trapezoid(64, 0.0, 2.0, 0.5)
+    assert abs(w.real.sum()) < 1e-14
+    assert abs(w.imag.sum() - 2.0 / math.pi) < 1e-4
+    assert np.all(z.imag > 0) and np.all(np.diff(z.real) < 0)
+
+
+def test_feast_with_trapezoid_rule_matches_closed_form():
+    """1D Laplacian, 31 eigenvalues in [0, 0.01] (closed form), trapezoidal
+    nodes (fpm(16)=1)."""
+    p = fw.tridiag_1d(n=1000, emin=0.0, emax=0.01, m0=48, ratio=30)
+    ref = O.feast_scsr(p.A, None, 0.0, 0.01, 48, Y0=p.y0(), ne=8, ratio=30, tol_exp=11, rule=1)
+    lam = 2 - 2 * np.cos(np.arange(1, 32) * np.pi / 1001)
+    assert ref["info"] == 0 and ref["M"] == 31
+    assert np.abs(ref["E"][:31] - lam).max() < 1e-13
+
+
 # ------------------------------------------------------------------ linear algebra
 def _rand_sym_csr(n, bw, rng, shift=0.0):
     d = np.zeros((n, n))
