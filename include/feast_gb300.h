@@ -16,7 +16,8 @@
  *  - fpm is the 64-entry parameter array of the guide's parameter table
  *    (Sec. 3.1), C indexing fpm[i-1] = fpm(i).  Used entries:
  *      fpm(1)  0 silent, 1 per-iteration log on stdout, n<0 append to feast<|n|>.log
- *      fpm(2)  Ne, number of half-contour nodes (1..20, 24, 32, 40, 48, 56)
+ *      fpm(2)  Ne, number of half-contour nodes (Gauss: 1..20, 24, 32, 40, 48, 56;
+ *              trapezoidal: 1..1024)
  *      fpm(3)  stopping tolerance 10^-fpm(3) on the relative residual (0..16)
  *      fpm(4)  maximum number of refinement loops (>= 0)
  *      fpm(5)  1: X holds the start subspace on entry; 0: a random start block
@@ -24,7 +25,7 @@
  *      fpm(14) 0 normal run; 1 return the block Q after one contour pass
  *              (info 4); 2 stochastic estimate of the number of eigenvalues
  *              inside the contour (info 5), see feast_scsr_solve
- *      fpm(16) must be 0 (Gauss-Legendre nodes)
+ *      fpm(16) 0 Gauss-Legendre nodes, 1 trapezoidal nodes (2, Zolotarev, -> 116)
  *      fpm(18) ellipse ratio in percent (> 0)
  *      fpm(40) 0 search interval given (feast_scsr_solve*); -1 / +1 search
  *              the M0/2 lowest / largest eigenpairs (feast_scsr_extreme*)
@@ -82,6 +83,17 @@ const char* feast_last_error(void);
  * arrays of 2*ne doubles, (re, im) interleaved.  Returns 0, 102 for a bad ne,
  * 200 for emin >= emax. */
 int feast_contour_nodes(int ne, double emin, double emax, int ratio_pct, double* z, double* w);
+
+/* Nodes and weights of the quadrature rule fpm(16) = rule (guide Sec. 3.1,
+ * parameter table: 0 Gauss-Legendre, 1 trapezoidal) on the same half
+ * contour.  A rule with nodes t_e in [0, pi] and t-weights v_e gives
+ * w_e = (v_e r / pi)(a cos(t_e) + i sin(t_e)); the trapezoidal rule takes the
+ * midpoints t_e = pi (e - 1/2) / ne, e = 1..ne, v_e = pi / ne (with the
+ * conjugate half, 2 ne equally spaced points of the whole contour; on a
+ * circle its filter is 1 / (1 + ((lambda - c)/r)^(2 ne))).  rule 0 equals
+ * feast_contour_nodes.  Returns 0, 116 for another rule, 102 for a bad ne
+ * (trapezoidal: 1..1024), 200 for emin >= emax. */
+int feast_contour_nodes_rule(int rule, int ne, double emin, double emax, int ratio_pct, double* z, double* w);
 
 /* Timings of the last feast_scsr_solve / feast_scsr_solve_dev of the calling
  * thread run with fpm(53) = 1 (all zero otherwise), measured with CUDA events

@@ -13,6 +13,7 @@ from ._lib import (  # noqa: F401
     FeastError,
     FeastResult,
     feast_contour_nodes,
+    feast_contour_nodes_rule,
     feast_eig_grad_dev,
     feast_filter_dev,
     feast_filter_layout,

@@ -22,6 +22,7 @@ _SIGS = {
     "feast_init": (_i, [_p]),
     "feast_last_error": (C.c_char_p, []),
     "feast_contour_nodes": (_i, [_i, _d, _d, _i, _p, _p]),
+    "feast_contour_nodes_rule": (_i, [_i, _i, _d, _d, _i, _p, _p]),
     "feast_scsr_solve": (_i, [C.c_char, _i, _p, _p, _p, _p, _p, _p, _p, _d, _d, _p, _p, _p, _p, _p, _p, _p,
                               _p]),
     "feast_scsr_workspace_bytes": (C.c_size_t, [_i, _i, _i, _i, _p]),
@@ -140,6 +141,15 @@ def feast_contour_nodes(ne: int, emin: float, emax: float, ratio_pct: int):
     z = np.zeros(2 * ne)
     w = np.zeros(2 * ne)
     _check(library().feast_contour_nodes(ne, emin, emax, ratio_pct, _ptr(z), _ptr(w)), "feast_contour_nodes")
+    return z[0::2] + 1j * z[1::2], w[0::2] + 1j * w[1::2]
+
+
+def feast_contour_nodes_rule(rule: int, ne: int, emin: float, emax: float, ratio_pct: int):
+    """Nodes of quadrature rule fpm(16) = rule (0 Gauss-Legendre, 1 trapezoidal)."""
+    z = np.zeros(2 * ne)
+    w = np.zeros(2 * ne)
+    _check(library().feast_contour_nodes_rule(rule, ne, emin, emax, ratio_pct, _ptr(z), _ptr(w)),
+           "feast_contour_nodes_rule")
     return z[0::2] + 1j * z[1::2], w[0::2] + 1j * w[1::2]
 
 

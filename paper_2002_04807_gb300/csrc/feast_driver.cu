@@ -68,15 +68,17 @@ static bool gauss_ne_ok(int ne)
     return (ne >= 1 && ne <= 20) || ne == 24 || ne == 32 || ne == 40 || ne == 48 || ne == 56;
 }
 
+static constexpr int kMaxTrapezoidNodes = 1024;
+
 static int check_fpm(const int* fpm)
 {
-    if (!gauss_ne_ok(fpm[1])) return 102;
+    if (fpm[15] != 0 && fpm[15] != 1) return 116;  // Zolotarev (2) is not built
+    if (fpm[15] == 0 ? !gauss_ne_ok(fpm[1]) : (fpm[1] < 1 || fpm[1] > kMaxTrapezoidNodes)) return 102;
     if (fpm[2] < 0 || fpm[2] > 16) return 103;
     if (fpm[3] < 0) return 104;
     if (fpm[4] != 0 && fpm[4] != 1) return 105;
     if (fpm[5] != 0 && fpm[5] != 1) return 106;
     if (fpm[13] < 0 || fpm[13] > 2) return 114;
-    if (fpm[15] != 0) return 116;
     if (fpm[17] <= 0) return 118;
     if (fpm[39] < -1 || fpm[39] > 1) return 140;
     if (fpm[41] != 0 && fpm[41] != 1) return 142;
@@ -125,19 +127,37 @@ static void gl_rule(int n, std::vector<double>& x, std::vector<double>& w)
 }
 
 // zw[4e..4e+3] = (Re z_e, Im z_e, Re w_e, Im w_e)
-static void contour(int ne, double emin, double emax, double ratio, std::vector<double>& zw)
+// Nodes and weights of the quadrature rule fpm(16) on the upper half of the
+// ellipse z(t) = c + r cos t + i a r sin t, t in [0, pi]: a rule with nodes
+// t_e and t-weights v_e gives w_e = (v_e / (i pi)) z'(t_e)
+// = (v_e r / pi)(a cos t_e + i sin t_e).  rule 0: Gauss-Legendre mapped by
+// t = (pi/2)(1 - x), v_e = (pi/2) omega_e; rule 1: trapezoidal (midpoints)
+// t_e = pi (e + 1/2) / ne, v_e = pi / ne, which with the conjugate lower
+// half are 2 ne equally spaced points of the whole contour.
+static void contour(int rule, int ne, double emin, double emax, double ratio, std::vector<double>& zw)
 {
-    std::vector<double> x, om;
-    gl_rule(ne, x, om);
+    std::vector<double> t(ne), v(ne);
+    if (rule == 1) {
+        for (int e = 0; e < ne; ++e) {
+            t[e] = M_PI * (e + 0.5) / ne;
+            v[e] = M_PI / ne;
+        }
+    } else {
+        std::vector<double> x, om;
+        gl_rule(ne, x, om);
+        for (int e = 0; e < ne; ++e) {
+            t[e] = 0.5 * M_PI * (1.0 - x[e]);
+            v[e] = 0.5 * M_PI * om[e];
+        }
+    }
     const double c = 0.5 * (emin + emax), r = 0.5 * (emax - emin);
     zw.assign(4 * (size_t)ne, 0.0);
     for (int e = 0; e < ne; ++e) {
-        const double th = 0.5 * M_PI * (1.0 - x[e]);
-        const double ct = std::cos(th), st = std::sin(th);
+        const double ct = std::cos(t[e]), st = std::sin(t[e]);
         zw[4 * e] = c + r * ct;
         zw[4 * e + 1] = ratio * r * st;
-        zw[4 * e + 2] = 0.5 * om[e] * r * ratio * ct;
-        zw[4 * e + 3] = 0.5 * om[e] * r * st;
+        zw[4 * e + 2] = v[e] / M_PI * r * ratio * ct;
+        zw[4 * e + 3] = v[e] / M_PI * r * st;
     }
 }
 
@@ -146,7 +166,24 @@ extern "C" int feast_contour_nodes(int ne, double emin, double emax, int ratio_p
     if (!gauss_ne_ok(ne)) return 102;
     if (!(emin < emax)) return 200;
     std::vector<double> zw;
-    contour(ne, emin, emax, ratio_pct / 100.0, zw);
+    contour(0, ne, emin, emax, ratio_pct / 100.0, zw);
+    for (int e = 0; e < ne; ++e) {
+        z[2 * e] = zw[4 * e];
+        z[2 * e + 1] = zw[4 * e + 1];
+        w[2 * e] = zw[4 * e + 2];
+        w[2 * e + 1] = zw[4 * e + 3];
+    }
+    return 0;
+}
+
+extern "C" int feast_contour_nodes_rule(int rule, int ne, double emin, double emax, int ratio_pct, double* z,
+                                        double* w)
+{
+    if (rule != 0 && rule != 1) return 116;
+    if (rule == 0 ? !gauss_ne_ok(ne) : (ne < 1 || ne > kMaxTrapezoidNodes)) return 102;
+    if (!(emin < emax)) return 200;
+    std::vector<double> zw;
+    contour(rule, ne, emin, emax, ratio_pct / 100.0, zw);
     for (int e = 0; e < ne; ++e) {
         z[2 * e] = zw[4 * e];
         z[2 * e + 1] = zw[4 * e + 1];
@@ -666,7 +703,7 @@ int run_feast(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, int* fpm, dou
     const double tol = std::pow(10.0, -fpm[44]);
     const int maxit = fpm[45], maxloop = fpm[3];
     std::vector<double> zw;
-    contour(ne, emin, emax, fpm[17] / 100.0, zw);
+    contour(fpm[15], ne, emin, emax, fpm[17] / 100.0, zw);
     int st = setup_filter(P, B, A, Bm, zw, B.lam, B.mk, s);
     if (st) return st;
     // every subspace column is live until a reduced solve drops some
@@ -1416,7 +1453,7 @@ extern "C" int feast_filter_dev(int n, int nnz_a, const int* ia, const int* ja, 
     carve(P, base, B, true);
     Csr A{n, nnz_a, ia, ja, a}, Bm{n, b ? nnz_b : 0, ib, jb, b};
     std::vector<double> zw;
-    contour(P.ne, emin, emax, fpm[17] / 100.0, zw);
+    contour(fpm[15], P.ne, emin, emax, fpm[17] / 100.0, zw);
     int st = setup_filter(P, B, A, Bm, zw, lam, nullptr, s);
     if (st) return st;
     B.Q = Q;
@@ -1868,7 +1905,7 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
             opp += n + 1;
             opk += (long long)aja[p].size() + 7LL * n;
             std::vector<double> zw;
-            contour(ne, probs[p].emin, probs[p].emax, fpm[17] / 100.0, zw);
+            contour(fpm[15], ne, probs[p].emin, probs[p].emax, fpm[17] / 100.0, zw);
             std::copy(zw.begin(), zw.end(), zw_all.begin() + (size_t)p * ne * 4);
             f.zw = d_zw + (size_t)p * ne * 4;
             f.lam = d_lam + b.l_off;

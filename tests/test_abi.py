@@ -66,6 +66,34 @@ def test_contour_nodes_match_oracle(pkg, ne, ratio):
     assert np.abs(z - zo).max() < 1e-14 and np.abs(w - wo).max() < 1e-14
 
 
+@pytest.mark.parametrize("ne,ratio", [(1, 100), (3, 30), (8, 100), (37, 200), (1024, 50)])
+def test_trapezoid_nodes_match_oracle(pkg, ne, ratio):
+    z, w = pkg.feast_contour_nodes_rule(1, ne, -1.5, 2.5, ratio)
+    zo, wo = O.contour_trapezoid(ne, -1.5, 2.5, ratio / 100.0)
+    assert np.abs(z - zo).max() < 1e-14 and np.abs(w - wo).max() < 1e-14
+    zg, wg = pkg.feast_contour_nodes_rule(0, 8, -1.5, 2.5, ratio)
+    zg0, wg0 = pkg.feast_contour_nodes(8, -1.5, 2.5, ratio)
+    assert np.abs(zg - zg0).max() < 1e-15 and np.abs(wg - wg0).max() < 1e-15
+
+
+def test_rule_and_node_count_checks(pkg):
+    from paper_2002_04807_gb300 import FeastError
+
+    with pytest.raises(FeastError):
+        pkg.feast_contour_nodes_rule(2, 8, 0.0, 1.0, 30)
+    with pytest.raises(FeastError):
+        pkg.feast_contour_nodes_rule(1, 1025, 0.0, 1.0, 30)
+    A = fw.laplacian_1d(20)
+    base = dict(uplo="F", n=20, a=A.data, ia=A.indptr, ja=A.indices, emin=0.0, emax=0.5, m0=6)
+    f = pkg.feast_init()
+    f[15], f[1] = 2, 8
+    assert pkg.feast_scsr_solve(**base, fpm=f).info == 116
+    f[15], f[1] = 1, 0
+    assert pkg.feast_scsr_solve(**base, fpm=f).info == 102
+    f[15], f[1] = 0, 21  # 21 nodes: allowed for the trapezoidal rule only
+    assert pkg.feast_scsr_solve(**base, fpm=f).info == 102
+
+
 def test_contour_node_errors(pkg):
     from paper_2002_04807_gb300 import FeastError
 
@@ -99,7 +127,7 @@ def test_argument_errors_are_host_side(pkg):
     f[1] = 21
     assert run(fpm=f) == 102
     f = pkg.feast_init()
-    f[15] = 1
+    f[15] = 2
     assert run(fpm=f) == 116
     bad = A.indices.copy()
     bad[3] = 99

@@ -49,9 +49,10 @@ def cluster_angles(E, X, Eo, Xo, scale):
 
 
 def run_gpu(pkg, p, mixed, y0=None, tol_exp=10, inner=(2, 200), maxloop=30, B=None, uplo="F", csr=None,
-            nb=0):
+            nb=0, rule=0):
     fpm = pkg.feast_init()
     fpm[1], fpm[2], fpm[3], fpm[17], fpm[41] = p.ne, tol_exp, maxloop, p.ratio, mixed
+    fpm[15] = rule
     fpm[44], fpm[45] = inner
     fpm[49] = nb
     if y0 is None:
@@ -184,6 +185,17 @@ def test_generalized_27pt_config3_shape(pkg, config3_shape, mixed):
     p, ref = config3_shape
     r = run_gpu(pkg, p, mixed)
     check_against(r, ref, p.emax, B=p.B)
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_trapezoid_rule_matches_oracle(pkg, mixed):
+    """fpm(16) = 1: trapezoidal nodes, 12 of them (a count the Gauss rule does
+    not allow), against the oracle with the same rule."""
+    p = fw.laplace3d_potential(side=10, count=20, m0=32, ne=12, ratio=100, seed=13)
+    ref = O.feast_scsr(p.A, None, p.emin, p.emax, p.m0, Y0=p.y0(), ne=12, ratio=100, tol_exp=10, rule=1)
+    assert ref["info"] == 0 and ref["M"] == O.count_below(p.A, None, p.emax)
+    r = run_gpu(pkg, p, mixed, rule=1)
+    check_against(r, ref, p.emax)
 
 
 def test_node_batches_agree(pkg):
