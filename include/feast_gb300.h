@@ -144,6 +144,21 @@ int feast_scsr_solve(char uplo, int n, const double* a, const int* ia, const int
                      const int* ib, const int* jb, int* fpm, double emin, double emax, int* m0, double* e,
                      double* x, int* m, double* res, double* epsout, int* loop, int* info);
 
+/* Expert variant with custom integration nodes (guide Sec. 4.3 "Contour
+ * Customization": the "x" routines take the nodes and weights of a
+ * user-designed half contour for Hermitian problems).  Arguments as
+ * feast_scsr_solve, plus zne, wne: host arrays of 2*fpm(2) doubles,
+ * (re, im) interleaved, replacing the rule of fpm(16)/fpm(18); the filter is
+ * rho(lambda) = sum_e Re(wne_e / (zne_e - lambda)), the convention of
+ * feast_contour_nodes (whose output reproduces the built-in rule).  Every
+ * node must lie strictly in the upper half plane; emin/emax still select the
+ * eigenvalues reported inside and scale the residuals.  -120 for missing or
+ * invalid nodes. */
+int feast_scsr_solve_x(char uplo, int n, const double* a, const int* ia, const int* ja, const double* b,
+                       const int* ib, const int* jb, int* fpm, double emin, double emax, int* m0, double* e,
+                       double* x, int* m, double* res, double* epsout, int* loop, int* info, const double* zne,
+                       const double* wne);
+
 /* Extreme-eigenvalue mode (guide Sec. 3.1, fpm(40) = -1 / +1, and Sec. 3.2:
  * the sparse drivers search the M0/2 lowest or largest eigenpairs and return
  * the search interval).  Arguments as feast_scsr_solve, except:
@@ -227,6 +242,14 @@ int feast_scsr_solve_dev(int n, int nnz_a, const int* d_ia, const int* d_ja, con
                          double emax, int* m0, double* e, double* d_x, int* m, double* res,
                          double* epsout, int* loop, int* info, void* d_work, size_t work_bytes,
                          void* stream);
+
+/* feast_scsr_solve_dev with custom nodes zne, wne (host, as for
+ * feast_scsr_solve_x); -124 for missing or invalid nodes. */
+int feast_scsr_solve_dev_x(int n, int nnz_a, const int* d_ia, const int* d_ja, const double* d_a, int nnz_b,
+                           const int* d_ib, const int* d_jb, const double* d_b, int* fpm, double emin, double emax,
+                           int* m0, double* e, double* d_x, int* m, double* res, double* epsout, int* loop,
+                           int* info, void* d_work, size_t work_bytes, void* stream, const double* zne,
+                           const double* wne);
 
 /* feast_scsr_extreme with the matrices and X on the device, arguments as
  * feast_scsr_solve_dev; emin and emax are host pointers (out).  d_work: at

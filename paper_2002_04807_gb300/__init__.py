@@ -28,6 +28,8 @@ from ._lib import (  # noqa: F401
     feast_scsr_solve,
     feast_scsr_solve_batched,
     feast_scsr_solve_dev,
+    feast_scsr_solve_dev_x,
+    feast_scsr_solve_x,
     feast_scsr_extreme,
     feast_scsr_extreme_dev,
     feast_scsr_workspace_bytes,

@@ -40,6 +40,10 @@ _SIGS = {
     "feast_last_profile": (_i, [_p]),
     "feast_gram_noalloc_dev": (_i, [_i, _i, _p, _p, _p, _p]),
     "feast_scsr_solve_batched": (_i, [_i, _p, _p, _p]),
+    "feast_scsr_solve_x": (_i, [C.c_char, _i, _p, _p, _p, _p, _p, _p, _p, _d, _d, _p, _p, _p, _p, _p, _p, _p,
+                                _p, _p, _p]),
+    "feast_scsr_solve_dev_x": (_i, [_i, _i, _p, _p, _p, _i, _p, _p, _p, _p, _d, _d, _p, _p, _p, _p, _p, _p, _p,
+                                    _p, _p, C.c_size_t, _p, _p, _p]),
     "feast_scsr_extreme": (_i, [C.c_char, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p,
                                 _p]),
     "feast_scsr_extreme_dev": (_i, [_i, _i, _p, _p, _p, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p,
@@ -246,6 +250,76 @@ def feast_scsr_solve_dev(n: int, ia, ja, a, ib=None, jb=None, b=None, fpm=None, 
                                    _stream(stream))
     if info.value == -4:
         raise FeastError("feast_scsr_solve_dev: " + feast_last_error())
+    k = mm.value
+    return FeastResult(info.value, E[:k].copy(), x, res[:k].copy(), M.value, loop.value, eps.value, k, f)
+
+
+def _nodes(zne, wne):
+    zne = np.asarray(zne, dtype=np.complex128)
+    wne = np.asarray(wne, dtype=np.complex128)
+    z = np.ascontiguousarray(np.stack([zne.real, zne.imag], axis=1).ravel())
+    w = np.ascontiguousarray(np.stack([wne.real, wne.imag], axis=1).ravel())
+    return z, w
+
+
+def feast_scsr_solve_x(uplo: str, n: int, a, ia, ja, zne, wne, b=None, ib=None, jb=None, fpm=None, emin=0.0,
+                       emax=1.0, m0: int = 1, x0=None) -> FeastResult:
+    """Host driver with custom half-contour nodes zne and weights wne (complex
+    arrays of fpm(2) values, convention of feast_contour_nodes)."""
+    f = _fpm(fpm)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    ia = np.ascontiguousarray(ia, dtype=np.int32)
+    ja = np.ascontiguousarray(ja, dtype=np.int32)
+    if b is not None:
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        ib = np.ascontiguousarray(ib, dtype=np.int32)
+        jb = np.ascontiguousarray(jb, dtype=np.int32)
+    z, w = _nodes(zne, wne)
+    x = np.zeros((n, m0), order="F")
+    if x0 is not None:
+        x[:] = x0
+    E = np.zeros(m0)
+    res = np.zeros(m0)
+    M, loop, info, mm = _i(0), _i(0), _i(0), _i(m0)
+    eps = _d(0)
+    library().feast_scsr_solve_x(uplo.encode(), n, _ptr(a), _ptr(ia), _ptr(ja), _ptr(b), _ptr(ib), _ptr(jb),
+                                 _ptr(f), emin, emax, C.byref(mm), _ptr(E), _ptr(x), C.byref(M), _ptr(res),
+                                 C.byref(eps), C.byref(loop), C.byref(info), _ptr(z), _ptr(w))
+    k = mm.value
+    if info.value == -4:
+        raise FeastError("feast_scsr_solve_x: " + feast_last_error())
+    return FeastResult(info.value, E[:k].copy(), np.asfortranarray(x[:, :k]), res[:k].copy(), M.value,
+                       loop.value, eps.value, k, f)
+
+
+def feast_scsr_solve_dev_x(n: int, ia, ja, a, zne, wne, ib=None, jb=None, b=None, fpm=None, emin=0.0, emax=1.0,
+                           m0: int = 1, x=None, work=None, stream=None) -> FeastResult:
+    """Device driver with custom half-contour nodes (see feast_scsr_solve_x)."""
+    import torch
+
+    f = _fpm(fpm)
+    ia, ja, a = _dev(ia, torch.int32), _dev(ja, torch.int32), _dev(a, torch.float64)
+    nnzb = 0
+    if b is not None:
+        ib, jb, b = _dev(ib, torch.int32), _dev(jb, torch.int32), _dev(b, torch.float64)
+        nnzb = b.numel()
+    if x is None:
+        x = torch.zeros((m0, n), dtype=torch.float64, device=a.device)
+    x = _dev(x, torch.float64)
+    need = feast_scsr_workspace_bytes(n, a.numel(), nnzb, m0, f)
+    if work is None or work.numel() < need:
+        work = torch.empty(need, dtype=torch.uint8, device=a.device)
+    z, w = _nodes(zne, wne)
+    E = np.zeros(m0)
+    res = np.zeros(m0)
+    M, loop, info, mm = _i(0), _i(0), _i(0), _i(m0)
+    eps = _d(0)
+    library().feast_scsr_solve_dev_x(n, a.numel(), _ptr(ia), _ptr(ja), _ptr(a), nnzb, _ptr(ib), _ptr(jb), _ptr(b),
+                                     _ptr(f), emin, emax, C.byref(mm), _ptr(E), _ptr(x), C.byref(M), _ptr(res),
+                                     C.byref(eps), C.byref(loop), C.byref(info), _ptr(work), work.numel(),
+                                     _stream(stream), _ptr(z), _ptr(w))
+    if info.value == -4:
+        raise FeastError("feast_scsr_solve_dev_x: " + feast_last_error())
     k = mm.value
     return FeastResult(info.value, E[:k].copy(), x, res[:k].copy(), M.value, loop.value, eps.value, k, f)
 

@@ -695,7 +695,7 @@ void log_line(int lvl, const char* text)
 // The FEAST iteration on device data.  x_dev: column-major n x m0 in/out.
 int run_feast(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, int* fpm, double emin, double emax, int* m0io,
               double* e_host, double* x_dev, int* M_out, double* res_host, double* epsout, int* loop_out,
-              cudaStream_t s)
+              cudaStream_t s, const double* custom_zw = nullptr)
 {
     const int n = P.n, m0 = P.m0, ne = P.ne;
     const double alpha = std::max(std::fabs(emin), std::fabs(emax));
@@ -703,7 +703,8 @@ int run_feast(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, int* fpm, dou
     const double tol = std::pow(10.0, -fpm[44]);
     const int maxit = fpm[45], maxloop = fpm[3];
     std::vector<double> zw;
-    contour(fpm[15], ne, emin, emax, fpm[17] / 100.0, zw);
+    if (custom_zw) zw.assign(custom_zw, custom_zw + 4 * (size_t)ne);  // the caller's nodes (expert entry points)
+    else contour(fpm[15], ne, emin, emax, fpm[17] / 100.0, zw);
     int st = setup_filter(P, B, A, Bm, zw, B.lam, B.mk, s);
     if (st) return st;
     // every subspace column is live until a reduced solve drops some
@@ -1146,11 +1147,57 @@ extern "C" int feast_scsr_extreme_dev(int n, int nnz_a, const int* d_ia, const i
     return ret(inf);
 }
 
+// Custom nodes (expert entry points): z, w host arrays of 2 ne doubles (re,
+// im) in the convention of feast_contour_nodes; every node strictly in the
+// upper half plane and finite.  Returns 0 and fills zw (z.re, z.im, w.re,
+// w.im per node), or the given error code.
+static int custom_nodes(int ne, const double* z, const double* w, int bad, std::vector<double>& zw)
+{
+    if (!z || !w) return bad;
+    zw.assign(4 * (size_t)ne, 0.0);
+    for (int e = 0; e < ne; ++e) {
+        if (!(z[2 * e + 1] > 0.0) || !std::isfinite(z[2 * e]) || !std::isfinite(z[2 * e + 1]) ||
+            !std::isfinite(w[2 * e]) || !std::isfinite(w[2 * e + 1]))
+            return bad;
+        zw[4 * e] = z[2 * e];
+        zw[4 * e + 1] = z[2 * e + 1];
+        zw[4 * e + 2] = w[2 * e];
+        zw[4 * e + 3] = w[2 * e + 1];
+    }
+    return 0;
+}
+
+static int solve_dev_impl(int n, int nnz_a, const int* d_ia, const int* d_ja, const double* d_a, int nnz_b,
+                          const int* d_ib, const int* d_jb, const double* d_b, int* fpm, double emin, double emax,
+                          int* m0, double* e, double* d_x, int* m, double* res, double* epsout, int* loop,
+                          int* info, void* d_work, size_t work_bytes, void* stream, const double* zne,
+                          const double* wne, bool expert);
+
 extern "C" int feast_scsr_solve_dev(int n, int nnz_a, const int* d_ia, const int* d_ja, const double* d_a,
                                     int nnz_b, const int* d_ib, const int* d_jb, const double* d_b, int* fpm,
                                     double emin, double emax, int* m0, double* e, double* d_x, int* m,
                                     double* res, double* epsout, int* loop, int* info, void* d_work,
                                     size_t work_bytes, void* stream)
+{
+    return solve_dev_impl(n, nnz_a, d_ia, d_ja, d_a, nnz_b, d_ib, d_jb, d_b, fpm, emin, emax, m0, e, d_x, m, res,
+                          epsout, loop, info, d_work, work_bytes, stream, nullptr, nullptr, false);
+}
+
+extern "C" int feast_scsr_solve_dev_x(int n, int nnz_a, const int* d_ia, const int* d_ja, const double* d_a,
+                                      int nnz_b, const int* d_ib, const int* d_jb, const double* d_b, int* fpm,
+                                      double emin, double emax, int* m0, double* e, double* d_x, int* m,
+                                      double* res, double* epsout, int* loop, int* info, void* d_work,
+                                      size_t work_bytes, void* stream, const double* zne, const double* wne)
+{
+    return solve_dev_impl(n, nnz_a, d_ia, d_ja, d_a, nnz_b, d_ib, d_jb, d_b, fpm, emin, emax, m0, e, d_x, m, res,
+                          epsout, loop, info, d_work, work_bytes, stream, zne, wne, true);
+}
+
+static int solve_dev_impl(int n, int nnz_a, const int* d_ia, const int* d_ja, const double* d_a, int nnz_b,
+                          const int* d_ib, const int* d_jb, const double* d_b, int* fpm, double emin, double emax,
+                          int* m0, double* e, double* d_x, int* m, double* res, double* epsout, int* loop,
+                          int* info, void* d_work, size_t work_bytes, void* stream, const double* zne,
+                          const double* wne, bool expert)
 {
     int inf = 0;
     auto ret = [&](int v) { if (info) *info = v; return v; };
@@ -1167,13 +1214,16 @@ extern "C" int feast_scsr_solve_dev(int n, int nnz_a, const int* d_ia, const int
     Bufs B;
     const size_t need = carve(P, nullptr, B);
     if (!d_work || work_bytes < need) return ret(-120);
+    std::vector<double> czw;
+    if (expert && (inf = custom_nodes(fpm[1], zne, wne, -124, czw))) return ret(inf);
     carve(P, d_work, B);
     Csr A{n, nnz_a, d_ia, d_ja, d_a}, Bm{n, d_b ? nnz_b : 0, d_ib, d_jb, d_b};
     g_err.clear();
     g_prof.reset(fpm[52] == 1);
     const long long l0 = launch_count();
     CK(cudaMemsetAsync(B.work, 0, sizeof(unsigned long long), (cudaStream_t)stream));
-    inf = run_feast(P, B, A, Bm, fpm, emin, emax, m0, e, d_x, m, res, epsout, loop, (cudaStream_t)stream);
+    inf = run_feast(P, B, A, Bm, fpm, emin, emax, m0, e, d_x, m, res, epsout, loop, (cudaStream_t)stream,
+                    expert ? czw.data() : nullptr);
     g_prof.out[15] = (double)(launch_count() - l0);
     return ret(inf);
 }
@@ -1248,7 +1298,8 @@ struct DevMem {
 // device entry point and copies X back.
 static int host_driver(bool extreme, char uplo, int n, const double* a, const int* ia, const int* ja,
                        const double* b, const int* ib, const int* jb, int* fpm, double* emin_io, double* emax_io,
-                       int* m0, double* e, double* x, int* m, double* res, double* epsout, int* loop, int* info)
+                       int* m0, double* e, double* x, int* m, double* res, double* epsout, int* loop, int* info,
+                       const double* zne = nullptr, const double* wne = nullptr, bool expert = false)
 {
     auto ret = [&](int v) { if (info) *info = v; return v; };
     if (uplo != 'F' && uplo != 'L' && uplo != 'U') return ret(-101);
@@ -1260,6 +1311,10 @@ static int host_driver(bool extreme, char uplo, int n, const double* a, const in
     if (extreme && fpm[39] != -1 && fpm[39] != 1) return ret(140);
     if (extreme && fpm[13] != 0) return ret(114);
     if (!extreme && !(*emin_io < *emax_io)) return ret(200);
+    if (expert) {
+        std::vector<double> czw;
+        if ((inf = custom_nodes(fpm[1], zne, wne, -120, czw))) return ret(inf);
+    }
     if (!m0 || *m0 <= (extreme ? 1 : 0) || *m0 > n) return ret(201);
     if (!e) return ret(-113);
     if (!x) return ret(-114);
@@ -1310,8 +1365,9 @@ static int host_driver(bool extreme, char uplo, int n, const double* a, const in
         inf = feast_scsr_extreme_dev(n, (int)aja.size(), d_ia, d_ja, d_a, hasB ? (int)bja.size() : 0, d_ib, d_jb,
                                      d_b, fpm, emin_io, emax_io, m0, e, d_x, m, res, epsout, loop, info, d_work, wb, s);
     else
-        inf = feast_scsr_solve_dev(n, (int)aja.size(), d_ia, d_ja, d_a, hasB ? (int)bja.size() : 0, d_ib, d_jb, d_b,
-                                   fpm, *emin_io, *emax_io, m0, e, d_x, m, res, epsout, loop, info, d_work, wb, s);
+        inf = solve_dev_impl(n, (int)aja.size(), d_ia, d_ja, d_a, hasB ? (int)bja.size() : 0, d_ib, d_jb, d_b, fpm,
+                             *emin_io, *emax_io, m0, e, d_x, m, res, epsout, loop, info, d_work, wb, s, zne, wne,
+                             expert);
     if ((inf >= 0 && inf != 5) || inf == -3 || inf == -2)  // info 5 (count only) leaves X alone
         HK(cudaMemcpy(x, d_x, sizeof(double) * (size_t)n * mm0, cudaMemcpyDeviceToHost));
 #undef HK
@@ -1324,6 +1380,15 @@ extern "C" int feast_scsr_solve(char uplo, int n, const double* a, const int* ia
 {
     return host_driver(false, uplo, n, a, ia, ja, b, ib, jb, fpm, &emin, &emax, m0, e, x, m, res, epsout, loop,
                        info);
+}
+
+extern "C" int feast_scsr_solve_x(char uplo, int n, const double* a, const int* ia, const int* ja, const double* b,
+                                  const int* ib, const int* jb, int* fpm, double emin, double emax, int* m0,
+                                  double* e, double* x, int* m, double* res, double* epsout, int* loop, int* info,
+                                  const double* zne, const double* wne)
+{
+    return host_driver(false, uplo, n, a, ia, ja, b, ib, jb, fpm, &emin, &emax, m0, e, x, m, res, epsout, loop,
+                       info, zne, wne, true);
 }
 
 extern "C" int feast_scsr_extreme(char uplo, int n, const double* a, const int* ia, const int* ja, const double* b,

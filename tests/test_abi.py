@@ -190,6 +190,18 @@ def test_extreme_workspace_includes_search_buffers(pkg):
     assert ext >= base + 20000 * 8 + 4096 * 8
 
 
+def test_custom_node_checks(pkg):
+    """Expert entry point: every node strictly in the upper half plane."""
+    A = fw.laplacian_1d(20)
+    base = dict(uplo="F", n=20, a=A.data, ia=A.indptr, ja=A.indices, emin=0.0, emax=0.5, m0=6)
+    z, w = pkg.feast_contour_nodes(8, 0.0, 0.5, 100)
+    zb = z.copy()
+    zb[3] = zb[3].real - 0.1j
+    assert pkg.feast_scsr_solve_x(**base, zne=zb, wne=w).info == -120
+    zb[3] = zb[3].real + np.nan * 1j
+    assert pkg.feast_scsr_solve_x(**base, zne=zb, wne=w).info == -120
+
+
 def test_no_cpu_fallback_without_gpu(pkg):
     """With valid arguments the host driver goes to the GPU; without one it
     must fail with the CUDA error code, never compute on the CPU."""

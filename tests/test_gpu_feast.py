@@ -198,6 +198,30 @@ def test_trapezoid_rule_matches_oracle(pkg, mixed):
     check_against(r, ref, p.emax)
 
 
+@pytest.mark.parametrize("kind", ["tall_ellipse", "trapezoid"])
+def test_custom_nodes_match_oracle(pkg, kind):
+    """Expert entry points (custom half-contour nodes): nodes of a taller
+    ellipse, or trapezoidal nodes, passed by the caller while fpm(16)/fpm(18)
+    say otherwise, give the oracle's result for that contour."""
+    p = fw.laplace3d_potential(side=10, count=20, m0=32, ne=8, ratio=100, seed=14)
+    if kind == "tall_ellipse":
+        z, w = O.contour_gauss(8, p.emin, p.emax, 3.0)
+        ref = O.feast_scsr(p.A, None, p.emin, p.emax, p.m0, Y0=p.y0(), ne=8, ratio=300, tol_exp=10)
+    else:
+        z, w = O.contour_trapezoid(8, p.emin, p.emax, 1.0)
+        ref = O.feast_scsr(p.A, None, p.emin, p.emax, p.m0, Y0=p.y0(), ne=8, ratio=100, tol_exp=10, rule=1)
+    fpm = pkg.feast_init()
+    fpm[1], fpm[2], fpm[3], fpm[4], fpm[17], fpm[41], fpm[44], fpm[45] = 8, 10, 30, 1, 100, 1, 2, 200
+    r = pkg.feast_scsr_solve_x("F", p.n, p.A.data, p.A.indptr, p.A.indices, z, w, fpm=fpm, emin=p.emin,
+                               emax=p.emax, m0=p.m0, x0=p.y0())
+    check_against(r, ref, p.emax)
+    ia, ja, av = (torch.as_tensor(p.A.indptr).cuda(), torch.as_tensor(p.A.indices).cuda(),
+                  torch.as_tensor(p.A.data).cuda())
+    x = torch.as_tensor(np.ascontiguousarray(p.y0().T)).cuda()
+    rd = pkg.feast_scsr_solve_dev_x(p.n, ia, ja, av, z, w, fpm=fpm, emin=p.emin, emax=p.emax, m0=p.m0, x=x)
+    assert rd.info == 0 and np.array_equal(rd.E, r.E)  # same kernels, same order
+
+
 def test_node_batches_agree(pkg):
     """Solving the 16 nodes in batches of 4 gives the same eigenpairs."""
     p = fw.laplace3d_potential(side=12, count=16, m0=28, ne=16, seed=9)
