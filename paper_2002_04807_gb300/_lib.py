@@ -186,10 +186,32 @@ def _fpm(fpm):
     return np.ascontiguousarray(f)
 
 
+def _host_block(n, m0, x0, x_out, f):
+    """The host X block (column-major n x m0) handed to the library: x_out in
+    place when given (filled from x0 if that is another array), else a new
+    array holding x0, else zeros when the library reads or may not write it."""
+    if x_out is not None:
+        if x_out.shape != (n, m0) or x_out.dtype != np.float64 or not x_out.flags.f_contiguous:
+            raise FeastError("x_out must be a Fortran-ordered float64 array of shape (n, m0)")
+        if x0 is not None and x0 is not x_out:
+            np.copyto(x_out, x0)
+        return x_out
+    if x0 is not None:
+        x = np.array(x0, dtype=np.float64, order="F", copy=True)
+        if x.shape != (n, m0):
+            raise FeastError("x0 must have shape (n, m0)")
+        return x
+    if f[4] == 1 or f[13] != 0:
+        return np.zeros((n, m0), order="F")
+    return np.empty((n, m0), order="F")
+
+
 def feast_scsr_solve(uplo: str, n: int, a, ia, ja, b=None, ib=None, jb=None, fpm=None, emin=0.0, emax=1.0,
-                     m0: int = 1, x0=None) -> FeastResult:
+                     m0: int = 1, x0=None, x_out=None) -> FeastResult:
     """Host driver: CSR arrays (numpy, base ia[0] in {0,1}), returns a FeastResult.
-    x0 (n x m0) is the start subspace when fpm(5)=1."""
+    x0 (n x m0) is the start subspace when fpm(5)=1.  x_out: optional
+    Fortran-ordered float64 (n, m0) array used in place as the library's X
+    (pinned host memory makes the copies faster); it receives the eigenvectors."""
     f = _fpm(fpm)
     a = np.ascontiguousarray(a, dtype=np.float64)
     ia = np.ascontiguousarray(ia, dtype=np.int32)
@@ -198,9 +220,7 @@ def feast_scsr_solve(uplo: str, n: int, a, ia, ja, b=None, ib=None, jb=None, fpm
         b = np.ascontiguousarray(b, dtype=np.float64)
         ib = np.ascontiguousarray(ib, dtype=np.int32)
         jb = np.ascontiguousarray(jb, dtype=np.int32)
-    x = np.zeros((n, m0), order="F")
-    if x0 is not None:
-        x[:] = x0
+    x = _host_block(n, m0, x0, x_out, f)
     E = np.zeros(m0)
     res = np.zeros(m0)
     M, loop, info, mm = _i(0), _i(0), _i(0), _i(m0)
@@ -263,7 +283,7 @@ def _nodes(zne, wne):
 
 
 def feast_scsr_solve_x(uplo: str, n: int, a, ia, ja, zne, wne, b=None, ib=None, jb=None, fpm=None, emin=0.0,
-                       emax=1.0, m0: int = 1, x0=None) -> FeastResult:
+                       emax=1.0, m0: int = 1, x0=None, x_out=None) -> FeastResult:
     """Host driver with custom half-contour nodes zne and weights wne (complex
     arrays of fpm(2) values, convention of feast_contour_nodes)."""
     f = _fpm(fpm)
@@ -275,9 +295,7 @@ def feast_scsr_solve_x(uplo: str, n: int, a, ia, ja, zne, wne, b=None, ib=None, 
         ib = np.ascontiguousarray(ib, dtype=np.int32)
         jb = np.ascontiguousarray(jb, dtype=np.int32)
     z, w = _nodes(zne, wne)
-    x = np.zeros((n, m0), order="F")
-    if x0 is not None:
-        x[:] = x0
+    x = _host_block(n, m0, x0, x_out, f)
     E = np.zeros(m0)
     res = np.zeros(m0)
     M, loop, info, mm = _i(0), _i(0), _i(0), _i(m0)
@@ -325,7 +343,7 @@ def feast_scsr_solve_dev_x(n: int, ia, ja, a, zne, wne, ib=None, jb=None, b=None
 
 
 def feast_scsr_extreme(uplo: str, n: int, a, ia, ja, b=None, ib=None, jb=None, fpm=None, m0: int = 2,
-                       x0=None) -> FeastResult:
+                       x0=None, x_out=None) -> FeastResult:
     """Host driver of the extreme-eigenvalue mode: fpm(40) = -1 (lowest) or +1
     (largest) selects the m0/2 wanted pairs; the returned FeastResult carries
     the interval found in emin/emax."""
@@ -337,9 +355,7 @@ def feast_scsr_extreme(uplo: str, n: int, a, ia, ja, b=None, ib=None, jb=None, f
         b = np.ascontiguousarray(b, dtype=np.float64)
         ib = np.ascontiguousarray(ib, dtype=np.int32)
         jb = np.ascontiguousarray(jb, dtype=np.int32)
-    x = np.zeros((n, m0), order="F")
-    if x0 is not None:
-        x[:] = x0
+    x = _host_block(n, m0, x0, x_out, f)
     E = np.zeros(m0)
     res = np.zeros(m0)
     M, loop, info, mm = _i(0), _i(0), _i(0), _i(m0)
