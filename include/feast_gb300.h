@@ -299,8 +299,11 @@ int feast_filter_dev(int n, int nnz_a, const int* ia, const int* ja, const doubl
                      const double* lam, int rii, const int* fpm, double emin, double emax, double* Q,
                      int* iters, void* stream);
 
-/* C = X^T Y (m x m, row-major), X and Y device row-major n x m, FP64; the
- * result is symmetrised ((C + C^T)/2) as the Rayleigh-Ritz matrices are. */
+/* C = X^T Y (m x m, row-major), X and Y device row-major n x m, FP64; only
+ * the upper triangle is computed and the result is that triangle mirrored,
+ * C[i][j] = (X^T Y)[min(i,j)][max(i,j)] (the Rayleigh-Ritz matrices Q^T A Q
+ * and Q^T B Q are symmetric up to rounding, and this is their symmetric
+ * form). */
 int feast_gram_dev(int n, int m, const double* X, const double* Y, double* C, void* stream);
 
 /* Allocation-free variant of feast_gram_dev (the paper has no counterpart:

@@ -126,6 +126,10 @@ __global__ void __launch_bounds__(128) gram_f64(int n, int m, const double* __re
     const int r0 = (int)min((long long)n, split * chunk), r1 = (int)min((long long)n, (split + 1) * chunk);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wr = (warp >> 1) * 32, wc = (warp & 1) * 32;
+    // a warp's 32 x 32 sub-tile is needed when it lies inside the m x m matrix
+    // and is not strictly below the diagonal (the result keeps the upper
+    // triangle); the others only help load the shared tiles
+    const bool live = a0 + wr < m && b0 + wc < m && !(ta == tb && wr > wc);
     double acc[4][4][2];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -143,9 +147,10 @@ __global__ void __launch_bounds__(128) gram_f64(int n, int m, const double* __re
             Bs[kk][c] = (rok && b0 + c < m) ? __ldg(Y + (size_t)r * m + b0 + c) : 0.0;
         }
         __syncthreads();
-        tile_mma(As, Bs, acc, wr, wc, lane);
+        if (live) tile_mma(As, Bs, acc, wr, wc, lane);  // warp-uniform
         __syncthreads();
     }
+    if (!live) return;
     double* out = part + (size_t)split * m * m;
     const int g = lane >> 2, tq = lane & 3;
 #pragma unroll
@@ -159,29 +164,17 @@ __global__ void __launch_bounds__(128) gram_f64(int n, int m, const double* __re
         }
 }
 
-// C[i][j] from the upper-tile partials, summed over splits in order.  Diagonal
-// tiles are symmetrised (C + C^T)/2, off-diagonal tiles mirrored.
+// C[i][j] = the upper-triangle partial at (min(i,j), max(i,j)), summed over
+// splits in order: the upper triangle of X^T Y, mirrored.
 __global__ void gram_reduce(int m, const double* __restrict__ part, int ksplit, double* __restrict__ C)
 {
     const long long total = (long long)m * m;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(idx / m), j = (int)(idx % m);
-        const int ti = i / TM, tj = j / TM;
-        double v;
-        if (ti == tj) {
-            double s1 = 0.0, s2 = 0.0;
-            for (int s = 0; s < ksplit; ++s) {
-                s1 += part[(size_t)s * m * m + (size_t)i * m + j];
-                s2 += part[(size_t)s * m * m + (size_t)j * m + i];
-            }
-            v = 0.5 * (s1 + s2);
-        } else {
-            const int a = ti < tj ? i : j, b = ti < tj ? j : i;
-            double s1 = 0.0;
-            for (int s = 0; s < ksplit; ++s) s1 += part[(size_t)s * m * m + (size_t)a * m + b];
-            v = s1;
-        }
+        const int a = i < j ? i : j, b = i < j ? j : i;
+        double v = 0.0;
+        for (int s = 0; s < ksplit; ++s) v += part[(size_t)s * m * m + (size_t)a * m + b];
         C[idx] = v;
     }
 }

@@ -152,15 +152,12 @@ def test_gram(pkg, n, m):
     Y = rng.standard_normal((n, m))
     C = torch.zeros((m, m), dtype=torch.float64, device="cuda")
     pkg.feast_gram_dev(n, m, dev(X), dev(Y), C)
-    ref = X.T @ Y
-    ref = 0.5 * (ref + ref.T)
     got = C.cpu().numpy()
-    # off-diagonal tiles keep the upper product, diagonal tiles are symmetrised
+    # the upper triangle of X^T Y, mirrored
     scale = np.sqrt(n)
     assert np.abs(got - got.T).max() == 0.0
     full = X.T @ Y
-    up = np.where(np.arange(m)[:, None] // 64 < np.arange(m)[None, :] // 64, full, full.T)
-    exp = np.where(np.arange(m)[:, None] // 64 == np.arange(m)[None, :] // 64, ref, up)
+    exp = np.where(np.arange(m)[:, None] <= np.arange(m)[None, :], full, full.T)
     assert np.abs(got - exp).max() < 1e-13 * scale, np.abs(got - exp).max()
 
 
