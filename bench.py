@@ -47,9 +47,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--side", type=int, default=None, help="grid side (default 64; 96 for --workload stencil27)")
-    ap.add_argument("--workload", default="laplace3d", choices=["laplace3d", "stencil27"],
+    ap.add_argument("--workload", default="laplace3d", choices=["laplace3d", "stencil27", "batched", "grad48"],
                     help="laplace3d: 7-point 3D Laplacian + potential, B = I (the headline line); stencil27: "
-                         "27-point generalized problem, B diagonal, lowest 200 eigenvalues, M0 = 300, Ne = 16")
+                         "27-point generalized problem, B diagonal, lowest 200 eigenvalues, M0 = 300, Ne = 16; "
+                         "batched: 512 2D problems in one batched solve; grad48: eigenvalue-loss forward and "
+                         "backward at 48^3")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -555,6 +557,126 @@ def run_stencil27(args):
         print(json.dumps(out))
 
 
+# ---------------------------------------------------------------- batched and gradient workloads
+def _lib_setup():
+    import torch
+
+    import paper_2002_04807_gb300 as pkg
+    from paper_2002_04807_gb300 import build
+
+    rank, ws, local = dist_setup()
+    torch.cuda.set_device(local)
+    build.build()
+    pkg.library()
+    return pkg, rank, ws
+
+
+def run_batched(args):
+    """512 independent 2D 5-point Laplacians + V ~ U[0,1] (sides log-uniform in
+    [32, 256], 8-64 wanted eigenvalues each, M0 = 1.5 x count) in one call of
+    the batched host entry point; timed on the host around the call (copies
+    of the 512 CSRs in and of the results out included)."""
+    import torch
+
+    import feast_workloads as fw
+
+    pkg, rank, ws = _lib_setup()
+    t0 = time.time()
+    probs = fw.batched_laplace2d()
+    t_gen = time.time() - t0
+    dicts = [dict(n=p.n, a=p.A.data, ia=p.A.indptr, ja=p.A.indices, emin=p.emin, emax=p.emax, m0=p.m0, x0=None)
+             for p in probs]
+
+    def fpm(mixed):
+        f = pkg.feast_init()
+        f[1], f[2], f[3], f[17], f[41], f[44], f[45] = 8, 10, 40, 200, mixed, 2, 80
+        return f
+
+    def run(mixed):
+        torch.cuda.synchronize()
+        t = time.time()
+        st, res = pkg.feast_scsr_solve_batched(dicts, fpm(mixed))
+        torch.cuda.synchronize()
+        dt = time.time() - t
+        if st != 0 or any(r.info != 0 for r in res):
+            raise RuntimeError(f"batched FEAST status {st}, infos {sorted(set(r.info for r in res))}")
+        return dt, sum(int(np.sum(r.res[: r.M] <= RES_TOL)) for r in res), res
+
+    for _ in range(args.warmup):
+        run(1)
+    tt, conv = 0.0, 0
+    for _ in range(args.steps):
+        dt, c, res = run(1)
+        tt += dt
+        conv += c
+    value = conv / tt
+    fp64 = None
+    if args.fp64_steps > 0:
+        dt64, c64, _ = run(0)
+        fp64 = {"value": c64 / dt64, "unit": UNIT, "ms_per_step": 1e3 * dt64, "mixed_over_fp64": value / (c64 / dt64)}
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": 1e3 * tt / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "c32 solves + f64 Rayleigh-Ritz",
+               "data": "synthetic (seeded generator, no dataset)",
+               "config": {"workload": "batched_laplace2d_512_sides_32-256_seed3", "problems": len(probs),
+                          "sum_N": int(sum(p.n for p in probs)), "sum_M0": int(sum(p.m0 for p in probs)),
+                          "wanted": int(sum(p.notes.get("target_count", 0) for p in probs)),
+                          "Ne": 8, "contour_ratio_pct": 200, "timing": "host clock around the batched call",
+                          "generation_s": t_gen},
+               "converged_pairs": conv // args.steps, "max_residual": float(max(r.res[: r.M].max() for r in res)),
+               "fp64": fp64}
+        print(json.dumps(out))
+
+
+def run_grad(args):
+    """The differentiation workload: lowest ~64 eigenvalues of the 48^3
+    Laplacian + potential (M0 = 96) as a differentiable tensor, loss
+    sum_k g_k lambda_k, backward over A's CSR values; forward and backward
+    timed separately with CUDA events."""
+    import torch
+
+    import feast_workloads as fw
+    from paper_2002_04807_gb300.autograd import feast_eigenvalues
+
+    pkg, rank, ws = _lib_setup()
+    p = fw.laplace3d_grad()
+    dev = torch.device("cuda")
+    ia, ja = torch.as_tensor(p.A.indptr).to(dev), torch.as_tensor(p.A.indices).to(dev)
+    x0 = torch.as_tensor(np.ascontiguousarray(p.y0().T)).to(dev)
+    f = pkg.feast_init()
+    f[1], f[2], f[3], f[17], f[41], f[44], f[45], f[49] = 8, 12, 40, 200, 1, 2, 200, 1
+
+    def step():
+        av = torch.as_tensor(p.A.data).to(dev).requires_grad_(True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        ev = feast_eigenvalues(av, ia, ja, p.n, p.emin, p.emax, p.m0, f, x0=x0)
+        e1.record()
+        g = torch.as_tensor(fw.loss_weights(ev.numel(), 4), device=dev)
+        (g * ev).sum().backward()
+        e2.record()
+        torch.cuda.synchronize()
+        return ev.numel(), e0.elapsed_time(e1), e1.elapsed_time(e2)
+
+    for _ in range(args.warmup):
+        step()
+    M, fw_ms, bw_ms = 0, 0.0, 0.0
+    for _ in range(args.steps):
+        M, a, b = step()
+        fw_ms += a
+        bw_ms += b
+    if rank == 0:
+        out = {"metric": METRIC, "value": M * args.steps / ((fw_ms + bw_ms) / 1e3), "unit": UNIT, "n_gpus": ws,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": (fw_ms + bw_ms) / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "c32 solves + f64 Rayleigh-Ritz and backward", "data": "synthetic (seeded generator, no dataset)",
+               "config": {"workload": "laplace3d_7pt_48^3_potential_U[0,0.5]_seed4_eigenvalue_loss", "N": p.n,
+                          "M0": p.m0, "M": M, "Ne": 8, "contour_ratio_pct": 200, "tol": 1e-12},
+               "forward_ms": fw_ms / args.steps, "backward_ms": bw_ms / args.steps}
+        print(json.dumps(out))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.side is None:
@@ -563,5 +685,9 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.workload == "stencil27":
         run_stencil27(a)
+    elif a.workload == "batched":
+        run_batched(a)
+    elif a.workload == "grad48":
+        run_grad(a)
     else:
         run_gpu(a)
