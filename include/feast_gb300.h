@@ -95,8 +95,9 @@ int feast_contour_nodes(int ne, double emin, double emax, int ratio_pct, double*
  * (trapezoidal: 1..1024), 200 for emin >= emax. */
 int feast_contour_nodes_rule(int rule, int ne, double emin, double emax, int ratio_pct, double* z, double* w);
 
-/* Timings of the last feast_scsr_solve / feast_scsr_solve_dev of the calling
- * thread run with fpm(53) = 1 (all zero otherwise), measured with CUDA events
+/* Timings of the last solve entry point (feast_scsr_solve*, feast_scsr_extreme*)
+ * of the calling thread run with fpm(53) = 1 (all zero otherwise; an
+ * extreme-eigenvalue search reports the totals of its solves), measured with CUDA events
  * on the solve's stream.  out (host, 16 doubles): [0] ms in COCG step A
  * launches, [1] ms in COCG step B launches, [2] step A launches, [3] step B
  * launches, [4] group-iterations (column groups x COCG steps done), [5] ms in

@@ -873,6 +873,9 @@ int run_feast(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, int* fpm, dou
         CK(cudaMemcpyAsync(&work, B.work, sizeof(work), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         double* o = g_prof.out;
+        // totals over every solve since the entry point started (the extreme
+        // search runs several): recomputed, not added to
+        for (int i = 0; i < 15; ++i) o[i] = 0.0;
         for (auto& pr : g_prof.a) o[0] += g_prof.ms(pr.first, pr.second);
         for (auto& pr : g_prof.b) o[1] += g_prof.ms(pr.first, pr.second);
         o[2] = (double)g_prof.a.size();
