@@ -172,6 +172,68 @@ def helloworld_csr_1based():
 # --------------------------------------------------------------------------
 # Start block and search-interval estimates
 # --------------------------------------------------------------------------
+# --------------------------------------------------------------------------
+# complex Hermitian inputs (zfeast_hcsr-type problems)
+# --------------------------------------------------------------------------
+@dataclass
+class ZCSR:
+    """0-based CSR with complex128 values (full storage)."""
+    n: int
+    indptr: np.ndarray
+    indices: np.ndarray
+    data: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.indptr[-1])
+
+    def to_dense(self) -> np.ndarray:
+        d = np.zeros((self.n, self.n), dtype=np.complex128)
+        for i in range(self.n):
+            s, e = self.indptr[i], self.indptr[i + 1]
+            d[i, self.indices[s:e]] += self.data[s:e]
+        return d
+
+
+def zcsr_from_dense(d: np.ndarray) -> ZCSR:
+    n = d.shape[0]
+    indptr = np.zeros(n + 1, dtype=np.int32)
+    cols, vals = [], []
+    for i in range(n):
+        nz = np.nonzero(d[i])[0]
+        cols.append(nz.astype(np.int32))
+        vals.append(d[i, nz].astype(np.complex128))
+        indptr[i + 1] = indptr[i] + len(nz)
+    return ZCSR(n, indptr, np.concatenate(cols), np.concatenate(vals))
+
+
+def flux_ring(n: int, phi: float) -> ZCSR:
+    """Ring of n sites threaded by a magnetic flux: 2 on the diagonal,
+    -exp(i phi) at (j, j+1 mod n) and its conjugate at (j+1 mod n, j)."""
+    d = np.zeros((n, n), dtype=np.complex128)
+    j = np.arange(n)
+    d[j, j] = 2.0
+    d[j, (j + 1) % n] = -np.exp(1j * phi)
+    d[(j + 1) % n, j] = -np.exp(-1j * phi)
+    return zcsr_from_dense(d)
+
+
+def hermitian_banded(n: int, bw: int, rng: np.random.Generator, shift: float = 0.0) -> ZCSR:
+    """Random complex Hermitian band matrix (half-bandwidth bw), plus shift * I."""
+    d = np.zeros((n, n), dtype=np.complex128)
+    for k in range(1, bw + 1):
+        v = rng.standard_normal(n - k) + 1j * rng.standard_normal(n - k)
+        d += np.diag(v, k) + np.diag(v.conj(), -k)
+    d += np.diag(rng.standard_normal(n) + shift)
+    return zcsr_from_dense(d)
+
+
+def complex_gaussian_block(n: int, m0: int, seed: int) -> np.ndarray:
+    """Y0 with independent N(0,1) real and imaginary parts, (n, m0), Fortran order."""
+    rng = np.random.default_rng(seed)
+    return np.asfortranarray(rng.standard_normal((n, m0)) + 1j * rng.standard_normal((n, m0)))
+
+
 def gaussian_block(n: int, m0: int, seed: int) -> np.ndarray:
     """Y0 ~ N(0,1), shape (n, m0), Fortran (column-major) order."""
     rng = np.random.default_rng(seed)

@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "feast_oracle.c")
+_SRC_HERM = os.path.join(_HERE, "feast_oracle_herm.c")
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -31,9 +32,10 @@ _ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/_build/liboracle.so (gcc, OpenMP)."""
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_HERM))
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < newest:
         tmp = _OUT + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"],
+        subprocess.run(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, _SRC_HERM, "-lm"],
                        check=True)
         os.replace(tmp, _OUT)
     return _OUT
@@ -298,3 +300,91 @@ def feast_scsr(A, B, emin, emax, m0, Y0=None, X0=None, ne=8, ratio=30, tol_exp=1
             "res": res[:k].copy(), "M": M.value, "loop": loop.value, "epsout": eps.value,
             "m0": k, "trace": th[: loop.value + 1].copy(), "maxres": mh[: loop.value + 1].copy(),
             "inner_iters": it.value}
+
+
+# ---------------------------------------------------------------- complex Hermitian (feast_oracle_herm.c)
+def _zcsr_args(M):
+    if M is None:
+        return None, None, None
+    return _c(M.indptr, np.int32), _c(M.indices, np.int32), _c(M.data, np.complex128)
+
+
+def _zf(a):
+    return np.asfortranarray(a, dtype=np.complex128)
+
+
+def h_jacobi_eig(a):
+    """Hermitian Jacobi: (w ascending, V unitary, status)."""
+    a = _zf(a).copy(order="F")
+    n = a.shape[0]
+    w = np.zeros(n)
+    V = np.zeros((n, n), dtype=np.complex128, order="F")
+    st = lib().orc_h_jacobi_eig(C.c_int(n), _ptr(a), _ptr(w), _ptr(V))
+    return w, V, int(st)
+
+
+def h_reduced_gev(Aq, Bq):
+    """Reduced generalized Hermitian problem: (info, lam[:mk], V[:, :mk])."""
+    m = Aq.shape[0]
+    Aq, Bq = _zf(Aq), _zf(Bq)
+    lam = np.zeros(m)
+    V = np.zeros((m, m), dtype=np.complex128, order="F")
+    mk = C.c_int(0)
+    info = lib().orc_h_reduced_gev(C.c_int(m), _ptr(Aq), _ptr(Bq), _ptr(lam), _ptr(V), C.byref(mk))
+    k = mk.value
+    return int(info), lam[:k].copy(), V[:, :k].copy()
+
+
+def h_shifted_solve(A, B, z: complex, R):
+    """(z B - A) X = R by banded LU without pivoting."""
+    R = _zf(R)
+    n, m = R.shape
+    X = np.zeros((n, m), dtype=np.complex128, order="F")
+    ip, ix, v = _zcsr_args(A)
+    bip, bix, bv = _zcsr_args(B)
+    st = lib().orc_h_shifted_solve(C.c_int(n), _ptr(ip), _ptr(ix), _ptr(v), _ptr(bip), _ptr(bix), _ptr(bv),
+                                   C.c_double(z.real), C.c_double(z.imag), C.c_int(m), _ptr(R), _ptr(X))
+    if st:
+        raise RuntimeError("oracle Hermitian shifted solve failed")
+    return X
+
+
+def h_filter(A, B, ne, emin, emax, ratio, Y, rule=0):
+    """Q = sum_e (1/2)[w_e G(z_e) + conj(w_e) G(conj z_e)] B Y (ratio = fpm(18)/100)."""
+    Y = _zf(Y)
+    n, m = Y.shape
+    Q = np.zeros((n, m), dtype=np.complex128, order="F")
+    ip, ix, v = _zcsr_args(A)
+    bip, bix, bv = _zcsr_args(B)
+    st = lib().orc_h_filter(C.c_int(n), _ptr(ip), _ptr(ix), _ptr(v), _ptr(bip), _ptr(bix), _ptr(bv), C.c_int(ne),
+                            C.c_double(emin), C.c_double(emax), C.c_double(ratio), C.c_int(rule), C.c_int(m),
+                            _ptr(Y), _ptr(Q))
+    if st:
+        raise RuntimeError("oracle Hermitian filter failed")
+    return Q
+
+
+def feast_hcsr(A, B, emin, emax, m0, Y0=None, X0=None, ne=8, ratio=100, tol_exp=10, maxloop=20, rule=0):
+    """Plain FP64 FEAST on a complex Hermitian CSR problem (classic filter).
+    Returns a dict with E, X (n x m0', complex), res, M, loop, epsout, info, m0."""
+    n = A.n
+    fpm = feastinit()
+    fpm[1], fpm[2], fpm[3], fpm[15], fpm[17] = ne, tol_exp, maxloop, rule, ratio
+    X = np.zeros((n, m0), dtype=np.complex128, order="F")
+    if X0 is not None:
+        fpm[4] = 1
+        X[:] = X0
+        Y = np.zeros((n, m0), dtype=np.complex128, order="F")
+    else:
+        Y = _zf(Y0)
+    E = np.zeros(m0)
+    res = np.zeros(m0)
+    M, loop, eps, m0io = C.c_int(0), C.c_int(0), C.c_double(0), C.c_int(m0)
+    ip, ix, v = _zcsr_args(A)
+    bip, bix, bv = _zcsr_args(B)
+    info = lib().orc_feast_hcsr(C.c_int(n), _ptr(ip), _ptr(ix), _ptr(v), _ptr(bip), _ptr(bix), _ptr(bv), _ptr(fpm),
+                                C.c_double(emin), C.c_double(emax), C.byref(m0io), _ptr(Y), _ptr(E), _ptr(X),
+                                _ptr(res), C.byref(M), C.byref(loop), C.byref(eps))
+    k = m0io.value
+    return {"info": int(info), "E": E[:k].copy(), "X": np.asfortranarray(X[:, :k]), "res": res[:k].copy(),
+            "M": M.value, "loop": loop.value, "epsout": eps.value, "m0": k}

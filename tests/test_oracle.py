@@ -415,3 +415,98 @@ def test_stochastic_count_estimates_eigenvalue_count():
     assert abs(trace - cnt) < 0.05
     assert 0.0 < sem < 1.0
     assert abs(est - cnt) < 5 * sem
+
+
+# ------------------------------------------------------------------ complex Hermitian oracle (zfeast_hcsr)
+def test_hermitian_jacobi_matches_eigh():
+    rng = np.random.default_rng(41)
+    m = 30
+    g = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    a = g + g.conj().T
+    w, V, st = O.h_jacobi_eig(a)
+    assert st == 0
+    ref = np.linalg.eigvalsh(a)
+    assert np.abs(w - ref).max() < 1e-13 * np.abs(ref).max()
+    assert np.abs(V.conj().T @ V - np.eye(m)).max() < 1e-13
+    assert np.abs(a @ V - V * w).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_hermitian_shifted_solve_matches_dense():
+    rng = np.random.default_rng(42)
+    A = fw.hermitian_banded(60, 3, rng)
+    B = fw.zcsr_from_dense(np.diag(rng.uniform(1, 2, 60)).astype(np.complex128))
+    R = rng.standard_normal((60, 4)) + 1j * rng.standard_normal((60, 4))
+    for z in (0.3 + 0.7j, 0.3 - 0.7j, -2.0 + 0.01j):
+        X = O.h_shifted_solve(A, B, z, R)
+        ref = np.linalg.solve(z * B.to_dense() - A.to_dense(), R)
+        assert np.abs(X - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("gen", [False, True])
+def test_hermitian_filter_matches_dense_spectral_formula(gen):
+    """Q = rho(B^{-1}A) Y = X diag(rho(lambda)) X^H B Y (X^H B X = I): both
+    halves of the contour are needed once A is complex."""
+    rng = np.random.default_rng(43)
+    A = fw.hermitian_banded(80, 4, rng, shift=6.0)
+    B = fw.zcsr_from_dense(np.diag(rng.uniform(1, 2, 80)).astype(np.complex128)) if gen else None
+    db = np.eye(80) if B is None else B.to_dense()
+    lam, X = scipy.linalg.eigh(A.to_dense(), db)
+    emin, emax = lam[10] - 0.3, 0.5 * (lam[25] + lam[26])
+    Y = rng.standard_normal((80, 5)) + 1j * rng.standard_normal((80, 5))
+    Q = O.h_filter(A, B, 8, emin, emax, 1.0, Y)
+    r = _rho_dense(8, emin, emax, 1.0, lam)
+    ref = X @ (r[:, None] * (X.conj().T @ (db @ Y)))
+    assert np.abs(Q - ref).max() < 1e-11 * np.abs(ref).max()
+    # dropping the conjugate half (as the real symmetric filter may) is wrong here
+    z, w = O.contour_gauss(8, emin, emax, 1.0)
+    half = sum(O.h_shifted_solve(A, B, complex(ze), db @ Y) * we for ze, we in zip(z, w))
+    assert np.abs(half.real - ref.real).max() > 1e-3 * np.abs(ref).max()
+
+
+def test_hermitian_feast_flux_ring_closed_form():
+    """Ring of 200 sites with flux phi: lambda_m = 2 - 2 cos(2 pi m / n + phi),
+    eigenvectors the plane waves exp(i (2 pi m / n) j) / sqrt(n)."""
+    n, phi = 200, 0.013
+    A = fw.flux_ring(n, phi)
+    mm = np.arange(n)
+    lam = 2 - 2 * np.cos(2 * np.pi * mm / n + phi)
+    order = np.argsort(lam)
+    lam_s = lam[order]
+    emax = 0.5 * (lam_s[20] + lam_s[21])
+    Y0 = fw.complex_gaussian_block(n, 32, 0)
+    ref = O.feast_hcsr(A, None, 0.0, emax, 32, Y0=Y0, ne=8, ratio=100, tol_exp=12)
+    assert ref["info"] == 0 and ref["M"] == 21
+    assert np.abs(ref["E"][:21] - lam_s[:21]).max() < 1e-13
+    assert ref["res"][:21].max() < 1e-12
+    waves = np.exp(1j * np.outer(np.arange(n), 2 * np.pi * mm[order[:21]] / n)) / np.sqrt(n)
+    X = ref["X"][:, :21]
+    assert np.abs(X.conj().T @ X - np.eye(21)).max() < 1e-12
+    qx, _ = np.linalg.qr(X)
+    assert np.linalg.norm(waves - qx @ (qx.conj().T @ waves), 2) < 1e-9
+
+
+def test_hermitian_feast_generalized_matches_dense():
+    rng = np.random.default_rng(44)
+    A = fw.hermitian_banded(300, 5, rng, shift=8.0)
+    B = fw.zcsr_from_dense(np.diag(rng.uniform(1, 2, 300)).astype(np.complex128))
+    lam = scipy.linalg.eigh(A.to_dense(), B.to_dense(), eigvals_only=True)
+    emin, emax = lam[0] - 0.5, 0.5 * (lam[29] + lam[30])
+    ref = O.feast_hcsr(A, B, emin, emax, 48, Y0=fw.complex_gaussian_block(300, 48, 1), ne=8, ratio=100,
+                       tol_exp=12)
+    assert ref["info"] == 0 and ref["M"] == 30
+    assert np.abs(ref["E"][:30] - lam[:30]).max() < 1e-12 * np.abs(lam).max()
+    X = ref["X"][:, :30]
+    assert np.abs(X.conj().T @ B.to_dense() @ X - np.eye(30)).max() < 1e-12
+
+
+def test_hermitian_feast_reduces_to_real_symmetric():
+    """A real symmetric matrix stored as complex: same eigenvalues as the real
+    oracle, trapezoidal rule included."""
+    p = fw.laplace3d_potential(side=6, count=10, m0=16, seed=12)
+    Az = fw.zcsr_from_dense(p.A.to_dense().astype(np.complex128))
+    for rule in (0, 1):
+        r = O.feast_scsr(p.A, None, p.emin, p.emax, 16, Y0=p.y0(), ne=8, ratio=100, tol_exp=12, rule=rule)
+        h = O.feast_hcsr(Az, None, p.emin, p.emax, 16, Y0=p.y0().astype(np.complex128), ne=8, ratio=100,
+                         tol_exp=12, rule=rule)
+        assert r["info"] == h["info"] == 0 and r["M"] == h["M"]
+        assert np.abs(r["E"][: r["M"]] - h["E"][: h["M"]]).max() < 1e-12
