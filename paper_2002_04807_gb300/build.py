@@ -46,7 +46,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
 
-    extra = os.environ.get("FEAST_NVCC_EXTRA", "").split()  # developer knob, e.g. -DFEAST_ROWS=2
+    extra = os.environ.get("FEAST_NVCC_EXTRA", "").split()  # developer knob, e.g. -DFEAST_MINB=4 (CTAs per SM of the gathering step)
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
