@@ -226,3 +226,20 @@ def test_workspace_size_grows_with_problem(pkg):
     f64 = f.copy()
     f64[41] = 0
     assert pkg.feast_scsr_workspace_bytes(262144, 1810432, 0, 150, f64) > big
+
+
+def test_host_block_argument_checks(pkg):
+    """x_out must be a Fortran-ordered float64 (n, m0) array; x0 must have
+    shape (n, m0).  Checked before the library is called."""
+    from paper_2002_04807_gb300 import FeastError
+
+    A = fw.laplacian_1d(20)
+    base = dict(uplo="F", n=20, a=A.data, ia=A.indptr, ja=A.indices, emin=0.0, emax=0.5, m0=6)
+    with pytest.raises(FeastError):
+        pkg.feast_scsr_solve(**base, x_out=np.zeros((20, 6)))  # C order
+    with pytest.raises(FeastError):
+        pkg.feast_scsr_solve(**base, x_out=np.zeros((20, 5), order="F"))
+    with pytest.raises(FeastError):
+        pkg.feast_scsr_solve(**base, x_out=np.zeros((20, 6), dtype=np.float32, order="F"))
+    with pytest.raises(FeastError):
+        pkg.feast_scsr_solve(**base, x0=np.zeros((19, 6)))
