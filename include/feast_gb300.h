@@ -16,8 +16,8 @@
  *  - fpm is the 64-entry parameter array of the guide's parameter table
  *    (Sec. 3.1), C indexing fpm[i-1] = fpm(i).  Used entries:
  *      fpm(1)  0 silent, 1 per-iteration log on stdout, n<0 append to feast<|n|>.log
- *      fpm(2)  Ne, number of half-contour nodes (Gauss: 1..20, 24, 32, 40, 48, 56;
- *              trapezoidal: 1..1024)
+ *      fpm(2)  Ne, number of half-contour nodes (Gauss and Zolotarev: 1..20, 24,
+ *              32, 40, 48, 56; trapezoidal: 1..1024)
  *      fpm(3)  stopping tolerance 10^-fpm(3) on the relative residual (0..16)
  *      fpm(4)  maximum number of refinement loops (>= 0)
  *      fpm(5)  1: X holds the start subspace on entry; 0: a random start block
@@ -25,7 +25,8 @@
  *      fpm(14) 0 normal run; 1 return the block Q after one contour pass
  *              (info 4); 2 stochastic estimate of the number of eigenvalues
  *              inside the contour (info 5), see feast_scsr_solve
- *      fpm(16) 0 Gauss-Legendre nodes, 1 trapezoidal nodes (2, Zolotarev, -> 116)
+ *      fpm(16) 0 Gauss-Legendre nodes, 1 trapezoidal nodes, 2 Zolotarev nodes
+ *              (see feast_contour_nodes_rule)
  *      fpm(18) ellipse ratio in percent (> 0)
  *      fpm(40) 0 search interval given (feast_scsr_solve*); -1 / +1 search
  *              the M0/2 lowest / largest eigenpairs (feast_scsr_extreme*)
@@ -85,14 +86,21 @@ const char* feast_last_error(void);
 int feast_contour_nodes(int ne, double emin, double emax, int ratio_pct, double* z, double* w);
 
 /* Nodes and weights of the quadrature rule fpm(16) = rule (guide Sec. 3.1,
- * parameter table: 0 Gauss-Legendre, 1 trapezoidal) on the same half
- * contour.  A rule with nodes t_e in [0, pi] and t-weights v_e gives
- * w_e = (v_e r / pi)(a cos(t_e) + i sin(t_e)); the trapezoidal rule takes the
- * midpoints t_e = pi (e - 1/2) / ne, e = 1..ne, v_e = pi / ne (with the
- * conjugate half, 2 ne equally spaced points of the whole contour; on a
- * circle its filter is 1 / (1 + ((lambda - c)/r)^(2 ne))).  rule 0 equals
+ * parameter table: 0 Gauss-Legendre, 1 trapezoidal, 2 Zolotarev).  Gauss and
+ * trapezoidal lie on the half ellipse of ratio_pct: a rule with nodes t_e in
+ * [0, pi] and t-weights v_e gives w_e = (v_e r / pi)(a cos(t_e) + i sin(t_e));
+ * the trapezoidal rule takes the midpoints t_e = pi (e - 1/2) / ne,
+ * v_e = pi / ne (with the conjugate half, 2 ne equally spaced points of the
+ * whole contour; on a circle its filter is 1 / (1 + ((lambda - c)/r)^(2 ne))).
+ * Zolotarev (the guide cites Guettel, Polizzi, Tang and Viaud; ratio_pct not
+ * used): with x = (lambda - c)/r, the filter is the best uniform rational
+ * approximation of the interval's indicator outside the edge bands
+ * 1/(1.05) < |x| < 1.05, built from Zolotarev's best approximation of the
+ * sign function through u = (1 + x)/(1 - x); its ne conjugate pole pairs lie
+ * on the circle through Emin and Emax and its error equioscillates (constant
+ * term rho(inf), below half that error, left out).  rule 0 equals
  * feast_contour_nodes.  Returns 0, 116 for another rule, 102 for a bad ne
- * (trapezoidal: 1..1024), 200 for emin >= emax. */
+ * (trapezoidal: 1..1024; otherwise the Gauss counts), 200 for emin >= emax. */
 int feast_contour_nodes_rule(int rule, int ne, double emin, double emax, int ratio_pct, double* z, double* w);
 
 /* Timings of the last solve entry point (feast_scsr_solve*, feast_scsr_extreme*)

@@ -48,6 +48,7 @@ def lib():
             _lib = C.CDLL(build())
             _lib.orc_rho.restype = C.c_double
             _lib.orc_count_below.restype = C.c_long
+            _lib.orc_ellipk.restype = C.c_double
     return _lib
 
 
@@ -96,12 +97,35 @@ def contour_trapezoid(ne: int, emin: float, emax: float, ratio: float):
     return z[0::2] + 1j * z[1::2], w[0::2] + 1j * w[1::2]
 
 
+def contour_zolotarev(ne: int, emin: float, emax: float, eta: float = 0.05):
+    """Zolotarev nodes z_e and weights w_e (fpm(16)=2) on the circle through
+    Emin, Emax; eta = width of the edge transition band / half-width."""
+    z = np.zeros(2 * ne)
+    w = np.zeros(2 * ne)
+    lib().orc_contour_zolotarev(C.c_int(ne), C.c_double(emin), C.c_double(emax), C.c_double(eta),
+                                _ptr(z), _ptr(w))
+    return z[0::2] + 1j * z[1::2], w[0::2] + 1j * w[1::2]
+
+
+def ellipk(m: float) -> float:
+    return float(lib().orc_ellipk(C.c_double(m)))
+
+
+def ellipj(u: float, m: float):
+    sn, cn = C.c_double(0), C.c_double(0)
+    lib().orc_ellipj(C.c_double(u), C.c_double(m), C.byref(sn), C.byref(cn))
+    return sn.value, cn.value
+
+
 def rho(ne: int, emin: float, emax: float, ratio: float, lam, rule: int = 0):
     z = np.zeros(2 * ne)
     w = np.zeros(2 * ne)
     L = lib()
-    nodes = L.orc_contour_trapezoid if rule == 1 else L.orc_contour_gauss
-    nodes(C.c_int(ne), C.c_double(emin), C.c_double(emax), C.c_double(ratio), _ptr(z), _ptr(w))
+    if rule == 2:
+        L.orc_contour_zolotarev(C.c_int(ne), C.c_double(emin), C.c_double(emax), C.c_double(0.05), _ptr(z), _ptr(w))
+    else:
+        nodes = L.orc_contour_trapezoid if rule == 1 else L.orc_contour_gauss
+        nodes(C.c_int(ne), C.c_double(emin), C.c_double(emax), C.c_double(ratio), _ptr(z), _ptr(w))
     lam = np.atleast_1d(np.asarray(lam, dtype=np.float64))
     return np.array([L.orc_rho(C.c_int(ne), _ptr(z), _ptr(w), C.c_double(v)) for v in lam])
 

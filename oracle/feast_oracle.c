@@ -128,9 +128,138 @@ int orc_contour_trapezoid(int ne, double emin, double emax, double ratio, double
     return 0;
 }
 
-/* Nodes of the quadrature rule fpm(16): 0 Gauss-Legendre, 1 trapezoidal. */
+/* Jacobi elliptic functions for the Zolotarev rule.  K(m) = pi / (2 AGM(1,
+ * sqrt(1-m))); sn and cn by the descending Landen (AGM) scheme: a_0 = 1,
+ * b_0 = sqrt(1-m), c_0 = sqrt(m), a_{i+1} = (a_i+b_i)/2, b_{i+1} = sqrt(a_i b_i),
+ * c_{i+1} = (a_i-b_i)/2 until c_N is negligible; phi_N = 2^N a_N u and
+ * phi_{i-1} = (phi_i + asin(c_i sin(phi_i) / a_i)) / 2; sn = sin phi_0,
+ * cn = cos phi_0 (m = k^2 is the parameter). */
+double orc_ellipk(double m)
+{
+    double a = 1.0, b = sqrt(1.0 - m);
+    for (int i = 0; i < 60 && fabs(a - b) > 1e-16 * a; ++i) {
+        double an = 0.5 * (a + b);
+        b = sqrt(a * b);
+        a = an;
+    }
+    return M_PI / (2.0 * a);
+}
+
+void orc_ellipj(double u, double m, double* sn, double* cn)
+{
+    double a[64], c[64];
+    double b = sqrt(1.0 - m);
+    a[0] = 1.0;
+    c[0] = sqrt(m);
+    int N = 0;
+    while (N < 62 && fabs(c[N]) > 1e-16) {
+        a[N + 1] = 0.5 * (a[N] + b);
+        c[N + 1] = 0.5 * (a[N] - b);
+        b = sqrt(a[N] * b);
+        ++N;
+    }
+    double phi = ldexp(a[N] * u, N);
+    for (int i = N; i > 0; --i) phi = 0.5 * (phi + asin(c[i] * sin(phi) / a[i]));
+    *sn = sin(phi);
+    *cn = cos(phi);
+}
+
+/* Zolotarev rule (fpm(16)=2).  With x = (lambda - c)/r and the Moebius map
+ * u = (1 + x)/(1 - x), the indicator of [Emin, Emax] is (1 + sign(u))/2.
+ * Outside a transition band |x -+ 1| < eta at the two edges, u lies in
+ * [-R, -1/R] or [1/R, R], R = (2 + eta)/eta; s = u/R lies in
+ * [-1, -l] U [l, 1], l = 1/R^2.  Zolotarev's best approximation of sign(s)
+ * there among odd rationals of type (2n-1, 2n), n = 2 ne, vanishing at 0 and
+ * infinity, is Z(s) = M s prod_{j<ne} (s^2 + c_{2j}) / prod_{j<=ne} (s^2 + c_{2j-1}),
+ * c_j = l^2 sn^2(j K'/n; l') / cn^2(j K'/n; l'), l' = sqrt(1 - l^2),
+ * K' = K(l'^2), and M = 2 / (max Zhat + min Zhat) over [l, 1] (Zhat = Z/M) so
+ * that 1 - Z equioscillates.  The filter rho = (1 + Z(u/R))/2 is a real
+ * rational function of lambda with ne conjugate pole pairs; its poles
+ * s_k = i sqrt(c_{2k-1}) map to x_k = (R s_k - 1)/(R s_k + 1) on the unit
+ * circle, z_k = c + r x_k, and partial fractions give
+ * rho(lambda) = rho(inf) + sum_k Re(w_k / (z_k - lambda)),
+ * w_k = -nu_k R r (1 - x_k)^2 / 2, nu_k the residue of Z at s_k.  The constant
+ * rho(inf) = (1 + Z(-1/R))/2, at most half the approximation error, is
+ * dropped (the filter form has no constant term).  Returns 0, or -1 for ne < 1. */
+static cplx zolo_hat(int ne, const double* codd, const double* ceven, cplx s)
+{
+    cplx num = s, den = 1.0;
+    for (int j = 0; j < ne - 1; ++j) num *= s * s + ceven[j];
+    for (int j = 0; j < ne; ++j) den *= s * s + codd[j];
+    return num / den;
+}
+
+int orc_contour_zolotarev(int ne, double emin, double emax, double eta, double* z, double* w)
+{
+    if (ne < 1) return -1;
+    const int n = 2 * ne;
+    const double R = (2.0 + eta) / eta, l = 1.0 / (R * R), mp = 1.0 - l * l;
+    const double Kp = orc_ellipk(mp);
+    double* codd = (double*)malloc(sizeof(double) * ne);
+    double* ceven = (double*)malloc(sizeof(double) * (ne > 1 ? ne - 1 : 1));
+    for (int j = 1; j < n; ++j) {
+        double sn, cn;
+        orc_ellipj(j * Kp / n, mp, &sn, &cn);
+        const double cj = l * l * sn * sn / (cn * cn);
+        if (j % 2) codd[j / 2] = cj;
+        else ceven[j / 2 - 1] = cj;
+    }
+    /* extremes of Zhat on [l, 1]: log-spaced grid, then golden-section refinement */
+    const int G = 20000;
+    double zmin = INFINITY, zmax = -INFINITY;
+    for (int g = 0; g <= G; ++g) {
+        const double s = l * pow(1.0 / l, (double)g / G);
+        const double v = creal(zolo_hat(ne, codd, ceven, s));
+        if (v < zmin) zmin = v;
+        if (v > zmax) zmax = v;
+        if (g > 0 && g < G) {
+            const double s0 = l * pow(1.0 / l, (double)(g - 1) / G), s1 = l * pow(1.0 / l, (double)(g + 1) / G);
+            const double v0 = creal(zolo_hat(ne, codd, ceven, s0)), v1 = creal(zolo_hat(ne, codd, ceven, s1));
+            const int is_max = v >= v0 && v >= v1, is_min = v <= v0 && v <= v1;
+            if (is_max || is_min) {
+                double a = s0, b = s1;
+                const double gr = 0.5 * (sqrt(5.0) - 1.0);
+                for (int it = 0; it < 80; ++it) {
+                    const double c1 = b - gr * (b - a), c2 = a + gr * (b - a);
+                    const double f1 = creal(zolo_hat(ne, codd, ceven, c1)), f2 = creal(zolo_hat(ne, codd, ceven, c2));
+                    if (is_max ? f1 > f2 : f1 < f2) b = c2;
+                    else a = c1;
+                }
+                const double ve = creal(zolo_hat(ne, codd, ceven, 0.5 * (a + b)));
+                if (ve < zmin) zmin = ve;
+                if (ve > zmax) zmax = ve;
+            }
+        }
+    }
+    const double M = 2.0 / (zmax + zmin);
+    const double c = 0.5 * (emin + emax), r = 0.5 * (emax - emin);
+    for (int k = 0; k < ne; ++k) {
+        const cplx sk = I * sqrt(codd[k]);
+        cplx num = M;
+        for (int j = 0; j < ne - 1; ++j) num *= sk * sk + ceven[j];
+        double den = 2.0;
+        for (int j = 0; j < ne; ++j)
+            if (j != k) den *= codd[j] - codd[k];
+        const cplx nu = num / den;
+        const cplx xk = (R * sk - 1.0) / (R * sk + 1.0);
+        const cplx zk = c + r * xk, wk = -nu * R * r * (1.0 - xk) * (1.0 - xk) / 2.0;
+        z[2 * k] = creal(zk);
+        z[2 * k + 1] = cimag(zk);
+        w[2 * k] = creal(wk);
+        w[2 * k + 1] = cimag(wk);
+    }
+    free(codd);
+    free(ceven);
+    return 0;
+}
+
+/* Nodes of the quadrature rule fpm(16): 0 Gauss-Legendre, 1 trapezoidal,
+ * 2 Zolotarev (circle, ratio ignored, edge band eta = 0.05). */
+static const double kZoloEta = 0.05;
+
 static int contour_nodes(int rule, int ne, double emin, double emax, double ratio, double* z, double* w)
 {
+    if (rule == 2) return orc_contour_zolotarev(ne, emin, emax, kZoloEta, z, w);
     return rule == 1 ? orc_contour_trapezoid(ne, emin, emax, ratio, z, w)
                      : orc_contour_gauss(ne, emin, emax, ratio, z, w);
 }
@@ -756,7 +885,7 @@ int orc_feast_scsr(int n, const int* ip, const int* ix, const double* av,
     if (!(emin < emax)) return 200;
     int ne = fpm[1];
     if (ne < 1) return 102;
-    if (fpm[15] != 0 && fpm[15] != 1) return 116;
+    if (fpm[15] < 0 || fpm[15] > 2) return 116;
     ocsr A = {n, ip, ix, av}, Bm = {n, bip, bix, bv};
     const ocsr* B = bip ? &Bm : NULL;
     double ratio = fpm[17] / 100.0;

@@ -32,6 +32,7 @@ typedef double complex cplx;
 
 int orc_contour_gauss(int ne, double emin, double emax, double ratio, double* z, double* w);
 int orc_contour_trapezoid(int ne, double emin, double emax, double ratio, double* z, double* w);
+int orc_contour_zolotarev(int ne, double emin, double emax, double eta, double* z, double* w);
 
 typedef struct {
     int n;
@@ -333,7 +334,8 @@ int orc_h_filter(int n, const int* ip, const int* ix, const cplx* av, const int*
     hcsr A = {n, ip, ix, av}, Bm = {n, bip, bix, bv};
     double* z = (double*)malloc(sizeof(double) * 2 * ne);
     double* w = (double*)malloc(sizeof(double) * 2 * ne);
-    if (rule == 1) orc_contour_trapezoid(ne, emin, emax, ratio, z, w);
+    if (rule == 2) orc_contour_zolotarev(ne, emin, emax, 0.05, z, w);
+    else if (rule == 1) orc_contour_trapezoid(ne, emin, emax, ratio, z, w);
     else orc_contour_gauss(ne, emin, emax, ratio, z, w);
     const int st = h_filter(&A, bip ? &Bm : NULL, ne, z, w, m, Y, Q);
     free(z);
@@ -386,7 +388,8 @@ int orc_feast_hcsr(int n, const int* ip, const int* ix, const cplx* av, const in
     const double alpha = fmax(fabs(emin), fabs(emax));
     double* z = (double*)malloc(sizeof(double) * 2 * ne);
     double* w = (double*)malloc(sizeof(double) * 2 * ne);
-    if (fpm[15] == 1) orc_contour_trapezoid(ne, emin, emax, ratio, z, w);
+    if (fpm[15] == 2) orc_contour_zolotarev(ne, emin, emax, 0.05, z, w);
+    else if (fpm[15] == 1) orc_contour_trapezoid(ne, emin, emax, ratio, z, w);
     else orc_contour_gauss(ne, emin, emax, ratio, z, w);
     const size_t nm = (size_t)n * m0;
     cplx* Q = (cplx*)malloc(sizeof(cplx) * nm);

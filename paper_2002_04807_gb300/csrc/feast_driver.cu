@@ -16,6 +16,7 @@
 // inverse form (right-hand side R, see k_filter.cu), which keeps the
 // single-precision solves from limiting the FP64 accuracy of the result.
 #include <algorithm>
+#include <complex>
 #include <cmath>
 #include <mutex>
 #include <cstdio>
@@ -72,8 +73,8 @@ static constexpr int kMaxTrapezoidNodes = 1024;
 
 static int check_fpm(const int* fpm)
 {
-    if (fpm[15] != 0 && fpm[15] != 1) return 116;  // Zolotarev (2) is not built
-    if (fpm[15] == 0 ? !gauss_ne_ok(fpm[1]) : (fpm[1] < 1 || fpm[1] > kMaxTrapezoidNodes)) return 102;
+    if (fpm[15] < 0 || fpm[15] > 2) return 116;
+    if (fpm[15] != 1 ? !gauss_ne_ok(fpm[1]) : (fpm[1] < 1 || fpm[1] > kMaxTrapezoidNodes)) return 102;
     if (fpm[2] < 0 || fpm[2] > 16) return 103;
     if (fpm[3] < 0) return 104;
     if (fpm[4] != 0 && fpm[4] != 1) return 105;
@@ -127,6 +128,112 @@ static void gl_rule(int n, std::vector<double>& x, std::vector<double>& w)
 }
 
 // zw[4e..4e+3] = (Re z_e, Im z_e, Re w_e, Im w_e)
+// ---------------------------------------------------------------- Zolotarev rule
+// Complete elliptic integral K(m) by the arithmetic-geometric mean, and
+// sn(u|m), cn(u|m) by the descending Landen transformation (m = k^2).
+static double ell_k(double m)
+{
+    double a = 1.0, g = std::sqrt(1.0 - m);
+    for (int it = 0; it < 64 && std::fabs(a - g) > 4e-16 * a; ++it) {
+        const double t = 0.5 * (a + g);
+        g = std::sqrt(a * g);
+        a = t;
+    }
+    return M_PI / (2.0 * a);
+}
+
+static void ell_sncn(double u, double m, double& sn, double& cn)
+{
+    std::vector<double> as{1.0}, cs{std::sqrt(m)};
+    double b = std::sqrt(1.0 - m);
+    while (std::fabs(cs.back()) > 1e-16 && as.size() < 64) {
+        const double a = as.back();
+        as.push_back(0.5 * (a + b));
+        cs.push_back(0.5 * (a - b));
+        b = std::sqrt(a * b);
+    }
+    const int N = (int)as.size() - 1;
+    double phi = std::ldexp(as[N] * u, N);
+    for (int i = N; i >= 1; --i) phi = 0.5 * (phi + std::asin(cs[i] * std::sin(phi) / as[i]));
+    sn = std::sin(phi);
+    cn = std::cos(phi);
+}
+
+static constexpr double kZolotarevEta = 0.05;  // edge band half-width / interval half-width
+
+// Zolotarev rule (fpm(16) = 2; the guide cites Guettel, Polizzi, Tang and
+// Viaud and prints no formula).  With x = (lambda - c)/r and u = (1+x)/(1-x)
+// the interval's indicator is (1 + sign u)/2; away from the edge bands
+// (|x| <= 1/(1+eta) inside, |x| >= 1+eta outside) s = u/R, R = (2+eta)/eta,
+// lies in [-1, -l] U [l, 1], l = 1/R^2.  Zolotarev's best odd rational
+// approximation of sign(s) there of type (2n-1, 2n), n = 2 ne:
+// Z(s) = M s prod_{j=1}^{ne-1} (s^2 + c_{2j}) / prod_{j=1}^{ne} (s^2 + c_{2j-1}),
+// c_j = l^2 sn^2(j K'/n | 1-l^2) / cn^2(j K'/n | 1-l^2), K' = K(1-l^2), with
+// M = 2/(max + min of Z/M over [l, 1]).  rho = (1 + Z(u/R))/2 has ne
+// conjugate pole pairs on the circle through Emin and Emax: the node of
+// s_k = i sqrt(c_{2k-1}) is z_k = c + r x_k, x_k = (R s_k - 1)/(R s_k + 1),
+// with weight w_k = -nu_k R r (1 - x_k)^2 / 2 (nu_k: residue of Z at s_k), so
+// that rho(lambda) = rho(inf) + sum_k Re(w_k/(z_k - lambda)); the constant
+// rho(inf), below half the approximation error, is left out.
+static void zolotarev(int ne, double emin, double emax, std::vector<double>& zw)
+{
+    const int n = 2 * ne;
+    const double R = (2.0 + kZolotarevEta) / kZolotarevEta, l = 1.0 / (R * R), mc = 1.0 - l * l;
+    const double Kc = ell_k(mc);
+    std::vector<double> co(ne), ce(std::max(ne - 1, 0));  // c_{2k-1}, c_{2k}
+    for (int j = 1; j < n; ++j) {
+        double sn = 0.0, cn = 0.0;
+        ell_sncn(j * Kc / n, mc, sn, cn);
+        const double cj = l * l * (sn / cn) * (sn / cn);
+        if (j & 1) co[(j - 1) / 2] = cj;
+        else ce[j / 2 - 1] = cj;
+    }
+    auto zhat = [&](double sv) {  // Z/M on the positive real axis
+        double v = sv;
+        for (double c : ce) v *= sv * sv + c;
+        for (double c : co) v /= sv * sv + c;
+        return v;
+    };
+    // extremes over [l, 1]: log grid; at each local extremum the vertex of the
+    // parabola through its three grid points (error in the value ~ h^4)
+    const int G = 40000;
+    std::vector<double> t(G + 1), v(G + 1);
+    for (int g = 0; g <= G; ++g) {
+        t[g] = std::log(l) * (1.0 - (double)g / G);
+        v[g] = zhat(std::exp(t[g]));
+    }
+    double vmin = std::min(v[0], v[G]), vmax = std::max(v[0], v[G]);
+    for (int g = 1; g < G; ++g) {
+        if ((v[g] - v[g - 1]) * (v[g + 1] - v[g]) > 0.0) continue;
+        const double h = t[g + 1] - t[g], curv = v[g + 1] - 2.0 * v[g] + v[g - 1];
+        double f = v[g];
+        if (curv != 0.0) {
+            const double d = std::max(-1.0, std::min(1.0, 0.5 * (v[g - 1] - v[g + 1]) / curv));
+            f = zhat(std::exp(t[g] + d * h));
+        }
+        vmin = std::min(vmin, f);
+        vmax = std::max(vmax, f);
+    }
+    const double M = 2.0 / (vmax + vmin);
+    const double c = 0.5 * (emin + emax), r = 0.5 * (emax - emin);
+    zw.assign(4 * (size_t)ne, 0.0);
+    for (int k = 0; k < ne; ++k) {
+        const std::complex<double> sk(0.0, std::sqrt(co[k]));
+        std::complex<double> num(M, 0.0);
+        for (double cv : ce) num *= sk * sk + cv;
+        double den = 2.0;
+        for (int j = 0; j < ne; ++j)
+            if (j != k) den *= co[j] - co[k];
+        const std::complex<double> nu = num / den;
+        const std::complex<double> xk = (R * sk - 1.0) / (R * sk + 1.0);
+        const std::complex<double> zk = c + r * xk, wk = -nu * (R * r / 2.0) * (1.0 - xk) * (1.0 - xk);
+        zw[4 * k] = zk.real();
+        zw[4 * k + 1] = zk.imag();
+        zw[4 * k + 2] = wk.real();
+        zw[4 * k + 3] = wk.imag();
+    }
+}
+
 // Nodes and weights of the quadrature rule fpm(16) on the upper half of the
 // ellipse z(t) = c + r cos t + i a r sin t, t in [0, pi]: a rule with nodes
 // t_e and t-weights v_e gives w_e = (v_e / (i pi)) z'(t_e)
@@ -136,6 +243,10 @@ static void gl_rule(int n, std::vector<double>& x, std::vector<double>& w)
 // half are 2 ne equally spaced points of the whole contour.
 static void contour(int rule, int ne, double emin, double emax, double ratio, std::vector<double>& zw)
 {
+    if (rule == 2) {  // Zolotarev: its own nodes on the circle (ratio not used)
+        zolotarev(ne, emin, emax, zw);
+        return;
+    }
     std::vector<double> t(ne), v(ne);
     if (rule == 1) {
         for (int e = 0; e < ne; ++e) {
@@ -179,8 +290,8 @@ extern "C" int feast_contour_nodes(int ne, double emin, double emax, int ratio_p
 extern "C" int feast_contour_nodes_rule(int rule, int ne, double emin, double emax, int ratio_pct, double* z,
                                         double* w)
 {
-    if (rule != 0 && rule != 1) return 116;
-    if (rule == 0 ? !gauss_ne_ok(ne) : (ne < 1 || ne > kMaxTrapezoidNodes)) return 102;
+    if (rule < 0 || rule > 2) return 116;
+    if (rule != 1 ? !gauss_ne_ok(ne) : (ne < 1 || ne > kMaxTrapezoidNodes)) return 102;
     if (!(emin < emax)) return 200;
     std::vector<double> zw;
     contour(rule, ne, emin, emax, ratio_pct / 100.0, zw);

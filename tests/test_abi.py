@@ -76,17 +76,28 @@ def test_trapezoid_nodes_match_oracle(pkg, ne, ratio):
     assert np.abs(zg - zg0).max() < 1e-15 and np.abs(wg - wg0).max() < 1e-15
 
 
+@pytest.mark.parametrize("ne", [1, 2, 8, 16, 56])
+def test_zolotarev_nodes_match_oracle(pkg, ne):
+    """fpm(16)=2: the library's Zolotarev nodes and weights against the
+    oracle's, written separately from the same construction."""
+    z, w = pkg.feast_contour_nodes_rule(2, ne, -1.5, 2.5, 100)
+    zo, wo = O.contour_zolotarev(ne, -1.5, 2.5)
+    assert np.abs(z - zo).max() < 1e-13 and np.abs(w - wo).max() < 1e-13 * np.abs(wo).max()
+
+
 def test_rule_and_node_count_checks(pkg):
     from paper_2002_04807_gb300 import FeastError
 
     with pytest.raises(FeastError):
-        pkg.feast_contour_nodes_rule(2, 8, 0.0, 1.0, 30)
+        pkg.feast_contour_nodes_rule(3, 8, 0.0, 1.0, 30)
     with pytest.raises(FeastError):
         pkg.feast_contour_nodes_rule(1, 1025, 0.0, 1.0, 30)
+    with pytest.raises(FeastError):
+        pkg.feast_contour_nodes_rule(2, 21, 0.0, 1.0, 30)  # Zolotarev takes the Gauss node counts
     A = fw.laplacian_1d(20)
     base = dict(uplo="F", n=20, a=A.data, ia=A.indptr, ja=A.indices, emin=0.0, emax=0.5, m0=6)
     f = pkg.feast_init()
-    f[15], f[1] = 2, 8
+    f[15], f[1] = 3, 8
     assert pkg.feast_scsr_solve(**base, fpm=f).info == 116
     f[15], f[1] = 1, 0
     assert pkg.feast_scsr_solve(**base, fpm=f).info == 102
@@ -127,7 +138,7 @@ def test_argument_errors_are_host_side(pkg):
     f[1] = 21
     assert run(fpm=f) == 102
     f = pkg.feast_init()
-    f[15] = 2
+    f[15] = 3
     assert run(fpm=f) == 116
     bad = A.indices.copy()
     bad[3] = 99

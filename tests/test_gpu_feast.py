@@ -198,6 +198,20 @@ def test_trapezoid_rule_matches_oracle(pkg, mixed):
     check_against(r, ref, p.emax)
 
 
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_zolotarev_rule_matches_oracle(pkg, mixed):
+    """fpm(16) = 2: 1D Laplacian n = 1000, the 5 eigenvalues of
+    [-5e-4, (lambda_5 + lambda_6)/2] (none in the edge bands), against the
+    oracle with the same rule."""
+    lam = 2 - 2 * np.cos(np.arange(1, 40) * np.pi / 1001)
+    emin, emax = -5e-4, 0.5 * (lam[4] + lam[5])
+    p = fw.tridiag_1d(n=1000, emin=emin, emax=emax, m0=10, ratio=30)
+    ref = O.feast_scsr(p.A, None, emin, emax, 10, Y0=p.y0(), ne=8, ratio=30, tol_exp=11, rule=2)
+    assert ref["info"] == 0 and ref["M"] == 5
+    r = run_gpu(pkg, p, mixed, inner=(6, 3000), rule=2)
+    check_against(r, ref, emax)
+
+
 @pytest.mark.parametrize("kind", ["tall_ellipse", "trapezoid"])
 def test_custom_nodes_match_oracle(pkg, kind):
     """Expert entry points (custom half-contour nodes): nodes of a taller

@@ -510,3 +510,69 @@ def test_hermitian_feast_reduces_to_real_symmetric():
                          tol_exp=12, rule=rule)
         assert r["info"] == h["info"] == 0 and r["M"] == h["M"]
         assert np.abs(r["E"][: r["M"]] - h["E"][: h["M"]]).max() < 1e-12
+
+
+# ------------------------------------------------------------------ Zolotarev rule (fpm(16)=2)
+@pytest.mark.parametrize("m", [0.1, 0.5, 0.9, 0.999, 1 - 1e-8])
+def test_elliptic_functions_match_scipy(m):
+    import scipy.special as sps
+
+    assert abs(O.ellipk(m) - sps.ellipk(m)) < 1e-13 * sps.ellipk(m)
+    K = sps.ellipk(m)
+    for u in (0.0, 0.3, 0.5 * K, 0.9 * K, K):
+        sn, cn = O.ellipj(u, m)
+        ref = sps.ellipj(u, m)
+        assert abs(sn - ref[0]) < 1e-12 and abs(cn - ref[1]) < 1e-12
+
+
+def _refined_extrema(f, xs):
+    """Local extrema of the sampled function f on the sorted grid xs, each
+    refined by a bounded scalar search between its grid neighbours."""
+    import scipy.optimize
+
+    v = f(xs)
+    d = np.diff(np.sign(np.diff(v)))
+    out = []
+    for i in np.nonzero(d)[0] + 1:
+        sgn = -1.0 if d[i - 1] < 0 else 1.0  # -1: maximum, +1: minimum
+        r = scipy.optimize.minimize_scalar(lambda t: sgn * f(np.array([t]))[0], bounds=(xs[i - 1], xs[i + 1]),
+                                           method="bounded", options={"xatol": 1e-14 * max(1.0, abs(xs[i]))})
+        out.append(f(np.array([r.x]))[0])
+    return np.array(out)
+
+
+@pytest.mark.parametrize("ne", [2, 4, 8])
+def test_zolotarev_filter_is_equiripple(ne):
+    """Zolotarev's filter is the best uniform approximation of the interval's
+    indicator outside the edge bands (|x| <= 1/(1+eta) inside, |x| >= 1+eta
+    outside, x = (lambda - c)/r, eta = 0.05): its error equioscillates with
+    equal extrema, and the two ripples sit exactly 1 apart."""
+    eta, emin, emax = 0.05, -1.0, 3.0
+    c, r = 1.0, 2.0
+    z, w = O.contour_zolotarev(ne, emin, emax, eta)
+    assert np.allclose(np.abs((z - c) / r), 1.0, atol=1e-13) and np.all(z.imag > 0)
+    f = lambda x: np.array([np.sum((w / (z - (c + r * t))).real) for t in x])
+    xin = np.linspace(-1 / (1 + eta), 1 / (1 + eta), 4001)
+    ein = np.concatenate([_refined_extrema(f, xin), f(xin[[0, -1]])])
+    eout = np.concatenate([_refined_extrema(f, np.geomspace(1 + eta, 1e9, 4001)),
+                           _refined_extrema(f, -np.geomspace(1e9, 1 + eta, 4001)), f(np.array([1 + eta, -1 - eta]))])
+    ripple = ein.max() - ein.min()
+    assert len(ein) >= ne + 2 and ripple > 0
+    assert abs((eout.max() - eout.min()) - ripple) < 1e-9 * ripple
+    assert abs((ein.max() + ein.min()) / 2 - (eout.max() + eout.min()) / 2 - 1.0) < 1e-12
+    # every extremum sits on one of the two levels of its region
+    for e in (ein, eout):
+        assert np.all(np.minimum(np.abs(e - e.max()), np.abs(e - e.min())) < 1e-9 * ripple)
+
+
+def test_feast_with_zolotarev_rule_matches_closed_form():
+    """1D Laplacian n = 1000, the 5 eigenvalues of [-5e-4, (lambda_5 + lambda_6)/2]
+    (closed form; none in the edge bands), Zolotarev nodes (fpm(16)=2)."""
+    lam = 2 - 2 * np.cos(np.arange(1, 40) * np.pi / 1001)
+    emin, emax = -5e-4, 0.5 * (lam[4] + lam[5])
+    x = (lam - 0.5 * (emin + emax)) / (0.5 * (emax - emin))
+    assert np.all((np.abs(x) < 1 / 1.05) | (np.abs(x) > 1.05))
+    p = fw.tridiag_1d(n=1000, emin=emin, emax=emax, m0=10, ratio=30)
+    ref = O.feast_scsr(p.A, None, emin, emax, 10, Y0=p.y0(), ne=8, ratio=30, tol_exp=11, rule=2)
+    assert ref["info"] == 0 and ref["M"] == 5
+    assert np.abs(ref["E"][:5] - lam[:5]).max() < 1e-15
