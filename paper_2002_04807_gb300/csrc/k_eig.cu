@@ -241,11 +241,11 @@ size_t jacobi_work_bytes(int m)
 
 static int coop_grid(int m)
 {
-    static int per_sm = 0;
-    if (!per_sm) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_coop, kEigThreads, rot_smem(2 * kMaxHalf));
-        if (per_sm < 1) per_sm = 1;
-    }
+    static const int per_sm = [] {  // initialised once, thread-safe
+        int v = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, jacobi_coop, kEigThreads, rot_smem(2 * kMaxHalf));
+        return v > 0 ? v : 1;
+    }();
     const int mp = m + (m & 1);
     const long long work = (long long)m * (mp / 2) > (long long)(mp / 2) * (mp / 2) ? (long long)m * (mp / 2)
                                                                                     : (long long)(mp / 2) * (mp / 2);

@@ -22,15 +22,16 @@ static std::atomic<long long> g_launches{0};
 long long launch_count() { return g_launches.load(); }
 void count_launches(int k) { g_launches += k; }
 
+// SM count of the device current at the first call (initialised once,
+// thread-safe; every GPU of a process is assumed to be the same part).
 int num_sms()
 {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
+    static const int n = [] {
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;
+    }();
     return n;
 }
 
