@@ -576,3 +576,30 @@ def test_feast_with_zolotarev_rule_matches_closed_form():
     ref = O.feast_scsr(p.A, None, emin, emax, 10, Y0=p.y0(), ne=8, ratio=30, tol_exp=11, rule=2)
     assert ref["info"] == 0 and ref["M"] == 5
     assert np.abs(ref["E"][:5] - lam[:5]).max() < 1e-15
+
+
+# ------------------------------------------------------------------ filter block against the spectral formula
+@pytest.mark.parametrize("solver", ["direct", "cocg"])
+@pytest.mark.parametrize("gen", [False, True])
+def test_filter_block_matches_dense_spectral_formula(gen, solver):
+    """Classic form: Q = rho(B^{-1}A) Y = X diag(rho(lambda)) X^T B Y; the
+    residual-inverse form applied to Ritz pairs of a random subspace gives the
+    same rho(B^{-1}A) applied to that subspace's Ritz vectors."""
+    rng = np.random.default_rng(51)
+    A = fw.laplacian_2d(10, rng.uniform(0, 1, (10, 10)))
+    B = fw.diagonal_csr(rng.uniform(1, 2, A.n)) if gen else None
+    db = np.eye(A.n) if B is None else B.to_dense()
+    lam, X = scipy.linalg.eigh(A.to_dense(), db)
+    emin, emax = 0.0, 0.5 * (lam[11] + lam[12])
+    r = _rho_dense(8, emin, emax, 0.3, lam)
+    P = X @ (r[:, None] * (X.T @ db))  # rho(B^{-1} A)
+    Y = rng.standard_normal((A.n, 7))
+    tol = 1e-12 if solver == "direct" else 1e-10
+    Q = O.filter_block(A, B, 8, emin, emax, 0.3, Y, solver=solver)
+    assert np.abs(Q - P @ Y).max() < tol * np.abs(P @ Y).max()
+    # Ritz pairs of a random 7-dimensional subspace (not eigenpairs)
+    Z = np.linalg.qr(rng.standard_normal((A.n, 7)))[0]
+    lr, W = scipy.linalg.eigh(Z.T @ A.to_dense() @ Z, Z.T @ db @ Z)
+    XR = Z @ W
+    Qr = O.filter_block(A, B, 8, emin, emax, 0.3, XR, lam=lr, rii=True, solver=solver)
+    assert np.abs(Qr - P @ XR).max() < 10 * tol * np.abs(P @ XR).max()
