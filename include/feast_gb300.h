@@ -252,6 +252,34 @@ int feast_scsr_solve_dev(int n, int nnz_a, const int* d_ia, const int* d_ja, con
                          double* epsout, int* loop, int* info, void* d_work, size_t work_bytes,
                          void* stream);
 
+/* Complex Hermitian problems A x = lambda B x (the guide's zfeast_hcsr{ev,gv},
+ * Sec. 3.2 "FEAST Hermitian"; algorithm of Sec. 1.1).  A Hermitian, B
+ * Hermitian positive definite or absent (B = I).  Arguments as
+ * feast_scsr_solve, except that a and b hold nnz complex values as
+ * interleaved (real, imaginary) doubles, 'L' / 'U' storage mirrors an entry
+ * a_ij as conj(a_ij), and x is column-major n x m0 complex (interleaved,
+ * 2 n m0 doubles).  The eigenvalues are real.  Both halves of the contour are
+ * solved: BiCG on z_e B - A with the conjugate-shift shadow system, so every
+ * node gives G(z_e) and G(conj z_e) in one run; Rayleigh-Ritz in complex FP64.
+ * fpm as for the real driver (fpm(2), (3), (4), (5), (6), (16) rules 0-2,
+ * (18), (42), (45), (46), (50) node batch <= 32, (52) seed), except that
+ * fpm(14) and fpm(40) must be 0 (info 114, 140); m0 <= 1024 (else 201).
+ * Device memory is allocated per call.  Returns info. */
+int feast_hcsr_solve(char uplo, int n, const double* a, const int* ia, const int* ja, const double* b,
+                     const int* ib, const int* jb, int* fpm, double emin, double emax, int* m0, double* e,
+                     double* x, int* m, double* res, double* epsout, int* loop, int* info);
+
+/* feast_hcsr_solve with the matrices and X on the device: d_ia/d_ja 0-based
+ * full-storage CSR, d_a / d_b nnz complex doubles (interleaved), d_ib NULL for
+ * B = I, d_x column-major n x m0 complex (in/out).  e, res and the scalars
+ * are host memory.  Work is enqueued on stream (NULL: the default stream) and
+ * the call returns once the results are written.  The CSR is not
+ * re-validated. */
+int feast_hcsr_solve_dev(int n, int nnz_a, const int* d_ia, const int* d_ja, const double* d_a, int nnz_b,
+                         const int* d_ib, const int* d_jb, const double* d_b, int* fpm, double emin,
+                         double emax, int* m0, double* e, double* d_x, int* m, double* res, double* epsout,
+                         int* loop, int* info, void* stream);
+
 /* feast_scsr_solve_dev with custom nodes zne, wne (host, as for
  * feast_scsr_solve_x); -124 for missing or invalid nodes. */
 int feast_scsr_solve_dev_x(int n, int nnz_a, const int* d_ia, const int* d_ja, const double* d_a, int nnz_b,

@@ -1,4 +1,5 @@
-"""GB300-native FEAST contour-filter eigensolver (real symmetric sparse problems).
+"""GB300-native FEAST contour-filter eigensolver (real symmetric and complex Hermitian
+sparse problems).
 
 Thin Python binding over the C ABI of ``libfeast_gb300.so`` (declared in
 ``include/feast_gb300.h``).  Every step of the method runs in the library's
@@ -20,6 +21,8 @@ from ._lib import (  # noqa: F401
     feast_gemm_dev,
     feast_gram_dev,
     feast_gram_noalloc_dev,
+    feast_hcsr_solve,
+    feast_hcsr_solve_dev,
     feast_init,
     feast_last_error,
     feast_last_profile,

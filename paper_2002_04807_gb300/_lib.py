@@ -48,6 +48,10 @@ _SIGS = {
                                 _p]),
     "feast_scsr_extreme_dev": (_i, [_i, _i, _p, _p, _p, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p,
                                     _p, _p, _p, C.c_size_t, _p]),
+    "feast_hcsr_solve": (_i, [C.c_char, _i, _p, _p, _p, _p, _p, _p, _p, _d, _d, _p, _p, _p, _p, _p, _p, _p,
+                              _p]),
+    "feast_hcsr_solve_dev": (_i, [_i, _i, _p, _p, _p, _i, _p, _p, _p, _p, _d, _d, _p, _p, _p, _p, _p, _p, _p,
+                                  _p, _p]),
 }
 
 
@@ -498,3 +502,72 @@ def feast_residual_dev(n, ia, ja, a, ib, jb, b, m, X, lam, alpha, R, res, stream
 def feast_eig_grad_dev(n, ia, ja, m, X, w, grad, stream=None):
     _check(library().feast_eig_grad_dev(n, _ptr(ia), _ptr(ja), m, _ptr(X), _ptr(w), _ptr(grad), _stream(stream)),
            "feast_eig_grad_dev")
+
+
+def _cvals(v):
+    """complex values -> contiguous interleaved (real, imaginary) float64"""
+    v = np.ascontiguousarray(v, dtype=np.complex128)
+    return v.view(np.float64)
+
+
+def feast_hcsr_solve(uplo: str, n: int, a, ia, ja, b=None, ib=None, jb=None, fpm=None, emin=0.0, emax=1.0,
+                     m0: int = 1, x0=None) -> FeastResult:
+    """Host driver for complex Hermitian CSR problems: a (and b) complex
+    values, CSR base ia[0] in {0,1}; x0 (n x m0 complex) is the start subspace
+    when fpm(5)=1.  The result's X is complex n x k."""
+    f = _fpm(fpm)
+    av = _cvals(a)
+    ia = np.ascontiguousarray(ia, dtype=np.int32)
+    ja = np.ascontiguousarray(ja, dtype=np.int32)
+    bv = None
+    if b is not None:
+        bv = _cvals(b)
+        ib = np.ascontiguousarray(ib, dtype=np.int32)
+        jb = np.ascontiguousarray(jb, dtype=np.int32)
+    x = np.zeros((n, m0), dtype=np.complex128, order="F")
+    if x0 is not None:
+        if np.shape(x0) != (n, m0):
+            raise FeastError("x0 must have shape (n, m0)")
+        x[:] = x0
+    E = np.zeros(m0)
+    res = np.zeros(m0)
+    M, loop, info, mm = _i(0), _i(0), _i(0), _i(m0)
+    eps = _d(0)
+    library().feast_hcsr_solve(uplo.encode(), n, _ptr(av), _ptr(ia), _ptr(ja), _ptr(bv), _ptr(ib), _ptr(jb),
+                               _ptr(f), emin, emax, C.byref(mm), _ptr(E), _ptr(x), C.byref(M), _ptr(res),
+                               C.byref(eps), C.byref(loop), C.byref(info))
+    k = mm.value
+    if info.value == -4:
+        raise FeastError("feast_hcsr_solve: " + feast_last_error())
+    return FeastResult(info.value, E[:k].copy(), np.asfortranarray(x[:, :k]), res[:k].copy(), M.value,
+                       loop.value, eps.value, k, f)
+
+
+def feast_hcsr_solve_dev(n: int, ia, ja, a, ib=None, jb=None, b=None, fpm=None, emin=0.0, emax=1.0, m0: int = 1,
+                         x=None, stream=None) -> FeastResult:
+    """Device driver for complex Hermitian CSR problems: 0-based CSR as torch
+    CUDA tensors (int32 indices, complex128 values); x a CUDA complex128
+    tensor holding the column-major n x m0 block (shape (m0, n) row-major is
+    the same memory), in/out."""
+    import torch
+
+    f = _fpm(fpm)
+    ia, ja, a = _dev(ia, torch.int32), _dev(ja, torch.int32), _dev(a, torch.complex128)
+    nnzb = 0
+    if b is not None:
+        ib, jb, b = _dev(ib, torch.int32), _dev(jb, torch.int32), _dev(b, torch.complex128)
+        nnzb = b.numel()
+    if x is None:
+        x = torch.zeros((m0, n), dtype=torch.complex128, device=a.device)
+    x = _dev(x, torch.complex128)
+    E = np.zeros(m0)
+    res = np.zeros(m0)
+    M, loop, info, mm = _i(0), _i(0), _i(0), _i(m0)
+    eps = _d(0)
+    library().feast_hcsr_solve_dev(n, a.numel(), _ptr(ia), _ptr(ja), _ptr(a), nnzb, _ptr(ib), _ptr(jb), _ptr(b),
+                                   _ptr(f), emin, emax, C.byref(mm), _ptr(E), _ptr(x), C.byref(M), _ptr(res),
+                                   C.byref(eps), C.byref(loop), C.byref(info), _stream(stream))
+    if info.value == -4:
+        raise FeastError("feast_hcsr_solve_dev: " + feast_last_error())
+    k = mm.value
+    return FeastResult(info.value, E[:k].copy(), x, res[:k].copy(), M.value, loop.value, eps.value, k, f)

@@ -2380,3 +2380,15 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
     (void)k;
     return 0;
 }
+
+// ---------------------------------------------------------------- helpers for the Hermitian driver
+namespace feast {
+int fpm_check(const int* fpm) { return check_fpm(fpm); }
+void contour_nodes(int rule, int ne, double emin, double emax, double ratio, std::vector<double>& zw)
+{
+    contour(rule, ne, emin, emax, ratio, zw);
+}
+int cuda_error(cudaError_t e, const char* where) { return cuda_fail(e, where); }
+void clear_last_error() { g_err.clear(); }
+void feast_log(int lvl, const char* text) { log_line(lvl, text); }
+}  // namespace feast

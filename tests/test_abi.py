@@ -254,3 +254,49 @@ def test_host_block_argument_checks(pkg):
         pkg.feast_scsr_solve(**base, x_out=np.zeros((20, 6), dtype=np.float32, order="F"))
     with pytest.raises(FeastError):
         pkg.feast_scsr_solve(**base, x0=np.zeros((19, 6)))
+
+
+def test_hermitian_argument_errors_are_host_side(pkg):
+    """feast_hcsr_solve validates its arguments before any device work (guide
+    info table; fpm(14), fpm(40) and m0 > 1024 are outside the Hermitian driver)."""
+    A = fw.flux_ring(20, 0.1)
+    ok = dict(uplo="F", n=20, a=A.data, ia=A.indptr, ja=A.indices, emin=0.0, emax=0.5, m0=6)
+
+    def run(**kw):
+        args = dict(ok)
+        args.update(kw)
+        return pkg.feast_hcsr_solve(**args).info
+
+    assert run(uplo="X") == -101
+    assert run(n=0) == 202
+    assert run(emin=1.0, emax=0.5) == 200
+    assert run(m0=0) == 201 and run(m0=21) == 201
+    for slot, val, code in ((1, 21, 102), (15, 3, 116), (13, 1, 114), (39, 1, 140), (49, 33, 150)):
+        f = pkg.feast_init()
+        f[slot] = val
+        assert run(fpm=f) == code
+    bad = A.indices.copy()
+    bad[3] = 99
+    assert run(ja=bad) == -105
+    nan = A.data.copy()
+    nan[0] = complex(np.nan, 0.0)
+    assert run(a=nan) == -103
+    bad_ia = A.indptr.copy()
+    bad_ia[5] = bad_ia[4] - 1
+    assert run(ia=bad_ia) == -104
+    assert run(uplo="L") == -105  # lower storage with an upper entry
+    big = fw.flux_ring(1100, 0.1)
+    assert pkg.feast_hcsr_solve("F", 1100, big.data, big.indptr, big.indices, emin=0.0, emax=0.5,
+                                m0=1025).info == 201
+
+
+def test_hermitian_no_cpu_fallback_without_gpu(pkg):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    A = fw.flux_ring(20, 0.1)
+    from paper_2002_04807_gb300 import FeastError
+
+    with pytest.raises(FeastError):
+        pkg.feast_hcsr_solve("F", 20, A.data, A.indptr, A.indices, emin=0.0, emax=0.5, m0=6)
