@@ -758,7 +758,8 @@ static int filter_classic(const ocsr* A, const ocsr* B, int ne, const double* z,
 /* Residual-inverse-iteration form of the same filter on the Ritz block X with
  * Ritz values lam:  for every column, (zB-A)^{-1} B x = [x + (zB-A)^{-1}(Ax - lam Bx)]/(z - lam),
  * so Q = X diag(rho(lam)) + sum_e Re(w_e/(z_e - lam_j) Y_e), (z_e B - A) Y_e = A X - B X Lam.
- * Parity unpinned by itself: it is checked against filter_classic by tests. */
+ * Pinned by tests against the dense spectral formula X diag(rho) X^T B applied to
+ * the Ritz pairs of a random subspace (not eigenpairs), and against filter_classic. */
 static int filter_rii(const ocsr* A, const ocsr* B, int ne, const double* z, const double* w,
                       int m, const double* X, const double* lam, double* Q, int solver,
                       double solve_tol, long* iters)
