@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--side", type=int, default=None, help="grid side (default 64; 96 for --workload stencil27)")
-    ap.add_argument("--workload", default="laplace3d", choices=["laplace3d", "stencil27", "batched", "grad48"],
+    ap.add_argument("--workload", default="laplace3d", choices=["laplace3d", "stencil27", "batched", "grad48", "hermitian"],
                     help="laplace3d: 7-point 3D Laplacian + potential, B = I (the headline line); stencil27: "
                          "27-point generalized problem, B diagonal, lowest 200 eigenvalues, M0 = 300, Ne = 16; "
                          "batched: 512 2D problems in one batched solve; grad48: eigenvalue-loss forward and "
@@ -677,6 +677,69 @@ def run_grad(args):
         print(json.dumps(out))
 
 
+# ---------------------------------------------------------------- complex Hermitian workload
+def run_hermitian(args):
+    """The complex Hermitian driver on the bench's 64^3 Laplacian + potential
+    with random gauge phases on every site (same ~100 lowest eigenvalues and
+    interval as the real workload, every off-diagonal entry complex), M0 = 150,
+    Ne = 8: both contour halves by BiCG, complex FP64 Rayleigh-Ritz.  Device
+    entry point, CUDA events around each solve."""
+    import torch
+
+    import feast_workloads as fw
+
+    pkg, rank, ws = _lib_setup()
+    p = fw.laplace3d_gauge(side=args.side)
+    dev = torch.device("cuda")
+    ia = torch.as_tensor(p.A.indptr).to(dev, torch.int32)
+    ja = torch.as_tensor(p.A.indices).to(dev, torch.int32)
+    av = torch.as_tensor(p.A.data).to(dev, torch.complex128)
+    x0 = torch.as_tensor(np.ascontiguousarray(p.y0().T)).to(dev)
+
+    def fpm(mixed):
+        f = pkg.feast_init()
+        f[1], f[2], f[3], f[4], f[5], f[17], f[41], f[44], f[45], f[49] = p.ne, 10, 40, 1, 1, p.ratio, mixed, 2, 80, 8
+        return f
+
+    def solve(mixed):
+        x = x0.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        r = pkg.feast_hcsr_solve_dev(p.n, ia, ja, av, fpm=fpm(mixed), emin=p.emin, emax=p.emax, m0=p.m0, x=x)
+        e1.record()
+        torch.cuda.synchronize()
+        if r.info != 0:
+            raise RuntimeError(f"Hermitian FEAST info {r.info}")
+        return e0.elapsed_time(e1), int(np.sum(r.res[: r.M] <= RES_TOL)), r
+
+    for _ in range(args.warmup):
+        solve(1)
+    ms, conv = 0.0, 0
+    for _ in range(args.steps):
+        t, c, r = solve(1)
+        ms += t
+        conv += c
+    value = conv / (ms / 1e3)
+    fp64 = None
+    if args.fp64_steps > 0:
+        t64, c64, _ = solve(0)
+        fp64 = {"value": c64 / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64,
+                "mixed_over_fp64": value / (c64 / (t64 / 1e3))}
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "c32 BiCG solves + c64 Rayleigh-Ritz",
+               "data": "synthetic (seeded generator, no dataset)",
+               "config": {"workload": f"laplace3d_7pt_{args.side}^3_potential_U[0,0.5]_seed1_random_gauge_phases",
+                          "N": p.n, "nnz": p.A.nnz, "M0": p.m0, "Ne": p.ne, "contour_ratio_pct": p.ratio,
+                          "interval": [p.emin, round(p.emax, 6)], "node_batch": 8,
+                          "inner_solver": "BiCG with the conjugate-shift shadow system, 1e-2, 80 steps"},
+               "M": r.M, "converged_pairs": conv // args.steps, "max_residual": float(r.res[: r.M].max()),
+               "bicg_iterations": int(r.fpm[59]), "fp64": fp64}
+        print(json.dumps(out))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.side is None:
@@ -693,5 +756,7 @@ if __name__ == "__main__":
         run_batched(a)
     elif a.workload == "grad48":
         run_grad(a)
+    elif a.workload == "hermitian":
+        run_hermitian(a)
     else:
         run_gpu(a)

@@ -322,6 +322,30 @@ def stencil27_generalized(side: int = 96, count: int = 200, m0: int = 300, ne: i
                    m0, ne, ratio, seed, {"target_count": count})
 
 
+def gauge_phases(A: CSR, seed: int) -> ZCSR:
+    """The complex Hermitian D A D^H with D = diag(exp(i theta_j)), theta_j ~
+    U[0, 2 pi) (seeded): entry (j, k) gets the phase exp(i (theta_j - theta_k)),
+    so every off-diagonal entry is complex while the spectrum stays A's (the
+    eigenvectors are D x)."""
+    rng = np.random.default_rng([seed, 7])
+    theta = rng.uniform(0.0, 2.0 * np.pi, size=A.n)
+    rows = np.repeat(np.arange(A.n), np.diff(A.indptr))
+    data = A.data * np.exp(1j * (theta[rows] - theta[A.indices]))  # (k, j) is exactly the conjugate
+    return ZCSR(A.n, A.indptr.copy(), A.indices.copy(), data.astype(np.complex128))
+
+
+def laplace3d_gauge(side: int = 64, count: int = 100, m0: int = 150, ne: int = 8, ratio: int = 200,
+                    seed: int = 1) -> Problem:
+    """Complex Hermitian workload: the 7-point 3D Laplacian + V ~ U[0, 0.5] of
+    laplace3d_potential with random gauge phases on every site (gauge_phases);
+    same interval and same eigenvalues as the real problem.  y0() is complex."""
+    p = laplace3d_potential(side=side, count=count, m0=m0, ne=ne, ratio=ratio, seed=seed)
+    q = Problem(f"laplace3d_gauge_{side}^3", gauge_phases(p.A, seed), None, p.emin, p.emax, m0, ne, ratio, seed,
+                dict(p.notes, real_problem=p))
+    q.y0 = lambda: complex_gaussian_block(q.n, q.m0, q.y0_seed)  # type: ignore[method-assign]
+    return q
+
+
 def count_below(A: CSR, sigma: float) -> int:
     """Number of eigenvalues of the symmetric A below sigma, by Sylvester's law
     of inertia: negative pivots of a sparse symmetric LDL^T of A - sigma I

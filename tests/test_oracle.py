@@ -603,3 +603,18 @@ def test_filter_block_matches_dense_spectral_formula(gen, solver):
     XR = Z @ W
     Qr = O.filter_block(A, B, 8, emin, emax, 0.3, XR, lam=lr, rii=True, solver=solver)
     assert np.abs(Qr - P @ XR).max() < 10 * tol * np.abs(P @ XR).max()
+
+
+def test_hermitian_feast_gauge_workload_matches_real_problem():
+    """Random gauge phases D A D^H keep the spectrum of the real 3D workload and
+    map its eigenvectors to D x: the Hermitian oracle on the gauged matrix gives
+    the real oracle's eigenvalues."""
+    p = fw.laplace3d_gauge(side=6, count=10, m0=16, ratio=100, seed=12)
+    real = p.notes["real_problem"]
+    r = O.feast_scsr(real.A, None, p.emin, p.emax, 16, Y0=real.y0(), ne=8, ratio=100, tol_exp=12)
+    h = O.feast_hcsr(p.A, None, p.emin, p.emax, 16, Y0=p.y0(), ne=8, ratio=100, tol_exp=12)
+    assert r["info"] == h["info"] == 0 and r["M"] == h["M"] >= 5
+    M = r["M"]
+    assert np.abs(r["E"][:M] - h["E"][:M]).max() < 1e-12
+    d = p.A.to_dense()
+    assert np.abs(d - d.conj().T).max() == 0.0 and np.abs(d.imag).max() > 0.5
