@@ -175,3 +175,16 @@ def test_device_entry_point(pkg):
     db = B.to_dense()
     R = A.to_dense() @ X - db @ X * r.E[:15]
     assert np.abs(R).max() < 1e-9 * np.abs(lam).max()
+
+
+def test_gauge_workload_matches_real_spectrum(pkg):
+    """The bench's Hermitian workload at 12^3: random gauge phases keep the real
+    problem's spectrum, so the eigenvalues are checked against a dense real eigh."""
+    p = fw.laplace3d_gauge(side=12, count=20, m0=32, ratio=200)
+    lam = np.linalg.eigvalsh(p.notes["real_problem"].A.to_dense())
+    emax = 0.5 * (lam[19] + lam[20])
+    r = pkg.feast_hcsr_solve("F", p.n, p.A.data, p.A.indptr, p.A.indices, fpm=fpm_for(pkg, 1, ratio=200),
+                             emin=p.emin, emax=emax, m0=32, x0=p.y0())
+    assert r.info == 0 and r.M == 20
+    assert np.abs(r.E[:20] - lam[:20]).max() < EIG_TOL * np.abs(lam).max()
+    assert r.res[:20].max() < RES_TOL
