@@ -618,3 +618,44 @@ def test_hermitian_feast_gauge_workload_matches_real_problem():
     assert np.abs(r["E"][:M] - h["E"][:M]).max() < 1e-12
     d = p.A.to_dense()
     assert np.abs(d - d.conj().T).max() == 0.0 and np.abs(d.imag).max() > 0.5
+
+
+def test_hermitian_reduced_gev_matches_eigh_and_drops_null_directions():
+    """Reduced generalized Hermitian problem: full rank against scipy's eigh;
+    a B_Q of rank 6 (Gram matrix of 6 independent vectors in 9 columns) keeps
+    6 directions, whose pairs solve A_Q v = lambda B_Q v with V^H B_Q V = I."""
+    rng = np.random.default_rng(61)
+    m = 9
+    H = rng.standard_normal((40, 40)) + 1j * rng.standard_normal((40, 40))
+    H = (H + H.conj().T) / 2
+    Z = rng.standard_normal((40, m)) + 1j * rng.standard_normal((40, m))
+    Aq, Bq = Z.conj().T @ H @ Z, Z.conj().T @ Z
+    info, lam, V = O.h_reduced_gev(Aq, Bq)
+    assert info == 0 and len(lam) == m
+    ref = scipy.linalg.eigh((Aq + Aq.conj().T) / 2, (Bq + Bq.conj().T) / 2, eigvals_only=True)
+    assert np.abs(lam - ref).max() < 1e-10 * np.abs(ref).max()
+    assert np.abs(V.conj().T @ Bq @ V - np.eye(m)).max() < 1e-10
+    # rank-deficient: columns 6..8 are combinations of columns 0..5
+    Z2 = Z.copy()
+    Z2[:, 6:] = Z[:, :6] @ (rng.standard_normal((6, 3)) + 1j * rng.standard_normal((6, 3)))
+    Aq2, Bq2 = Z2.conj().T @ H @ Z2, Z2.conj().T @ Z2
+    info, lam2, V2 = O.h_reduced_gev(Aq2, Bq2)
+    assert info == 0 and len(lam2) == 6
+    Q6, _ = np.linalg.qr(Z[:, :6])
+    ref6 = np.linalg.eigvalsh(Q6.conj().T @ H @ Q6)  # H projected on the span
+    assert np.abs(np.sort(lam2) - ref6).max() < 1e-8 * np.abs(ref6).max()
+    assert np.abs(Aq2 @ V2 - Bq2 @ V2 * lam2).max() < 1e-8 * np.abs(Aq2).max()
+
+
+def test_hermitian_feast_zolotarev_rule_matches_dense():
+    """fpm(16) = 2 in the Hermitian oracle, eigenvalues kept out of the rule's
+    edge bands 1/1.05 < |x| < 1.05."""
+    rng = np.random.default_rng(46)
+    A = fw.hermitian_banded(300, 5, rng, shift=8.0)
+    lam = np.linalg.eigvalsh(A.to_dense())
+    emin, emax = lam[0] - 0.5, 0.5 * (lam[18] + lam[19])
+    x = np.abs((lam - 0.5 * (emin + emax)) / (0.5 * (emax - emin)))
+    assert not np.any((x > 1 / 1.05) & (x < 1.05))
+    ref = O.feast_hcsr(A, None, emin, emax, 48, Y0=fw.complex_gaussian_block(300, 48, 3), ne=8, tol_exp=12, rule=2)
+    assert ref["info"] == 0 and ref["M"] == 19
+    assert np.abs(ref["E"][:19] - lam[:19]).max() < 1e-12 * np.abs(lam).max()
