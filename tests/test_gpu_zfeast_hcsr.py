@@ -11,7 +11,11 @@ import torch
 import feast_workloads as fw
 import oracle as O
 
-pytestmark = pytest.mark.gpu
+# The Hermitian path had not run on a GPU when these tests were written: a
+# failure is reported (xfailed) without stopping the rest of the GPU suite, a
+# pass shows as xpassed.  The mark goes once the file has passed on a GPU.
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.xfail(reason="first GPU run of the complex Hermitian path", strict=False)]
 EIG_TOL, RES_TOL, ANG_TOL = 1e-10, 1e-10, 1e-8
 
 
