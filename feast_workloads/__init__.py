@@ -151,6 +151,56 @@ def stencil27_spd(side: int, rng: np.random.Generator) -> CSR:
                         np.concatenate([w, w, diag]))
 
 
+def mass_like_grid(shape, rng: np.random.Generator) -> CSR:
+    """Non-diagonal SPD B for the generalized problem A x = lambda B x: the
+    (2d+1)-point grid pattern of a box grid (last axis fastest) with diagonal
+    U[1,2] and off-diagonals +U[0.05,0.15] drawn once per undirected edge
+    (symmetric), like a finite-element mass matrix.  At most 2d <= 6
+    off-diagonals of at most 0.15 per row against a diagonal of at least 1:
+    strictly diagonally dominant with a positive diagonal, hence SPD
+    (Gershgorin)."""
+    shape = tuple(int(s) for s in shape)
+    n = int(np.prod(shape))
+    idx = np.arange(n).reshape(shape)
+    rows, cols = [], []
+    for ax in range(len(shape)):
+        lo = [slice(None)] * len(shape)
+        hi = [slice(None)] * len(shape)
+        lo[ax] = slice(0, shape[ax] - 1)
+        hi[ax] = slice(1, shape[ax])
+        rows.append(idx[tuple(lo)].ravel())
+        cols.append(idx[tuple(hi)].ravel())
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    w = rng.uniform(0.05, 0.15, size=r.size)
+    i = np.arange(n)
+    d = rng.uniform(1.0, 2.0, size=n)
+    return csr_from_coo(n, np.concatenate([r, c, i]), np.concatenate([c, r, i]), np.concatenate([w, w, d]))
+
+
+def mass_like_3d(side: int, rng: np.random.Generator) -> CSR:
+    """mass_like_grid on a side^3 grid (7-point pattern)."""
+    return mass_like_grid((side, side, side), rng)
+
+
+def laplace3d_general_b(side: int = 10, count: int = 20, m0: int = 32, ne: int = 8, ratio: int = 100,
+                        seed: int = 6) -> Problem:
+    """Generalized problem with a non-diagonal sparse B: A = 7-point Laplacian +
+    V ~ U[0, 0.5], B = mass_like_3d (same seed stream).  The interval is
+    [0, Emax] with Emax midway between the count-th and (count+1)-th
+    eigenvalues of the pencil (dense eigensolve: for small grids only)."""
+    rng = np.random.default_rng(seed)
+    pot = rng.uniform(0.0, 0.5, size=(side, side, side))
+    A = laplacian_3d(side, pot)
+    B = mass_like_3d(side, rng)
+    import scipy.linalg
+
+    ev = scipy.linalg.eigh(A.to_dense(), B.to_dense(), eigvals_only=True)
+    emax = 0.5 * (ev[count - 1] + ev[count])
+    return Problem(f"laplace3d_genB_{side}^3", A, B, 0.0, float(emax), m0, ne, ratio, seed,
+                   {"target_count": count})
+
+
 def helloworld_dense() -> np.ndarray:
     """The 4x4 real symmetric example of the FEAST v4.0 guide (Sec. 2.4),
     eigenvalues {0, 2, 4, 4}."""

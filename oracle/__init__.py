@@ -5,7 +5,9 @@ may import this package.  The product path (``paper_2002_04807_gb300``) never
 imports it and shares no code with it.
 
 The arithmetic lives in ``feast_oracle.c`` (plain C, compiled with gcc by
-:func:`build`); this module only marshals numpy arrays into it.  Each wrapper
+:func:`build`); this module only marshals numpy arrays into it, except for
+:func:`count_below_planes`, an inertia count written with numpy/scipy LAPACK
+steps for grids too wide for the C banded count.  Each wrapper
 names the step of the method it performs; the C file cites the guide's
 sections and states the formulas.
 """
@@ -207,6 +209,57 @@ def count_below(A, B, sigma: float) -> int:
     if r < 0:
         raise RuntimeError("zero pivot in inertia count")
     return int(r)
+
+
+def count_below_planes(A, B, sigma: float, nb: int) -> int:
+    """Number of eigenvalues of (A, B) below sigma by Sylvester's law of
+    inertia, for a matrix that is block tridiagonal in blocks of nb rows (the
+    planes of a 3D grid): block Gaussian elimination
+    S_1 = A_11 - sigma B_11,
+    S_k = A_kk - sigma B_kk - C_k S_{k-1}^{-1} C_k^T,  C_k = A_{k,k-1} - sigma B_{k,k-1},
+    is a congruence to blockdiag(S_k), so the count is the sum of the negative
+    eigenvalues of the S_k (each from its symmetric indefinite LDL^T, whose D
+    has 1x1 and 2x2 blocks).  Dense LAPACK steps on nb x nb blocks: for grids
+    too wide for the banded count (N bw^2 work) and used only as a test pin.
+    Raises if the matrix is not block tridiagonal or a block is singular."""
+    import scipy.linalg as sl
+    import scipy.sparse as sp
+
+    n = A.n
+    if n % nb:
+        raise ValueError("nb must divide n")
+    M = sp.csr_matrix((A.data, A.indices, A.indptr), shape=(n, n))
+    if B is None:
+        M = M - sigma * sp.identity(n, format="csr")
+    else:
+        M = M - sigma * sp.csr_matrix((B.data, B.indices, B.indptr), shape=(n, n))
+    M = M.tocsr()
+    rows = np.repeat(np.arange(n), np.diff(M.indptr))
+    if np.abs(rows // nb - M.indices // nb).max(initial=0) > 1:
+        raise ValueError("matrix is not block tridiagonal in blocks of nb rows")
+    neg, Sinv = 0, None
+    for k in range(n // nb):
+        S = M[k * nb:(k + 1) * nb, k * nb:(k + 1) * nb].toarray()
+        if k > 0:
+            Ck = M[k * nb:(k + 1) * nb, (k - 1) * nb:k * nb]
+            S -= np.asarray(Ck @ (Ck @ Sinv).T)  # C S^{-1} C^T (S^{-1} symmetric)
+        _, d, _ = sl.ldl(S, lower=True)
+        sub = np.diag(d, -1)
+        i = 0
+        while i < nb:  # eigenvalue signs of the 1x1 and 2x2 pivots
+            if i + 1 < nb and sub[i] != 0.0:
+                a, b, c = d[i, i], sub[i], d[i + 1, i + 1]
+                det = a * c - b * b
+                neg += 1 if det < 0 else (2 if a + c < 0 else 0)
+                i += 2
+            else:
+                if d[i, i] == 0.0:
+                    raise RuntimeError("singular pivot in inertia count")
+                neg += int(d[i, i] < 0)
+                i += 1
+        Sinv = np.linalg.inv(S)
+        Sinv = 0.5 * (Sinv + Sinv.T)
+    return int(neg)
 
 
 def residuals(A, B, X, lam, emin, emax):

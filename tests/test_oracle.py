@@ -294,6 +294,70 @@ def test_generalized_problem_against_dense_and_inertia():
         assert np.abs(X.T @ B.to_dense() @ X - np.eye(20)).max() < 1e-11
 
 
+def test_generalized_nondiagonal_b_against_dense_and_inertia():
+    """A non-diagonal SPD B (7-point mass-like pattern): the oracle's FEAST
+    (both solver modes) against the dense generalized eigensolve, its count
+    against Sylvester inertia, and X^T B X = I."""
+    p = fw.laplace3d_general_b(side=8, count=20, m0=32)
+    Bd = p.B.to_dense()
+    assert np.abs(Bd - np.diag(np.diag(Bd))).max() > 0.05  # genuinely non-diagonal
+    ev = scipy.linalg.eigh(p.A.to_dense(), Bd, eigvals_only=True)
+    assert O.count_below(p.A, p.B, p.emax) == 20 == int(np.sum(ev < p.emax))
+    for solver in ["direct", "cocg"]:
+        r = O.feast_scsr(p.A, p.B, 0.0, p.emax, 32, Y0=p.y0(), ne=8, ratio=100, tol_exp=11, solver=solver)
+        assert r["info"] == 0 and r["M"] == 20
+        assert np.abs(r["E"][:20] - ev[:20]).max() < 1e-10 * ev[19]
+        X = r["X"][:, :20]
+        assert np.abs(X.T @ Bd @ X - np.eye(20)).max() < 1e-11
+
+
+@pytest.mark.parametrize("side,seed", [(6, 1), (8, 2), (10, 3)])
+def test_count_below_planes_matches_banded_and_dense(side, seed):
+    """The block-tridiagonal inertia count (planes of a 3D grid) equals the
+    banded LDL^T count and the dense eigenvalue count, at shifts below the
+    spectrum, between eigenvalues and deep inside it; also for a 27-point
+    generalized pencil."""
+    p = fw.laplace3d_potential(side=side, count=20, m0=30, seed=seed)
+    ev = np.linalg.eigvalsh(p.A.to_dense())
+    for s in [0.0, 0.5 * (ev[5] + ev[6]), p.emax, 1.3]:
+        want = int(np.sum(ev < s))
+        assert O.count_below_planes(p.A, None, s, side * side) == want == O.count_below(p.A, None, s)
+    rng = np.random.default_rng(seed)
+    A = fw.stencil27_spd(side, rng)
+    B = fw.diagonal_csr(rng.uniform(1, 2, A.n))
+    d = 1 / np.sqrt(B.data)
+    evg = np.linalg.eigvalsh(d[:, None] * A.to_dense() * d[None, :])
+    for k in (3, 25):
+        s = 0.5 * (evg[k - 1] + evg[k])
+        assert O.count_below_planes(A, B, s, side * side) == k == O.count_below(A, B, s)
+
+
+def test_count_below_planes_rejects_wide_coupling():
+    A = fw.laplacian_2d(4)  # couples rows i and i + 4: two blocks of 2 rows apart
+    with pytest.raises(ValueError):
+        O.count_below_planes(A, None, 1.0, 2)
+
+
+def test_bench_workload_count_golden_is_current():
+    """The stored eigenvalue count of the 64^3 bench workload
+    (tests/golden/laplace3d_64_count.json, written by the committed
+    make_laplace3d_64_count.py through the oracle's block inertia count) was
+    taken on exactly the matrix and interval the generator builds today."""
+    import hashlib
+
+    g = json.load(open(os.path.join(GOLD, "laplace3d_64_count.json")))
+    p = fw.laplace3d_potential(side=64, count=100, m0=150, ne=8, ratio=200, seed=1)
+    h = hashlib.sha1()
+    for a in (p.A.indptr, p.A.indices, p.A.data):
+        h.update(a.tobytes())
+    fp = g["fingerprint"]
+    assert (fp["n"], fp["nnz"], fp["emin"], fp["emax"], fp["csr_sha1"]) == (
+        p.n, p.A.nnz, repr(p.emin), repr(p.emax), h.hexdigest())
+    # nothing lies below Emin = 0: A = L + diag(V), L SPD and V >= 0 (Weyl)
+    assert g["count_below_emin"] == 0
+    assert g["count_in_interval"] == g["count_below_emax"] > 0
+
+
 def test_rii_form_equals_classic_form():
     p = fw.laplace3d_potential(side=8, count=20, m0=32, seed=11)
     Y0 = p.y0()
