@@ -37,7 +37,10 @@
  *    Library options in reserved slots (0 = automatic):
  *      fpm(50) contour nodes solved at once (node batch); fpm(51) rows per
  *      inner-solver work item; fpm(52) seed of the random start block;
- *      fpm(53) 1 = record per-kernel timings (see feast_last_profile).
+ *      fpm(53) 1 = record per-kernel timings (see feast_last_profile);
+ *      fpm(54) arithmetic of the Rayleigh-Ritz projections: 0 (default) =
+ *      FP64-accurate sums of exact BF16 slice products on the tensor cores
+ *      (feast_gram_oz_dev), 1 = FP64 tensor cores (mma.sync m8n8k4 f64).
  *  - Return value = info (also stored in *info where that argument exists),
  *    codes of the guide's info table (Sec. 3.1): 0 success; warnings 1 (no
  *    eigenvalue in the interval), 2 (no convergence within fpm(4) loops),
@@ -264,7 +267,8 @@ int feast_scsr_solve_dev(int n, int nnz_a, const int* d_ia, const int* d_ja, con
  * fpm as for the real driver (fpm(2), (3), (4), (5), (6), (16) rules 0-2,
  * (18), (42), (45), (46), (50) node batch <= 32, (52) seed), except that
  * fpm(14) and fpm(40) must be 0 (info 114, 140); m0 <= 1024 (else 201).
- * Device memory is allocated per call.  Returns info. */
+ * Device memory (CSR copies, X and the workspace) is allocated per call.
+ * Returns info. */
 int feast_hcsr_solve(char uplo, int n, const double* a, const int* ia, const int* ja, const double* b,
                      const int* ib, const int* jb, int* fpm, double emin, double emax, int* m0, double* e,
                      double* x, int* m, double* res, double* epsout, int* loop, int* info);
@@ -272,13 +276,23 @@ int feast_hcsr_solve(char uplo, int n, const double* a, const int* ia, const int
 /* feast_hcsr_solve with the matrices and X on the device: d_ia/d_ja 0-based
  * full-storage CSR, d_a / d_b nnz complex doubles (interleaved), d_ib NULL for
  * B = I, d_x column-major n x m0 complex (in/out).  e, res and the scalars
- * are host memory.  Work is enqueued on stream (NULL: the default stream) and
- * the call returns once the results are written.  The CSR is not
- * re-validated. */
+ * are host memory.  d_work: a caller-owned device workspace of work_bytes >=
+ * feast_hcsr_workspace_bytes(...) bytes (256-byte aligned), from which every
+ * device buffer of the solve is carved, so the call allocates nothing; or
+ * NULL, and the library allocates the workspace for the call (cudaMalloc) and
+ * frees it before returning.  A workspace that is too small gives -120.  Work
+ * is enqueued on stream (NULL: the default stream) and the call returns once
+ * the results are written.  The CSR is not re-validated. */
 int feast_hcsr_solve_dev(int n, int nnz_a, const int* d_ia, const int* d_ja, const double* d_a, int nnz_b,
                          const int* d_ib, const int* d_jb, const double* d_b, int* fpm, double emin,
-                         double emax, int* m0, double* e, double* d_x, int* m, double* res, double* epsout,
-                         int* loop, int* info, void* stream);
+                         double emax, int* m0, double* e, double* d_x, int* m, double* res,
+                         double* epsout, int* loop, int* info, void* d_work, size_t work_bytes,
+                         void* stream);
+
+/* Device workspace, in bytes, that feast_hcsr_solve_dev needs for this
+ * problem size and these parameters (fpm(2), fpm(42), fpm(50)); 0 for
+ * invalid sizes. */
+size_t feast_hcsr_workspace_bytes(int n, int nnz_a, int nnz_b, int m0, const int* fpm);
 
 /* feast_scsr_solve_dev with custom nodes zne, wne (host, as for
  * feast_scsr_solve_x); -124 for missing or invalid nodes. */
@@ -364,8 +378,26 @@ int feast_gram_dev(int n, int m, const double* X, const double* Y, double* C, vo
  *   - Enqueues on stream and returns after C is written. */
 int feast_gram_noalloc_dev(int n, int m, const double* X, const double* Y, double* C, void* stream);
 
+/* The same contraction C = X^T Y (upper triangle mirrored) computed from
+ * exact products of BF16 integer slices on the tensor cores (Ozaki et al.'s
+ * error-free splitting: 8 slices of 7 bits per value under a power-of-two
+ * column scale; products accumulated exactly in FP32 for 256 rows at a time,
+ * then in FP64), the arithmetic of the solvers' projections A_Q = Q^T A Q,
+ * B_Q = Q^T B Q when fpm(54) = 0 (Sec. 1.1's reduced problem, FP64 accuracy:
+ * the truncation error of an element is below 2^-55 max|X[:,a]| max|Y[:,b]|
+ * per row).  Device row-major n x m X, Y; C m x m.  Returns 0, -101 n <= 0,
+ * -102 m <= 0, -4 on a CUDA error. */
+int feast_gram_oz_dev(int n, int m, const double* X, const double* Y, double* C, void* stream);
+
 /* C = A V: A device row-major n x m, V device row-major m x k, C n x k, FP64. */
 int feast_gemm_dev(int n, int m, int k, const double* A, const double* V, double* C, void* stream);
+
+/* C = A V as feast_gemm_dev, from exact BF16 slice products on the tensor
+ * cores under a power-of-two scale per row of A and per column of V (the
+ * arithmetic of the Ritz vectors X = Q V when fpm(54) = 0; FP64 accuracy:
+ * truncation below 2^-55 max|A[i,:]| max|V[:,c]| per term).  Same arguments
+ * and return codes as feast_gemm_dev. */
+int feast_gemm_oz_dev(int n, int m, int k, const double* A, const double* V, double* C, void* stream);
 
 /* Symmetric eigen-decomposition (cyclic Jacobi) of the device m x m matrix A
  * (row-major, destroyed): lam ascending, V row-major with eigenvectors in
@@ -393,6 +425,48 @@ int feast_residual_dev(int n, const int* ia, const int* ja, const double* a, con
  * (0-based), X row-major n x m, w [m], grad [nnz].  m <= 2048. */
 int feast_eig_grad_dev(int n, const int* ia, const int* ja, int m, const double* X, const double* w,
                        double* grad, void* stream);
+
+/* Time limit of the library's bounded device waits (a library setting; the
+ * guide has no counterpart).  The reduced eigensolver runs its Jacobi rounds
+ * in one cooperative launch whose CTAs meet at a grid barrier every round;
+ * a CTA that spins there for more than `cycles` SM clock cycles sets an error
+ * flag that makes every CTA of the launch return, and the call reports the
+ * failure (-3 from the solvers and the reduced-eigensolver entry points) with the
+ * context still usable.  Default 4e9 cycles (about two seconds at 2 GHz);
+ * cycles < 1 restores the default.  Applies to launches issued after the
+ * call, process-wide.  Returns the previous limit. */
+long long feast_set_wait_limit(long long cycles);
+
+/* Gradient of an eigenvalue loss over the stored entries of A and B, host
+ * buffers (the boundary's counterpart of the device feast_eig_grad_dev; the
+ * guide has no differentiation interface: this is first-order perturbation
+ * theory of a simple eigenpair, not a passage of the guide).  For
+ * L = sum_k g_k lambda_k and eigenpairs of A x = lambda B x with x^T B x = 1:
+ *   grad_a[p] = sum_k g_k x_k[i_p] x_k[j_p]
+ *   grad_b[p] = -sum_k g_k lambda_k x_k[i_p] x_k[j_p]
+ * per stored entry p = (i_p, j_p) of the patterns as passed.
+ *   uplo      'F': full storage, one derivative per stored entry (perturbing a
+ *             symmetric pair (i,j),(j,i) moves L by the sum of both);
+ *             'L'/'U': one triangle stored, as for feast_scsr_solve, so an
+ *             off-diagonal value stands for both entries and gets twice the
+ *             entry-wise derivative
+ *   n         order (>= 1)
+ *   ia, ja    A's CSR pattern, base ia[0] in {0,1} (values are not needed)
+ *   ib, jb    B's CSR pattern, or both NULL for B = I (grad_b unused)
+ *   m         eigenpairs in the loss, 0 <= m <= 2048
+ *   x         [n*m] column-major eigenvectors (B-orthonormal, as returned by
+ *             feast_scsr_solve in its first m columns)
+ *   e         [m] eigenvalues (needed only with B)
+ *   g         [m] loss weights
+ *   grad_a    [nnz(A)] out;  grad_b  [nnz(B)] out
+ * Every array is caller-owned host memory; the library copies to the device,
+ * runs the SDDMM kernel and copies the gradients back (synchronous).
+ * Eigenvalues in the loss must be simple.  Returns 0; 202 for n <= 0;
+ * -101 bad uplo; -(100+i) for a bad i-th argument (pattern out of range or
+ * outside the stored triangle, NULL array, m out of range); -4 on a CUDA error
+ * (message in feast_last_error). */
+int feast_scsr_grad(char uplo, int n, const int* ia, const int* ja, const int* ib, const int* jb, int m,
+                    const double* x, const double* e, const double* g, double* grad_a, double* grad_b);
 
 #ifdef __cplusplus
 }

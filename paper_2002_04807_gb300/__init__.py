@@ -19,10 +19,13 @@ from ._lib import (  # noqa: F401
     feast_filter_dev,
     feast_filter_layout,
     feast_gemm_dev,
+    feast_gemm_oz_dev,
     feast_gram_dev,
     feast_gram_noalloc_dev,
+    feast_gram_oz_dev,
     feast_hcsr_solve,
     feast_hcsr_solve_dev,
+    feast_hcsr_workspace_bytes,
     feast_init,
     feast_last_error,
     feast_last_profile,
@@ -35,7 +38,9 @@ from ._lib import (  # noqa: F401
     feast_scsr_solve_x,
     feast_scsr_extreme,
     feast_scsr_extreme_dev,
+    feast_scsr_grad,
     feast_scsr_workspace_bytes,
+    feast_set_wait_limit,
     feast_shifted_spmm_dev,
     feast_sym_eig_dev,
     library,

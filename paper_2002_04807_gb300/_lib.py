@@ -37,8 +37,12 @@ _SIGS = {
     "feast_reduced_eig_dev": (_i, [_i, _p, _p, _p, _p, _p, _p]),
     "feast_residual_dev": (_i, [_i, _p, _p, _p, _p, _p, _p, _i, _p, _p, _d, _p, _p, _p]),
     "feast_eig_grad_dev": (_i, [_i, _p, _p, _i, _p, _p, _p, _p]),
+    "feast_scsr_grad": (_i, [C.c_char, _i, _p, _p, _p, _p, _i, _p, _p, _p, _p, _p]),
+    "feast_set_wait_limit": (C.c_longlong, [C.c_longlong]),
     "feast_last_profile": (_i, [_p]),
     "feast_gram_noalloc_dev": (_i, [_i, _i, _p, _p, _p, _p]),
+    "feast_gram_oz_dev": (_i, [_i, _i, _p, _p, _p, _p]),
+    "feast_gemm_oz_dev": (_i, [_i, _i, _i, _p, _p, _p, _p]),
     "feast_scsr_solve_batched": (_i, [_i, _p, _p, _p]),
     "feast_scsr_solve_x": (_i, [C.c_char, _i, _p, _p, _p, _p, _p, _p, _p, _d, _d, _p, _p, _p, _p, _p, _p, _p,
                                 _p, _p, _p]),
@@ -51,7 +55,8 @@ _SIGS = {
     "feast_hcsr_solve": (_i, [C.c_char, _i, _p, _p, _p, _p, _p, _p, _p, _d, _d, _p, _p, _p, _p, _p, _p, _p,
                               _p]),
     "feast_hcsr_solve_dev": (_i, [_i, _i, _p, _p, _p, _i, _p, _p, _p, _p, _d, _d, _p, _p, _p, _p, _p, _p, _p,
-                                  _p, _p]),
+                                  _p, _p, C.c_size_t, _p]),
+    "feast_hcsr_workspace_bytes": (C.c_size_t, [_i, _i, _i, _i, _p]),
 }
 
 
@@ -468,6 +473,14 @@ def feast_gram_dev(n, m, X, Y, Cm, stream=None):
     _check(library().feast_gram_dev(n, m, _ptr(X), _ptr(Y), _ptr(Cm), _stream(stream)), "feast_gram_dev")
 
 
+def feast_gram_oz_dev(n, m, X, Y, Cm, stream=None):
+    _check(library().feast_gram_oz_dev(n, m, _ptr(X), _ptr(Y), _ptr(Cm), _stream(stream)), "feast_gram_oz_dev")
+
+
+def feast_gemm_oz_dev(n, m, k, A, V, Cm, stream=None):
+    _check(library().feast_gemm_oz_dev(n, m, k, _ptr(A), _ptr(V), _ptr(Cm), _stream(stream)), "feast_gemm_oz_dev")
+
+
 def feast_gram_noalloc_dev(n, m, X, Y, Cm, stream=None):
     """C = X^T Y like feast_gram_dev, with the library's fixed device scratch
     instead of any allocation (for callers that cannot allocate)."""
@@ -502,6 +515,36 @@ def feast_residual_dev(n, ia, ja, a, ib, jb, b, m, X, lam, alpha, R, res, stream
 def feast_eig_grad_dev(n, ia, ja, m, X, w, grad, stream=None):
     _check(library().feast_eig_grad_dev(n, _ptr(ia), _ptr(ja), m, _ptr(X), _ptr(w), _ptr(grad), _stream(stream)),
            "feast_eig_grad_dev")
+
+
+def feast_set_wait_limit(cycles: int) -> int:
+    """Spin limit (SM clock cycles) of the library's bounded device waits;
+    cycles < 1 restores the default.  Returns the previous limit."""
+    return int(library().feast_set_wait_limit(int(cycles)))
+
+
+def feast_scsr_grad(uplo: str, n: int, ia, ja, x, g, ib=None, jb=None, e=None):
+    """Gradient of L = sum_k g_k lambda_k over the stored entries of A's (and
+    B's) CSR pattern, host buffers: x is n x m (eigenvectors in columns,
+    B-orthonormal), g [m] the loss weights, e [m] the eigenvalues (with B).
+    Returns (grad_a, grad_b or None)."""
+    ia_ = np.ascontiguousarray(ia, dtype=np.int32)
+    ja_ = np.ascontiguousarray(ja, dtype=np.int32)
+    x_ = np.asfortranarray(x, dtype=np.float64)
+    m = x_.shape[1] if x_.ndim == 2 else 0
+    g_ = np.ascontiguousarray(g, dtype=np.float64)
+    hasB = ib is not None or jb is not None
+    ib_ = None if ib is None else np.ascontiguousarray(ib, dtype=np.int32)
+    jb_ = None if jb is None else np.ascontiguousarray(jb, dtype=np.int32)
+    e_ = None if e is None else np.ascontiguousarray(e, dtype=np.float64)
+    base = int(ia_[0]) if ia_.size else 0
+    ga = np.zeros(max(1, int(ia_[-1]) - base))
+    gb = np.zeros(max(1, int(ib_[-1]) - int(ib_[0]))) if hasB and ib_ is not None else None
+    code = library().feast_scsr_grad(uplo.encode()[:1], n, _ptr(ia_), _ptr(ja_), _ptr(ib_), _ptr(jb_), m, _ptr(x_),
+                                     _ptr(e_), _ptr(g_), _ptr(ga), _ptr(gb))
+    _check(code, "feast_scsr_grad")
+    nnz_a = int(ia_[-1]) - base
+    return ga[:nnz_a], (None if gb is None else gb[: int(ib_[-1]) - int(ib_[0])])
 
 
 def _cvals(v):
@@ -543,12 +586,17 @@ def feast_hcsr_solve(uplo: str, n: int, a, ia, ja, b=None, ib=None, jb=None, fpm
                        loop.value, eps.value, k, f)
 
 
+def feast_hcsr_workspace_bytes(n: int, nnz_a: int, nnz_b: int, m0: int, fpm) -> int:
+    return int(library().feast_hcsr_workspace_bytes(n, nnz_a, nnz_b, m0, _ptr(_fpm(fpm))))
+
+
 def feast_hcsr_solve_dev(n: int, ia, ja, a, ib=None, jb=None, b=None, fpm=None, emin=0.0, emax=1.0, m0: int = 1,
-                         x=None, stream=None) -> FeastResult:
+                         x=None, work=None, stream=None) -> FeastResult:
     """Device driver for complex Hermitian CSR problems: 0-based CSR as torch
     CUDA tensors (int32 indices, complex128 values); x a CUDA complex128
     tensor holding the column-major n x m0 block (shape (m0, n) row-major is
-    the same memory), in/out."""
+    the same memory), in/out.  work: optional CUDA uint8 tensor of at least
+    feast_hcsr_workspace_bytes(...) bytes (else the library allocates)."""
     import torch
 
     f = _fpm(fpm)
@@ -566,7 +614,8 @@ def feast_hcsr_solve_dev(n: int, ia, ja, a, ib=None, jb=None, b=None, fpm=None, 
     eps = _d(0)
     library().feast_hcsr_solve_dev(n, a.numel(), _ptr(ia), _ptr(ja), _ptr(a), nnzb, _ptr(ib), _ptr(jb), _ptr(b),
                                    _ptr(f), emin, emax, C.byref(mm), _ptr(E), _ptr(x), C.byref(M), _ptr(res),
-                                   C.byref(eps), C.byref(loop), C.byref(info), _stream(stream))
+                                   C.byref(eps), C.byref(loop), C.byref(info), _ptr(work),
+                                   0 if work is None else work.numel(), _stream(stream))
     if info.value == -4:
         raise FeastError("feast_hcsr_solve_dev: " + feast_last_error())
     k = mm.value

@@ -87,6 +87,7 @@ static int check_fpm(const int* fpm)
     if (fpm[45] < 1) return 146;
     if (fpm[49] < 0) return 150;
     if (fpm[50] < 0) return 151;
+    if (fpm[53] != 0 && fpm[53] != 1) return 154;
     return 0;
 }
 
@@ -326,6 +327,7 @@ struct Plan {
     bool fp64 = false, hasB = false;
     int nnzA = 0, nnzB = 0;
     int ksplit = 1;
+    bool oz = true;  // projections from exact BF16 slice products (fpm(54) = 0) or FP64 DMMA (1)
     int nslot = 1;  // partial-sum slots per group (item slots + bucket slots)
     int nbk = 1;    // bucket counters per group
     size_t gpart = 0, rpart = 0;
@@ -353,6 +355,8 @@ struct Bufs {
     double *gpart = nullptr, *rpart = nullptr;
     int* mk = nullptr;
     int* perm = nullptr;
+    int* ozex = nullptr;  // column exponents of the sliced projections
+    void* ozw = nullptr;  // exponents and slices of the sliced Ritz-vector product
     void* eig = nullptr;
 };
 
@@ -386,7 +390,9 @@ Plan make_plan(int n, int nnzA, int nnzB, int m0, const int* fpm, bool filter_on
     P.nslot = std::max(part_slots(P.nrb), part_slots(P.nrb_b));
     P.nbk = std::max(part_buckets(P.nrb), part_buckets(P.nrb_b));
     if (!filter_only) {
-        P.gpart = gram_partial_doubles(n, m0, &P.ksplit, num_sms());
+        P.oz = fpm[53] == 0;
+        P.gpart = P.oz ? gram_oz_partial_doubles(n, m0, nullptr, nullptr, num_sms())
+                       : gram_partial_doubles(n, m0, &P.ksplit, num_sms());
         P.rpart = residual_partial_doubles(n, m0);
     }
     return P;
@@ -449,6 +455,8 @@ size_t carve(const Plan& P, void* base, Bufs& B, bool filter_only = false)
     B.rpart = c.take<double>(P.rpart);
     B.mk = c.take<int>(1);
     B.perm = c.take<int>(P.m0);
+    B.ozex = (int*)c.take<char>(gram_oz_work_bytes(P.m0));
+    B.ozw = c.take<char>(P.oz ? gemm_oz_work_bytes(P.n, P.m0, P.m0) : 0);
     B.eig = c.take<char>(reduced_work_bytes(P.m0));
     return c.off + 256;
 }
@@ -902,12 +910,16 @@ int run_feast(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, int* fpm, dou
         // Rayleigh-Ritz on Q
         if (g_prof.on) ph0 = g_prof.mark(s);
         CK(launch_spmm_f64(n, m0, A.ia, A.ja, A.v, B.Q, B.T, s));
-        CK(launch_gram_f64(n, m0, B.Q, B.T, B.Aq, B.gpart, P.ksplit, 1, s));
+        auto gram = [&](const double* Xg, const double* Yg, double* Cg) {
+            return P.oz ? launch_gram_oz(n, m0, Xg, Yg, Cg, B.gpart, B.ozex, s)
+                        : launch_gram_f64(n, m0, Xg, Yg, Cg, B.gpart, P.ksplit, 1, s);
+        };
+        CK(gram(B.Q, B.T, B.Aq));
         if (P.hasB) {
             CK(launch_spmm_f64(n, m0, Bm.ia, Bm.ja, Bm.v, B.Q, B.T2, s));
-            CK(launch_gram_f64(n, m0, B.Q, B.T2, B.Bq, B.gpart, P.ksplit, 1, s));
+            CK(gram(B.Q, B.T2, B.Bq));
         } else {
-            CK(launch_gram_f64(n, m0, B.Q, B.Q, B.Bq, B.gpart, P.ksplit, 1, s));
+            CK(gram(B.Q, B.Q, B.Bq));
         }
         for (int b = 0; b < P.nbatch; ++b) total_iters += itmax[b];
         size_t ph1 = 0, ph2 = 0;
@@ -916,7 +928,8 @@ int run_feast(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, int* fpm, dou
         if (rst == -4) return cuda_fail(cudaGetLastError(), "reduced eigensolver");
         if (rst) { info = -3; break; }
         if (g_prof.on) ph2 = g_prof.mark(s);
-        CK(launch_gemm_nn_f64(n, m0, m0, B.Q, B.Vr, B.X, s));
+        if (P.oz) CK(launch_gemm_oz(n, m0, m0, B.Q, B.Vr, B.X, B.ozw, s));
+        else CK(launch_gemm_nn_f64(n, m0, m0, B.Q, B.Vr, B.X, s));
         CK(launch_residual_f64(n, m0, A.ia, A.ja, A.v, P.hasB ? Bm.ia : nullptr, P.hasB ? Bm.ja : nullptr,
                                P.hasB ? Bm.v : nullptr, B.X, B.lam, B.Y, B.rpart, nullptr, B.res, alpha, s));
         if (g_prof.on) {
@@ -1664,6 +1677,36 @@ extern "C" int feast_gram_dev(int n, int m, const double* X, const double* Y, do
     return 0;
 }
 
+extern "C" int feast_gram_oz_dev(int n, int m, const double* X, const double* Y, double* C, void* stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n <= 0) return -101;
+    if (m <= 0) return -102;
+    const size_t gp = gram_oz_partial_doubles(n, m, nullptr, nullptr, num_sms());
+    AsyncMem am(s);
+    void* part = nullptr;
+    void* ex = nullptr;
+    CK(am.alloc(&part, gp * sizeof(double)));
+    CK(am.alloc(&ex, gram_oz_work_bytes(m)));
+    CK(launch_gram_oz(n, m, X, Y, C, (double*)part, (int*)ex, s));
+    CK(cudaStreamSynchronize(s));
+    return 0;
+}
+
+extern "C" int feast_gemm_oz_dev(int n, int m, int k, const double* A, const double* V, double* C, void* stream)
+{
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n <= 0) return -101;
+    if (m <= 0) return -102;
+    if (k <= 0) return -103;
+    AsyncMem am(s);
+    void* w = nullptr;
+    CK(am.alloc(&w, gemm_oz_work_bytes(n, m, k)));
+    CK(launch_gemm_oz(n, m, k, A, V, C, w, s));
+    CK(cudaStreamSynchronize(s));
+    return 0;
+}
+
 extern "C" int feast_gemm_dev(int n, int m, int k, const double* A, const double* V, double* C, void* stream)
 {
     cudaStream_t s = (cudaStream_t)stream;
@@ -1732,6 +1775,93 @@ extern "C" int feast_eig_grad_dev(int n, const int* ia, const int* ja, int m, co
     if (m <= 0 || m > 2048) return -104;
     CK(launch_eig_grad(n, ia, ja, m, X, w, grad, s));
     CK(cudaStreamSynchronize(s));
+    return 0;
+}
+
+// Validate one host CSR pattern (base ia[0] in {0,1}, rows nondecreasing,
+// columns in range and in the stored triangle for 'L'/'U') and make a 0-based
+// copy.  arg0 is the argument number of ia.
+static int host_pattern(char uplo, int n, const int* ia, const int* ja, int arg0, std::vector<int>& oia,
+                        std::vector<int>& oja)
+{
+    if (!ia) return -(100 + arg0);
+    if (!ja) return -(100 + arg0 + 1);
+    const int base = ia[0];
+    if (base != 0 && base != 1) return -(100 + arg0);
+    for (int i = 0; i < n; ++i)
+        if (ia[i + 1] < ia[i]) return -(100 + arg0);
+    oia.resize(n + 1);
+    for (int i = 0; i <= n; ++i) oia[i] = ia[i] - base;
+    oja.resize(std::max(1, oia[n]));
+    for (int i = 0; i < n; ++i)
+        for (int p = oia[i]; p < oia[i + 1]; ++p) {
+            const int j = ja[p] - base;
+            if (j < 0 || j >= n) return -(100 + arg0 + 1);
+            if ((uplo == 'L' && j > i) || (uplo == 'U' && j < i)) return -(100 + arg0 + 1);
+            oja[p] = j;
+        }
+    return 0;
+}
+
+extern "C" int feast_scsr_grad(char uplo, int n, const int* ia, const int* ja, const int* ib, const int* jb, int m,
+                               const double* x, const double* e, const double* g, double* grad_a, double* grad_b)
+{
+    if (uplo != 'F' && uplo != 'L' && uplo != 'U') return -101;
+    if (n <= 0) return 202;
+    const bool hasB = ib || jb;
+    if (m < 0 || m > 2048) return -107;
+    if (!x) return -108;
+    if (hasB && !e) return -109;
+    if (!g) return -110;
+    if (!grad_a) return -111;
+    if (hasB && !grad_b) return -112;
+    std::vector<int> aia, aja, bia, bja;
+    int inf = host_pattern(uplo, n, ia, ja, 3, aia, aja);
+    if (inf) return inf;
+    if (hasB && (inf = host_pattern(uplo, n, ib, jb, 5, bia, bja))) return inf;
+    const int nnz_a = aia[n], nnz_b = hasB ? bia[n] : 0;
+    if (m == 0) {
+        for (int p = 0; p < nnz_a; ++p) grad_a[p] = 0.0;
+        for (int p = 0; p < nnz_b; ++p) grad_b[p] = 0.0;
+        return 0;
+    }
+    g_err.clear();
+    DevMem dm;
+    int *d_ia = nullptr, *d_ja = nullptr, *d_ib = nullptr, *d_jb = nullptr;
+    double *d_xc = nullptr, *d_xr = nullptr, *d_g = nullptr, *d_e = nullptr, *d_ga = nullptr, *d_gb = nullptr;
+    const int half = uplo != 'F';
+#define GK(x)                                                  \
+    do {                                                       \
+        cudaError_t _e = (x);                                  \
+        if (_e != cudaSuccess) return cuda_fail(_e, #x);       \
+    } while (0)
+    GK(dm.alloc(&d_ia, (size_t)n + 1));
+    GK(dm.alloc(&d_ja, aja.size()));
+    GK(dm.alloc(&d_xc, (size_t)n * m));
+    GK(dm.alloc(&d_xr, (size_t)n * m));
+    GK(dm.alloc(&d_g, (size_t)m));
+    GK(dm.alloc(&d_ga, (size_t)std::max(1, nnz_a)));
+    GK(cudaMemcpy(d_ia, aia.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+    GK(cudaMemcpy(d_ja, aja.data(), sizeof(int) * aja.size(), cudaMemcpyHostToDevice));
+    GK(cudaMemcpy(d_xc, x, sizeof(double) * (size_t)n * m, cudaMemcpyHostToDevice));
+    GK(cudaMemcpy(d_g, g, sizeof(double) * m, cudaMemcpyHostToDevice));
+    k_col_to_row<<<grid_for((long long)n * m), 256>>>(n, m, d_xc, d_xr);
+    count_launches(1);
+    GK(cudaGetLastError());
+    GK(launch_eig_grad(n, d_ia, d_ja, m, d_xr, d_g, d_ga, nullptr, nullptr, half));
+    if (hasB) {
+        GK(dm.alloc(&d_ib, (size_t)n + 1));
+        GK(dm.alloc(&d_jb, bja.size()));
+        GK(dm.alloc(&d_e, (size_t)m));
+        GK(dm.alloc(&d_gb, (size_t)std::max(1, nnz_b)));
+        GK(cudaMemcpy(d_ib, bia.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+        GK(cudaMemcpy(d_jb, bja.data(), sizeof(int) * bja.size(), cudaMemcpyHostToDevice));
+        GK(cudaMemcpy(d_e, e, sizeof(double) * m, cudaMemcpyHostToDevice));
+        GK(launch_eig_grad(n, d_ib, d_jb, m, d_xr, d_g, d_gb, nullptr, d_e, half));
+    }
+    GK(cudaMemcpy(grad_a, d_ga, sizeof(double) * nnz_a, cudaMemcpyDeviceToHost));
+    if (hasB) GK(cudaMemcpy(grad_b, d_gb, sizeof(double) * nnz_b, cudaMemcpyDeviceToHost));
+#undef GK
     return 0;
 }
 

@@ -136,6 +136,19 @@ cudaError_t launch_spmm_f64(int n, int m, const int* ia, const int* ja, const do
 cudaError_t launch_gram_f64(int n, int m, const double* X, const double* Y, double* C,
                             double* part, int ksplit, int sym, cudaStream_t s);
 size_t gram_partial_doubles(int n, int m, int* ksplit_out, int nsm);
+// part [ksplit][m][m] (upper-triangle partials) -> C: summed in split order, mirrored
+cudaError_t launch_gram_reduce(int m, const double* part, int ksplit, double* C, cudaStream_t s);
+// C = X^T Y to FP64 accuracy from exact BF16 slice products (k_ozaki.cu); part:
+// gram_oz_partial_doubles(n, m, ...) doubles, ex: gram_oz_work_bytes(m) bytes.
+size_t gram_oz_partial_doubles(int n, int m, int* ksplit_out, long long* rows_per_split, int nsm);
+size_t gram_oz_work_bytes(int m);
+cudaError_t launch_gram_oz(int n, int m, const double* X, const double* Y, double* C, double* part, int* ex,
+                           cudaStream_t s);
+// C (n x k) = A (n x m) V (m x k), row-major, FP64 accuracy from exact BF16
+// slice products (k_ozaki.cu); work: gemm_oz_work_bytes(n, m, k) bytes.
+size_t gemm_oz_work_bytes(int n, int m, int k);
+cudaError_t launch_gemm_oz(int n, int m, int k, const double* A, const double* V, double* C, void* work,
+                           cudaStream_t s);
 // C (n x k) = A (n x m, row-major) * V (m x k, row-major)
 cudaError_t launch_gemm_nn_f64(int n, int m, int k, const double* A, const double* V, double* C,
                                cudaStream_t s);
@@ -164,8 +177,11 @@ int reduced_gev_dev(int m, const double* Aq, const double* Bq, double* lam, doub
                     void* work, cudaStream_t s);
 
 // ---------------------------------------------------------------- gradient (k_grad.cu)
+// grad[p] = sum_k w_k Xr[i_p][k] Xr[j_p][k], w_k = gw[k] (lam NULL) or -gw[k] lam[k];
+// half != 0 doubles the off-diagonal entries (one stored triangle).
 cudaError_t launch_eig_grad(int n, const int* ia, const int* ja, int m, const double* Xr,
-                            const double* gw, double* grad, cudaStream_t s);
+                            const double* gw, double* grad, cudaStream_t s, const double* lam = nullptr,
+                            int half = 0);
 
 // ---------------------------------------------------------------- batched Rayleigh-Ritz (k_batch.cu)
 // One entry per problem of a batch; all pointers device; offsets in doubles.

@@ -25,6 +25,8 @@
 // W Lambda W^T, V = S W (V^T B_Q V = I).  Dropped directions stay in the
 // m x m arrays as exact zero columns of S and get a sentinel eigenvalue, so
 // they sort last and the live count mk is the number of non-sentinel values.
+#include <atomic>
+
 #include "chol.cuh"
 #include "feast_internal.cuh"
 
@@ -49,11 +51,16 @@ struct JacWork {
     int status;
 };
 
+// Spin limit of the grid barrier in SM clock cycles (about two seconds at
+// 2 GHz); feast_set_wait_limit changes it for the launches that follow.
+static constexpr long long kDefaultSpinCycles = 4000000000LL;
+static std::atomic<long long> g_spin_cycles{kDefaultSpinCycles};
+
 // Bounded grid barrier for a cooperative launch: each CTA adds one arrival to
 // a counter that only grows, then waits until the counter reaches the end of
-// its generation.  Returns false when any CTA timed out (about two seconds of
-// spinning) or an earlier barrier failed.
-__device__ __forceinline__ bool grid_sync(GridBar* b)
+// its generation.  Returns false when any CTA spun longer than `limit` clock
+// cycles or an earlier barrier failed (the error flag is then set for all).
+__device__ __forceinline__ bool grid_sync(GridBar* b, long long limit)
 {
     __shared__ int ok;
     __syncthreads();
@@ -69,7 +76,7 @@ __device__ __forceinline__ bool grid_sync(GridBar* b)
                 asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(cur) : "l"(&b->count) : "memory");
                 if (cur >= target) break;
                 if (*(volatile int*)&b->err) { good = 0; break; }
-                if (clock64() - t0 > 4000000000LL) {
+                if (clock64() - t0 > limit) {
                     atomicExch(&b->err, 1);
                     good = 0;
                     break;
@@ -95,7 +102,7 @@ __device__ __forceinline__ int rr_player(int slot, int r, int mp)
 // copy of A into the other copy, so no CTA writes what another still reads.
 // Rotation tables in dynamic shared memory: c, s, t (doubles), p, q (ints).
 __global__ void __launch_bounds__(kEigThreads) jacobi_coop(int m, double* A, double* A2, double* V, double* lam,
-                                                          double* Vout, JacWork* w)
+                                                          double* Vout, JacWork* w, long long limit)
 {
     extern __shared__ double rsh[];
     const int mp = m + (m & 1);
@@ -123,7 +130,7 @@ __global__ void __launch_bounds__(kEigThreads) jacobi_coop(int m, double* A, dou
         }
         if (threadIdx.x == 0) w->fro = sqrt(red[0]);
     }
-    if (!grid_sync(&w->bar)) return;
+    if (!grid_sync(&w->bar, limit)) return;
     const double absfloor = 1e-18 * *(volatile double*)&w->fro;
     double* cur = A;
     double* nxt = A2;
@@ -204,7 +211,7 @@ __global__ void __launch_bounds__(kEigThreads) jacobi_coop(int m, double* A, dou
                 V[(size_t)i * m + p] = ck * vp - sk * vq;
                 V[(size_t)i * m + q] = sk * vp + ck * vq;
             }
-            if (!grid_sync(&w->bar)) return;
+            if (!grid_sync(&w->bar, limit)) return;
             double* tmp = cur;
             cur = nxt;
             nxt = tmp;
@@ -277,7 +284,8 @@ int jacobi_eig_dev(int m, double* A, double* lam, double* V, void* work, cudaStr
         cudaFuncSetAttribute(jacobi_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return -3;
     int grid = coop_grid(m);
-    void* args[] = {&m, &A, &A2, &Vw, &lam, &V, &w};
+    long long limit = g_spin_cycles.load();
+    void* args[] = {&m, &A, &A2, &Vw, &lam, &V, &w, &limit};
     cudaError_t e = cudaLaunchCooperativeKernel((void*)jacobi_coop, dim3(grid), dim3(kEigThreads), args, smem, s);
     count_launches(1);
     if (e != cudaSuccess) return -3;
@@ -439,3 +447,8 @@ int reduced_gev_dev(int m, const double* Aq, const double* Bq, double* lam, doub
 }
 
 }  // namespace feast
+
+extern "C" long long feast_set_wait_limit(long long cycles)
+{
+    return feast::g_spin_cycles.exchange(cycles >= 1 ? cycles : feast::kDefaultSpinCycles);
+}

@@ -11,9 +11,13 @@
 namespace feast {
 
 // One warp per row i; Xr is row-major n x m (eigenvectors in columns).
+// Weights: w_k = g_k, or w_k = -g_k lambda_k when lam is given (entries of B).
+// half: the pattern is one triangle of a symmetric matrix, so a stored
+// off-diagonal value stands for both (i, j) and (j, i) and its derivative is
+// twice the entry-wise one.
 __global__ void __launch_bounds__(256) eig_grad(int n, const int* __restrict__ ia, const int* __restrict__ ja, int m,
                                                 const double* __restrict__ Xr, const double* __restrict__ gw,
-                                                double* __restrict__ grad)
+                                                const double* __restrict__ lam, int half, double* __restrict__ grad)
 {
     extern __shared__ double u_sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -21,21 +25,24 @@ __global__ void __launch_bounds__(256) eig_grad(int n, const int* __restrict__ i
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int i = warp; i < n; i += nwarps) {
-        for (int k = lane; k < m; k += 32) u[k] = gw[k] * Xr[(size_t)i * m + k];
+        for (int k = lane; k < m; k += 32) {
+            const double w = lam ? -gw[k] * lam[k] : gw[k];
+            u[k] = w * Xr[(size_t)i * m + k];
+        }
         __syncwarp();
         for (int p = ia[i]; p < ia[i + 1]; ++p) {
             const int j = ja[p];
             double s = 0.0;
             for (int k = lane; k < m; k += 32) s = fma(u[k], __ldg(Xr + (size_t)j * m + k), s);
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) grad[p] = s;
+            if (lane == 0) grad[p] = (half && j != i) ? 2.0 * s : s;
         }
         __syncwarp();
     }
 }
 
 cudaError_t launch_eig_grad(int n, const int* ia, const int* ja, int m, const double* Xr, const double* gw,
-                            double* grad, cudaStream_t s)
+                            double* grad, cudaStream_t s, const double* lam, int half)
 {
     if (n <= 0) return cudaSuccess;
     if (m <= 0 || m > 2048) return cudaErrorInvalidValue;
@@ -47,7 +54,7 @@ cudaError_t launch_eig_grad(int n, const int* ia, const int* ja, int m, const do
     long long blocks = ((long long)n + 7) / 8;
     const long long cap = (long long)num_sms() * 8;
     if (blocks > cap) blocks = cap;
-    eig_grad<<<(int)blocks, 256, smem, s>>>(n, ia, ja, m, Xr, gw, grad);
+    eig_grad<<<(int)blocks, 256, smem, s>>>(n, ia, ja, m, Xr, gw, lam, half, grad);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -192,6 +192,15 @@ size_t gram_partial_doubles(int n, int m, int* ksplit_out, int nsm)
     return (size_t)ks * m * m;
 }
 
+cudaError_t launch_gram_reduce(int m, const double* part, int ksplit, double* C, cudaStream_t s)
+{
+    long long blocks = ((long long)m * m + 255) / 256;
+    if (blocks > 2048) blocks = 2048;
+    gram_reduce<<<(int)blocks, 256, 0, s>>>(m, part, ksplit, C);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gram_f64(int n, int m, const double* X, const double* Y, double* C, double* part, int ksplit,
                             int sym, cudaStream_t s)
 {

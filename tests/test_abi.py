@@ -290,6 +290,49 @@ def test_hermitian_argument_errors_are_host_side(pkg):
                                 m0=1025).info == 201
 
 
+def test_hermitian_input_must_be_hermitian(pkg):
+    """The Hermitian driver's shadow system needs A = A^H: a complex diagonal
+    entry (any storage) or a full-storage pair with a_ji != conj(a_ij) (or a
+    missing mirror) is rejected with the values argument's code -103 (-106 for
+    B) before any device work; a conjugated pair within rounding passes the
+    check (and then fails only for want of a GPU here)."""
+    A = fw.flux_ring(20, 0.3)
+    ok = dict(n=20, ia=A.indptr, ja=A.indices, emin=0.0, emax=0.5, m0=6)
+    rows = np.repeat(np.arange(20), np.diff(A.indptr))
+
+    def code(uplo, a, **kw):
+        args = dict(ok)
+        args.update(kw)
+        return pkg.feast_hcsr_solve(uplo, a=a, **args).info
+
+    diag = np.nonzero(rows == A.indices)[0][0]
+    off = np.nonzero(rows < A.indices)[0][0]
+    d = A.data.copy()
+    d[diag] += 1e-3j
+    assert code("F", d) == -103
+    L = fw.zcsr_from_dense(np.tril(A.to_dense()))
+    dl = L.data.copy()
+    dl[np.nonzero(np.repeat(np.arange(20), np.diff(L.indptr)) == L.indices)[0][0]] += 1e-3j
+    assert code("L", dl, ia=L.indptr, ja=L.indices) == -103
+    f = A.data.copy()
+    f[off] = np.conj(f[off])  # a_ij no longer the conjugate of a_ji
+    assert code("F", f) == -103
+    g = A.data.copy()
+    g[off] *= 1 + 1e-9
+    assert code("F", g) == -103
+    h = A.data.copy()
+    h[off] *= 1 + 1e-15  # within rounding: accepted by the check
+    import torch
+
+    if not torch.cuda.is_available():
+        from paper_2002_04807_gb300 import FeastError
+
+        with pytest.raises(FeastError):
+            code("F", h)
+    B = fw.zcsr_from_dense(np.diag(np.full(20, 1.0 + 1e-3j)))
+    assert code("F", A.data, b=B.data, ib=B.indptr, jb=B.indices) == -106
+
+
 def test_hermitian_no_cpu_fallback_without_gpu(pkg):
     import torch
 
@@ -300,3 +343,48 @@ def test_hermitian_no_cpu_fallback_without_gpu(pkg):
 
     with pytest.raises(FeastError):
         pkg.feast_hcsr_solve("F", 20, A.data, A.indptr, A.indices, emin=0.0, emax=0.5, m0=6)
+
+
+def test_grad_argument_errors_are_host_side(pkg):
+    """feast_scsr_grad validates its host arguments before any device work."""
+    from paper_2002_04807_gb300 import FeastError
+
+    A = fw.laplacian_1d(20)
+    x, g = np.zeros((20, 3)), np.ones(3)
+
+    def code(**kw):
+        args = dict(uplo="F", n=20, ia=A.indptr, ja=A.indices, x=x, g=g)
+        args.update(kw)
+        try:
+            pkg.feast_scsr_grad(**args)
+        except FeastError as err:
+            return int(str(err).split("returned")[1].split()[0])
+        return 0
+
+    assert code(uplo="X") == -101
+    assert code(n=0) == 202
+    bad = A.indices.copy()
+    bad[3] = 99
+    assert code(ja=bad) == -104
+    assert code(uplo="L") == -104  # upper entries in lower storage
+    bad_ia = A.indptr.copy()
+    bad_ia[5] = bad_ia[4] - 1
+    assert code(ia=bad_ia) == -103
+    assert code(ib=A.indptr, jb=A.indices) == -109  # B pattern without eigenvalues
+    assert code(x=np.zeros((20, 2049)), g=np.ones(2049)) == -107
+    B = fw.laplacian_1d(20)
+    badb = B.indices.copy()
+    badb[0] = -5
+    assert code(ib=B.indptr, jb=badb, e=np.ones(3)) == -106
+
+
+def test_grad_no_cpu_fallback_without_gpu(pkg):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    from paper_2002_04807_gb300 import FeastError
+
+    A = fw.laplacian_1d(20)
+    with pytest.raises(FeastError, match="-4"):
+        pkg.feast_scsr_grad("F", 20, A.indptr, A.indices, np.zeros((20, 3)), np.ones(3))

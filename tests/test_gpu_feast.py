@@ -164,6 +164,23 @@ def test_generalized_27pt(pkg, mixed):
     check_against(r, ref, emax, B=B)
 
 
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_generalized_nondiagonal_b(pkg, mixed):
+    """A non-diagonal SPD sparse B (7-point mass-like pattern, the guide's
+    dfeast_scsrgv with a full {B, IB, JB}): the packed general-B gathers of the
+    filter, the general-B residual and SpMM, in both precisions, against the
+    oracle; 1-based CSR input for both matrices on the FP64 run."""
+    p = fw.laplace3d_general_b(side=10, count=20, m0=32)
+    ref = O.feast_scsr(p.A, p.B, 0.0, p.emax, 32, Y0=p.y0(), ne=8, ratio=100, tol_exp=10)
+    assert ref["info"] == 0 and ref["M"] == 20 == O.count_below(p.A, p.B, p.emax)
+    if mixed:
+        r = run_gpu(pkg, p, mixed)
+    else:
+        one = lambda M: fw.CSR(M.n, M.indptr + 1, M.indices + 1, M.data)  # noqa: E731
+        r = run_gpu(pkg, p, mixed, csr=one(p.A), B=one(p.B))
+    check_against(r, ref, p.emax, B=p.B)
+
+
 @pytest.fixture(scope="module")
 def config3_shape():
     """The 27-point generalized workload's generator (off-diagonals -U[0.5,1.5],
@@ -295,6 +312,24 @@ def test_device_driver_with_torch_stream(pkg):
     assert np.array_equal(Xd, host.X)
 
 
+def test_projection_arithmetic_fp64_dmma_agrees(pkg):
+    """fpm(54) = 1 builds the reduced matrices on the FP64 tensor cores instead
+    of from BF16 slice products: same eigenpairs within the parity bars, both
+    against the oracle."""
+    p = fw.laplace3d_potential(side=14, count=24, m0=40, seed=12)
+    ref = O.feast_scsr(p.A, None, p.emin, p.emax, p.m0, Y0=p.y0(), ne=8, ratio=100, tol_exp=10)
+    out = []
+    for arith in (0, 1):
+        fpm = pkg.feast_init()
+        fpm[1], fpm[2], fpm[3], fpm[4], fpm[17], fpm[44], fpm[45], fpm[53] = 8, 10, 30, 1, 100, 2, 200, arith
+        r = pkg.feast_scsr_solve("F", p.n, p.A.data, p.A.indptr, p.A.indices, fpm=fpm, emin=p.emin, emax=p.emax,
+                                 m0=p.m0, x0=p.y0())
+        check_against(r, ref, p.emax)
+        out.append(r)
+    M = out[0].M
+    assert out[1].M == M and np.abs(out[0].E[:M] - out[1].E[:M]).max() <= 1e-12 * p.emax
+
+
 def test_random_start_block(pkg):
     p = fw.laplace3d_potential(side=12, count=16, m0=28, seed=9)
     fpm = pkg.feast_init()
@@ -309,18 +344,22 @@ def test_random_start_block(pkg):
 
 
 def test_bench_workload_properties(pkg):
-    """The 64^3 Laplacian + potential workload at full size (N = 262144, M0 =
-    150, Ne = 8): residuals recomputed by the oracle, B-orthonormality, and
-    agreement of the mixed and FP64 solvers."""
-    p = fw.laplace3d_potential()
-    mixed = run_gpu(pkg, p, 1)
-    assert mixed.info == 0 and 80 <= mixed.M <= 140
+    """The 64^3 Laplacian + potential workload at full size with the bench's
+    exact settings (N = 262144, M0 = 150, Ne = 8, ellipse ratio 200, inner
+    tolerance fpm(45) = 2, fpm(46) = 80 steps, one node per COCG batch): the
+    eigenvalue count equals the Sylvester-inertia count stored by the
+    oracle's golden script, residuals recomputed by the oracle,
+    B-orthonormality, and agreement of the mixed and FP64 solvers."""
+    p = fw.laplace3d_potential(side=64, count=100, m0=150, ne=8, ratio=200, seed=1)
+    gold = json.load(open(os.path.join(GOLD, "laplace3d_64_count.json")))
+    mixed = run_gpu(pkg, p, 1, inner=(2, 80), maxloop=40, nb=1)
+    assert mixed.info == 0 and mixed.M == gold["count_in_interval"], (mixed.info, mixed.M)
     M = mixed.M
     res = O.residuals(p.A, None, mixed.X[:, :M], mixed.E[:M], p.emin, p.emax)
     assert res.max() <= RES_TOL
     X = mixed.X[:, :M]
     assert np.abs(X.T @ X - np.eye(M)).max() < 1e-11
-    full = run_gpu(pkg, p, 0)
+    full = run_gpu(pkg, p, 0, inner=(2, 80), maxloop=40, nb=1)
     assert full.info == 0 and full.M == M
     assert (np.abs(mixed.E[:M] - full.E[:M]) / mixed.E[:M]).max() <= EIG_TOL
     assert cluster_angles(mixed.E[:M], X, full.E[:M], full.X[:, :M], p.emax) <= ANG_TOL

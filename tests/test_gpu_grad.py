@@ -125,3 +125,54 @@ def test_gradient_finite_differences_48cube(pkg):
         worst = max(worst, abs(fd - an) / (1e-5 + 1e-4 * abs(an)))
         assert abs(fd - an) <= 1e-5 + 1e-4 * abs(an), (pidx, fd, an)
     assert worst <= 1.0
+
+
+@pytest.mark.parametrize("bkind", [None, "general"])
+def test_host_grad_entry_point_matches_dense_reference(pkg, bkind):
+    """feast_scsr_grad (host buffers, the boundary's gradient call) on the
+    eigenpairs feast_scsr_solve returns for a 12^3 problem: grad_a and grad_b
+    against the oracle's gradient on a dense FP64 eigendecomposition, per
+    stored entry of the full patterns (B = I, or a non-diagonal SPD B)."""
+    p = fw.laplace3d_grad(side=12, count=20, m0=32)
+    A = p.A
+    B = fw.mass_like_3d(12, np.random.default_rng(3)) if bkind else None
+    lam, V = scipy.linalg.eigh(A.to_dense(), np.eye(A.n) if B is None else B.to_dense())
+    emax = 0.5 * (lam[19] + lam[20])
+    f = _fpm(pkg)
+    f[4] = 1
+    kw = {} if B is None else dict(b=B.data, ib=B.indptr, jb=B.indices)
+    r = pkg.feast_scsr_solve("F", A.n, A.data, A.indptr, A.indices, fpm=f, emin=0.0, emax=emax, m0=32,
+                             x0=fw.gaussian_block(A.n, 32, 4), **kw)
+    assert r.info == 0 and r.M == 20
+    g = fw.loss_weights(20, 4)
+    ga, gb = pkg.feast_scsr_grad("F", A.n, A.indptr, A.indices, r.X[:, :20], g,
+                                 ib=None if B is None else B.indptr, jb=None if B is None else B.indices,
+                                 e=r.E[:20])
+    ref_a = O.eig_grad(A, V[:, :20], g)
+    assert np.abs(ga - ref_a).max() < 1e-9 * np.abs(ref_a).max()
+    if B is None:
+        assert gb is None
+    else:
+        ref_b = O.eig_grad(B, V[:, :20], -g * lam[:20])
+        assert np.abs(gb - ref_b).max() < 1e-9 * np.abs(ref_b).max()
+
+
+def test_host_grad_half_storage_and_one_based(pkg):
+    """'L' storage with 1-based indices: a stored off-diagonal value stands for
+    both symmetric entries, so its derivative is the sum of the two full-
+    storage derivatives; diagonal entries keep theirs.  Exact against the
+    oracle's entry-wise gradient on the same eigenvectors."""
+    rng = np.random.default_rng(12)
+    A = fw.laplace3d_potential(side=9, count=10, m0=16, seed=3).A
+    X = rng.standard_normal((A.n, 23))
+    g = rng.standard_normal(23)
+    full = O.eig_grad(A, X, g)
+    L = fw.csr_from_dense(np.tril(A.to_dense()))
+    ga, _ = pkg.feast_scsr_grad("L", A.n, L.indptr + 1, L.indices + 1, X, g)
+    rows = np.repeat(np.arange(A.n), np.diff(A.indptr))
+    want = []
+    for i, j in zip(np.repeat(np.arange(A.n), np.diff(L.indptr)), L.indices):
+        pij = np.nonzero((rows == i) & (A.indices == j))[0][0]
+        pji = np.nonzero((rows == j) & (A.indices == i))[0][0]
+        want.append(full[pij] + (full[pji] if i != j else 0.0))
+    assert np.abs(ga - np.array(want)).max() < 1e-13 * np.abs(full).max()

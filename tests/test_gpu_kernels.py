@@ -65,14 +65,24 @@ def shifted_ref(A, B, z, Pstd):
     return out
 
 
+def make_b(kind, n, side, rng):
+    """B = I (None), a diagonal SPD B, or a non-diagonal SPD B with the 7-point
+    pattern (the packed general-B gather path of the filter kernels)."""
+    if kind == "diag":
+        return fw.diagonal_csr(rng.uniform(1, 2, n))
+    if kind == "general":
+        return fw.mass_like_3d(side, rng)
+    return None
+
+
 @pytest.mark.parametrize("fp64", [0, 1])
-@pytest.mark.parametrize("gen", [False, True])
+@pytest.mark.parametrize("bkind", [None, "diag", "general"])
 @pytest.mark.parametrize("nb,m", [(8, 10), (16, 3), (5, 7)])
-def test_shifted_spmm(pkg, fp64, gen, nb, m):
+def test_shifted_spmm(pkg, fp64, bkind, nb, m):
     rng = np.random.default_rng(10 + nb + m)
     p = fw.laplace3d_potential(side=11, count=10, m0=m, seed=4)  # n = 1331: 5 row blocks + tail
     A = p.A
-    B = fw.diagonal_csr(rng.uniform(1, 2, A.n)) if gen else None
+    B = make_b(bkind, A.n, 11, rng)
     n = A.n
     z = rng.uniform(0, 2, nb) + 1j * rng.uniform(0.05, 1, nb)
     Pstd = rng.standard_normal((nb, n, m)) + 1j * rng.standard_normal((nb, n, m))
@@ -104,20 +114,25 @@ def _filter_case(side=10, m=12, seed=5):
 
 
 @pytest.mark.parametrize("mixed", [0, 1])
-def test_filter_classic_matches_oracle(pkg, mixed):
+@pytest.mark.parametrize("bkind", [None, "general"])
+def test_filter_classic_matches_oracle(pkg, mixed, bkind):
     p = _filter_case()
     n, m = p.n, p.m0
     Y = p.y0()
+    B = make_b(bkind, n, 10, np.random.default_rng(21))
     fpm = pkg.feast_init()
     fpm[1], fpm[17], fpm[41] = 8, 100, mixed
     fpm[44], fpm[45] = (12, 3000) if not mixed else (6, 3000)
     ia, ja, av = dcsr(p.A)
-    R = dev(Y)  # row-major n x m == C-order copy
+    ib = jb = bv = None
+    if B is not None:
+        ib, jb, bv = dcsr(B)
+    # right-hand side of the first pass: B Y
+    R = dev(Y if B is None else O.csr_mm(B, Y))  # row-major n x m == C-order copy
     Q = torch.zeros((n, m), dtype=torch.float64, device="cuda")
-    it = pkg.feast_filter_dev(n, ia, ja, av, None, None, None, m, R, R, dev(np.zeros(m)), 0, fpm, p.emin, p.emax,
-                              Q)
+    it = pkg.feast_filter_dev(n, ia, ja, av, ib, jb, bv, m, R, R, dev(np.zeros(m)), 0, fpm, p.emin, p.emax, Q)
     assert it > 0
-    ref = O.filter_block(p.A, None, 8, p.emin, p.emax, 1.0, Y)
+    ref = O.filter_block(p.A, B, 8, p.emin, p.emax, 1.0, Y)
     err = np.abs(Q.cpu().numpy() - ref).max() / np.abs(ref).max()
     assert err < (1e-8 if not mixed else 2e-3), err
 
@@ -161,6 +176,52 @@ def test_gram(pkg, n, m):
     assert np.abs(got - exp).max() < 1e-13 * scale, np.abs(got - exp).max()
 
 
+@pytest.mark.parametrize("n,m", [(1000, 70), (4097, 150), (33, 1), (262144, 150), (300, 33), (20000, 300)])
+def test_gram_sliced_bf16(pkg, n, m):
+    """The projections' default arithmetic: X^T Y from exact BF16 slice
+    products (8 slices of 7 bits under a power-of-two column scale) against
+    numpy's FP64 product, at the FP64 Gram's tolerance; sizes with ragged
+    32-column tiles, a single column and more rows than one split."""
+    rng = np.random.default_rng(n + 3 * m)
+    X = rng.standard_normal((n, m))
+    Y = rng.standard_normal((n, m))
+    C = torch.full((m, m), np.nan, dtype=torch.float64, device="cuda")
+    pkg.feast_gram_oz_dev(n, m, dev(X), dev(Y), C)
+    got = C.cpu().numpy()
+    assert np.abs(got - got.T).max() == 0.0
+    full = X.T @ Y
+    exp = np.where(np.arange(m)[:, None] <= np.arange(m)[None, :], full, full.T)
+    assert np.abs(got - exp).max() < 1e-13 * np.sqrt(n), np.abs(got - exp).max()
+
+
+def test_gram_sliced_scaling_edge_cases(pkg):
+    """Columns 1e-150 .. 1e150 apart, a zero column, a column with one huge
+    entry among tiny ones, and the symmetric call X = Y: each element within
+    FP64 rounding of its own column norms (the column scale is per column)."""
+    rng = np.random.default_rng(42)
+    n, m = 5000, 40
+    X = rng.standard_normal((n, m)) * np.logspace(-150, 150, m)[None, :]
+    X[:, 7] = 0.0
+    X[:, 11] = 1e-8 * rng.standard_normal(n)
+    X[123, 11] = 3.0
+    Y = rng.standard_normal((n, m)) * np.logspace(100, -100, m)[None, :]
+    for Yc, same in ((Y, False), (X, True)):
+        C = torch.zeros((m, m), dtype=torch.float64, device="cuda")
+        Xd = dev(X)
+        pkg.feast_gram_oz_dev(n, m, Xd, Xd if same else dev(Yc), C)
+        got = C.cpu().numpy()
+        full = X.T @ Yc
+        exp = np.where(np.arange(m)[:, None] <= np.arange(m)[None, :], full, full.T)
+        nx, ny = np.linalg.norm(X, axis=0), np.linalg.norm(Yc, axis=0)
+        lo, hi = np.minimum.outer(np.arange(m), np.arange(m)), np.maximum.outer(np.arange(m), np.arange(m))
+        scale = nx[lo] * ny[hi]
+        bad = np.abs(got - exp) > 1e-13 * scale + 1e-300
+        assert not bad.any(), np.argwhere(bad)[:5]
+        assert np.all(got[7, 7:] == 0.0)  # X's zero column: row 7 of the upper triangle
+        if same:
+            assert np.all(got[7, :] == 0.0) and np.all(got[:, 7] == 0.0)
+
+
 @pytest.mark.parametrize("n,m,k", [(1000, 70, 65), (129, 150, 150), (7, 3, 2)])
 def test_gemm(pkg, n, m, k):
     rng = np.random.default_rng(n)
@@ -169,6 +230,26 @@ def test_gemm(pkg, n, m, k):
     C = torch.zeros((n, k), dtype=torch.float64, device="cuda")
     pkg.feast_gemm_dev(n, m, k, dev(A), dev(V), C)
     assert np.abs(C.cpu().numpy() - A @ V).max() < 1e-13 * np.sqrt(m)
+
+
+@pytest.mark.parametrize("n,m,k", [(1000, 70, 65), (129, 150, 150), (7, 3, 2), (262144, 150, 150), (3000, 300, 300),
+                                   (500, 301, 33)])
+def test_gemm_sliced_bf16(pkg, n, m, k):
+    """X = Q V, the Ritz vectors' default arithmetic, from exact BF16 slice
+    products under row and column power-of-two scales, against numpy FP64;
+    rows of very different size and a zero row are included."""
+    rng = np.random.default_rng(n + m + k)
+    A = rng.standard_normal((n, m)) * np.logspace(-30, 30, n)[:, None]
+    A[n // 2] = 0.0
+    V = rng.standard_normal((m, k))
+    C = torch.full((n, k), np.nan, dtype=torch.float64, device="cuda")
+    pkg.feast_gemm_oz_dev(n, m, k, dev(A), dev(V), C)
+    got = C.cpu().numpy()
+    exp = A @ V
+    scale = np.linalg.norm(A, axis=1)[:, None] * np.linalg.norm(V, axis=0)[None, :]
+    err = np.abs(got - exp) / np.maximum(scale, 1e-300)
+    assert err.max() < 1e-14, err.max()
+    assert np.all(got[n // 2] == 0.0)
 
 
 @pytest.mark.parametrize("m", [1, 2, 7, 64, 151, 300])
@@ -262,12 +343,13 @@ def test_reduced_eig_rank_deficient(pkg):
     assert np.all(lg[7:] >= 1e299)
 
 
-@pytest.mark.parametrize("gen", [False, True])
-def test_residual_matches_oracle(pkg, gen):
+@pytest.mark.parametrize("bkind", [None, "diag", "general"])
+def test_residual_matches_oracle(pkg, bkind):
     rng = np.random.default_rng(8)
     p = fw.laplace3d_potential(side=13, count=10, m0=37, seed=2)
     A = p.A
-    B = fw.diagonal_csr(rng.uniform(1, 2, A.n)) if gen else None
+    B = make_b(bkind, A.n, 13, rng)
+    gen = B is not None
     X = rng.standard_normal((A.n, 37))
     lam = rng.uniform(0, 1, 37)
     R = torch.zeros((A.n, 37), dtype=torch.float64, device="cuda")
@@ -281,3 +363,43 @@ def test_residual_matches_oracle(pkg, gen):
     assert np.abs(res.cpu().numpy() - ref).max() < 1e-13 * ref.max()
     BX = X if B is None else O.csr_mm(B, X)
     assert np.abs(R.cpu().numpy() - (O.csr_mm(A, X) - BX * lam)).max() < 1e-12
+
+
+def test_jacobi_barrier_time_limit_returns_error_and_recovers(pkg):
+    """The reduced eigensolver's cooperative Jacobi waits at a bounded grid
+    barrier.  With a one-cycle spin limit the barrier of a multi-CTA launch
+    (m = 150, about 40 CTAs) gives up: the kernel-level call fails with -3 and
+    a full solve returns info -3, with no hang.  With the default limit back,
+    the same calls succeed on the same context and match the oracle."""
+    from paper_2002_04807_gb300 import FeastError
+
+    m = 150
+    rng = np.random.default_rng(77)
+    a = rng.standard_normal((m, m))
+    a = a + a.T
+    lam = torch.zeros(m, dtype=torch.float64, device="cuda")
+    V = torch.zeros((m, m), dtype=torch.float64, device="cuda")
+    p = fw.laplace3d_potential(side=12, count=30, m0=100, seed=9)
+    fpm = pkg.feast_init()
+    fpm[1], fpm[2], fpm[4], fpm[17], fpm[44], fpm[45] = 8, 10, 1, 100, 2, 200
+
+    def solve():
+        return pkg.feast_scsr_solve("F", p.n, p.A.data, p.A.indptr, p.A.indices, fpm=fpm.copy(), emin=p.emin,
+                                    emax=p.emax, m0=p.m0, x0=p.y0())
+
+    prev = pkg.feast_set_wait_limit(1)
+    try:
+        with pytest.raises(FeastError, match="-3"):
+            pkg.feast_sym_eig_dev(m, dev(a), lam, V)
+        assert solve().info == -3
+    finally:
+        restored = pkg.feast_set_wait_limit(0)
+    assert prev == 4_000_000_000 and restored == 1
+    torch.cuda.synchronize()  # the context is still usable
+    pkg.feast_sym_eig_dev(m, dev(a), lam, V)
+    w, _, _ = O.jacobi_eig(a)
+    assert np.abs(lam.cpu().numpy() - w).max() < 1e-12 * np.abs(w).max()
+    r = solve()
+    ref = O.feast_scsr(p.A, None, p.emin, p.emax, p.m0, Y0=p.y0(), ne=8, ratio=100, tol_exp=10)
+    assert r.info == 0 and r.M == ref["M"]
+    assert np.abs(r.E[: r.M] - ref["E"][: r.M]).max() <= 1e-10 * p.emax

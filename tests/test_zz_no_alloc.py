@@ -46,6 +46,24 @@ def test_noalloc_gram_matches_allocating_entry_point(pkg):
         assert np.abs(g - g.T).max() == 0.0
 
 
+@pytest.mark.parametrize("n,m", [(300, 1448), (20000, 400), (262144, 150)])
+def test_noalloc_gram_at_limits_matches_numpy(pkg, n, m):
+    """Against numpy's FP64 X^T Y (upper triangle mirrored, as the Rayleigh-
+    Ritz projection uses it) at the sizes where the fixed array bounds the
+    split: m = 1448 fills it with one split; at (20000, 400) and (262144, 150)
+    the split count the allocating path would take (22, 102) is capped at what
+    fits (13, 93)."""
+    rng = np.random.default_rng(n + m)
+    X = rng.standard_normal((n, m))
+    Y = rng.standard_normal((n, m))
+    got = torch.full((m, m), np.nan, dtype=torch.float64, device="cuda")
+    pkg.feast_gram_noalloc_dev(n, m, _dev(X), _dev(Y), got)
+    g = got.cpu().numpy()
+    full = X.T @ Y
+    exp = np.where(np.arange(m)[:, None] <= np.arange(m)[None, :], full, full.T)
+    assert np.abs(g - exp).max() < 1e-13 * np.sqrt(n), np.abs(g - exp).max()
+
+
 def test_noalloc_gram_rejects_oversized_subspace(pkg):
     from paper_2002_04807_gb300 import FeastError
 
