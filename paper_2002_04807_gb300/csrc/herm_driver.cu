@@ -127,14 +127,18 @@ struct HBufs {
     int nb;    // nodes per filter batch
     int ks;    // Gram split
     bool fp64;
-    int* nactive_host;  // pinned
+    int* nactive_host;  // host copy of the two lane counters
 };
 
 // One contour pass: Q = sum over all nodes (first pass: b = B Y, rii = 0) or
 // the residual-inverse form (b = R, X, lam).  Returns 0 or -4; adds the BiCG
-// iterations taken to *iters.
+// steps launched to *iters and the lanes stopped by the iteration cap
+// fpm(46) (inexact solves) to *capped.  The count of lanes still iterating is
+// read back every kCheckSteps steps; lanes that stop in between idle.
+constexpr int kCheckSteps = 8;
+
 int h_filter_pass(HBufs& B, const HMat& A, const HMat& Bm, bool hasB, int m, int ne, int rii, const double2* b,
-                  const double2* X, int maxit, double tol, long long* iters, cudaStream_t s)
+                  const double2* X, int maxit, double tol, long long* iters, long long* capped, cudaStream_t s)
 {
     HArgs a = B.fa;
     a.n = A.n;
@@ -152,15 +156,18 @@ int h_filter_pass(HBufs& B, const HMat& A, const HMat& Bm, bool hasB, int m, int
         while (nbp < a.nb) nbp <<= 1;
         a.L = (long long)m * nbp;
         HCK(launch_h_init(a, B.fp64, b, X, B.zw + 4 * e0, B.lam, rii, ne, B.zw, e0 == 0 ? 1 : 0, s));
+        HCK(cudaMemsetAsync(a.nactive + 1, 0, sizeof(int), s));
         int it = 0;
         while (it < maxit) {
             HCK(launch_h_step(a, B.fp64, maxit, s));
             ++it;
-            HCK(cudaMemcpyAsync(B.nactive_host, a.nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
+            if (it % kCheckSteps != 0 && it < maxit) continue;
+            HCK(cudaMemcpyAsync(B.nactive_host, a.nactive, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
             HCK(cudaStreamSynchronize(s));
-            if (*B.nactive_host == 0) break;
+            if (B.nactive_host[0] == 0) break;
         }
         *iters += it;
+        *capped += B.nactive_host[1];
     }
     return 0;
 }
@@ -169,68 +176,100 @@ int h_filter_pass(HBufs& B, const HMat& A, const HMat& Bm, bool hasB, int m, int
 
 namespace {
 
+// Device memory of one solve, carved from one workspace (256-byte aligned
+// pieces): block vectors, reduced matrices, BiCG lane vectors and state, and
+// the filter-precision copies of the values in mixed precision.
+struct HPlan {
+    int n = 0, m0 = 0, ne = 0, nb = 0, nbp = 0, ks = 1, nnz_a = 0, nnz_b = 0;
+    long long Lmax = 0;
+    bool fp64 = false, hasB = false;
+};
+
+HPlan h_plan(int n, int nnz_a, int nnz_b, int m0, const int* fpm)
+{
+    HPlan P;
+    P.n = n;
+    P.m0 = m0;
+    P.ne = fpm[1];
+    P.nnz_a = nnz_a;
+    P.nnz_b = nnz_b;
+    P.hasB = nnz_b > 0;
+    P.fp64 = fpm[41] == 0;
+    P.nb = std::min(P.ne, fpm[49] > 0 ? std::min(fpm[49], 32) : 16);
+    P.nbp = 1;
+    while (P.nbp < P.nb) P.nbp <<= 1;
+    P.Lmax = (long long)m0 * P.nbp;
+    h_gram_partial(n, m0, &P.ks);
+    return P;
+}
+
+struct HCarve {
+    char* base;
+    size_t off = 0;
+    template <typename T>
+    T* take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? (T*)(base + off) : nullptr;
+        off += std::max<size_t>(count, 1) * sizeof(T);
+        return p;
+    }
+};
+
+// Carves B (and the filter-precision value copies af, bf) from base; with
+// base == nullptr only measures.  Returns the bytes needed.
+size_t h_carve(const HPlan& P, void* base, HBufs& B, float2** af, float2** bf)
+{
+    HCarve c{(char*)base};
+    const size_t blk = (size_t)P.n * P.m0, mm = (size_t)P.m0 * P.m0;
+    const size_t vb = P.fp64 ? sizeof(double2) : sizeof(float2);
+    B.Y = c.take<double2>(blk);
+    B.Q = c.take<double2>(blk);
+    B.T = c.take<double2>(blk);
+    B.X = c.take<double2>(blk);
+    B.T2 = P.hasB ? c.take<double2>(blk) : nullptr;
+    B.Aq = c.take<double2>(mm);
+    B.Bq = c.take<double2>(mm);
+    B.Vr = c.take<double2>(mm);
+    B.gpart = c.take<double2>(h_gram_partial(P.n, P.m0, nullptr));
+    B.lam = c.take<double>(P.m0);
+    B.res = c.take<double>(P.m0);
+    B.rpart = c.take<double>(h_resid_partial(P.n, P.m0));
+    B.zw = c.take<double>(4 * (size_t)P.ne);
+    B.mk = c.take<int>(1);
+    B.status = c.take<int>(2);
+    B.nactive = c.take<int>(2);
+    B.perm = c.take<int>(P.m0);
+    B.red = c.take<char>(h_reduced_work_bytes(P.m0));
+    void** fv[6] = {&B.fa.r, &B.fa.rh, &B.fa.p, &B.fa.ph, &B.fa.q, &B.fa.qh};
+    for (void** v : fv) *v = c.take<char>((size_t)P.n * P.Lmax * vb);
+    B.fa.st = c.take<HLane>(P.Lmax);
+    B.fa.part = c.take<double2>((size_t)row_blocks(P.n) * 2 * P.Lmax);
+    *af = P.fp64 ? nullptr : c.take<float2>(P.nnz_a);
+    *bf = (P.fp64 || !P.hasB) ? nullptr : c.take<float2>(P.nnz_b);
+    return c.off + 256;
+}
+
 // The FEAST loop on device CSR data; x_dev: caller's column-major n x m0
-// complex block (start subspace in, Ritz vectors out).
+// complex block (start subspace in, Ritz vectors out).  B: carved buffers.
 int h_solve(const HMat& A, const HMat& Bm, bool hasB, int* fpm, double emin, double emax, int* m0io, double* e_host,
-            double2* x_dev, int* M_out, double* res_host, double* epsout, int* loop_out, cudaStream_t s)
+            double2* x_dev, int* M_out, double* res_host, double* epsout, int* loop_out, HBufs& B, cudaStream_t s)
 {
     const int n = A.n, m0 = *m0io, ne = fpm[1];
-    const bool fp64 = fpm[41] == 0;
     const double alpha = std::max(std::fabs(emin), std::fabs(emax));
     const double eps = std::pow(10.0, -fpm[2]);
     const double tol = std::pow(10.0, -fpm[44]);
     const int maxit = fpm[45], maxloop = fpm[3];
     std::vector<double> zw;
     contour_nodes(fpm[15], ne, emin, emax, fpm[17] / 100.0, zw);
-    HDevMem dm;
-    HBufs B{};
-    B.fp64 = fp64;
-    B.nb = std::min(ne, fpm[49] > 0 ? std::min(fpm[49], 32) : 16);
-    int nbp = 1;
-    while (nbp < B.nb) nbp <<= 1;
-    const long long Lmax = (long long)m0 * nbp;
-    const size_t blk = (size_t)n * m0, mm = (size_t)m0 * m0;
-    const size_t vb = fp64 ? sizeof(double2) : sizeof(float2);
-    HCK(dm.alloc(&B.Y, blk));
-    HCK(dm.alloc(&B.Q, blk));
-    HCK(dm.alloc(&B.T, blk));
-    HCK(dm.alloc(&B.X, blk));
-    if (hasB) HCK(dm.alloc(&B.T2, blk));
-    HCK(dm.alloc(&B.Aq, mm));
-    HCK(dm.alloc(&B.Bq, mm));
-    HCK(dm.alloc(&B.Vr, mm));
-    HCK(dm.alloc(&B.gpart, h_gram_partial(n, m0, &B.ks)));
-    HCK(dm.alloc(&B.lam, m0));
-    HCK(dm.alloc(&B.res, m0));
-    HCK(dm.alloc(&B.rpart, h_resid_partial(n, m0)));
-    HCK(dm.alloc(&B.zw, 4 * (size_t)ne));
-    HCK(dm.alloc(&B.mk, 1));
-    HCK(dm.alloc(&B.status, 2));
-    HCK(dm.alloc(&B.nactive, 1));
-    HCK(dm.alloc(&B.perm, m0));
-    HCK(dm.alloc((char**)&B.red, h_reduced_work_bytes(m0)));
-    char* fv[6];
-    for (int k = 0; k < 6; ++k) HCK(dm.alloc(&fv[k], (size_t)n * Lmax * vb));
-    B.fa.r = fv[0];
-    B.fa.rh = fv[1];
-    B.fa.p = fv[2];
-    B.fa.ph = fv[3];
-    B.fa.q = fv[4];
-    B.fa.qh = fv[5];
-    HCK(dm.alloc(&B.fa.st, Lmax));
-    HCK(dm.alloc(&B.fa.part, (size_t)row_blocks(n) * 2 * Lmax));
+    const size_t blk = (size_t)n * m0;
     B.fa.Q = B.Q;
     B.fa.nactive = B.nactive;
-    int* pinned = nullptr;
-    HCK(cudaMallocHost(&pinned, sizeof(int)));
-    struct PinFree {
-        int* p;
-        ~PinFree() { cudaFreeHost(p); }
-    } pin_free{pinned};
-    B.nactive_host = pinned;
+    int nact_host[2] = {0, 0};
+    B.nactive_host = nact_host;
     HCK(cudaMemcpyAsync(B.zw, zw.data(), sizeof(double) * zw.size(), cudaMemcpyHostToDevice, s));
     HCK(cudaMemsetAsync(B.lam, 0, sizeof(double) * m0, s));
-    long long iters = 0;
+    long long iters = 0, capped = 0;
     int st = 0;
     if (fpm[4] == 1) {
         // a given subspace is tested by Rayleigh-Ritz before any filtering
@@ -247,7 +286,7 @@ int h_solve(const HMat& A, const HMat& Bm, bool hasB, int* fpm, double emin, dou
             HCK(launch_h_spmm(n, m0, Bm.ia, Bm.ja, Bm.v, B.Y, B.T, s));
             b = B.T;
         }
-        if ((st = h_filter_pass(B, A, Bm, hasB, m0, ne, 0, b, nullptr, maxit, tol, &iters, s))) return st;
+        if ((st = h_filter_pass(B, A, Bm, hasB, m0, ne, 0, b, nullptr, maxit, tol, &iters, &capped, s))) return st;
     }
     std::vector<double> lam(m0), res(m0);
     int mk = m0, M = 0, info = 0, k = 0, stat[2] = {0, 0};
@@ -290,12 +329,18 @@ int h_solve(const HMat& A, const HMat& Bm, bool hasB, int* fpm, double emin, dou
         snprintf(line, sizeof(line), "%3d  %6d      %.16E      %.16E      %.16E\n", k, M, trace, eo,
                  M ? maxres : 1.0);
         feast_log(fpm[0], line);
+        if (capped) {
+            snprintf(line, sizeof(line), "    %lld BiCG lanes stopped at the iteration cap fpm(46) = %d\n", capped,
+                     maxit);
+            feast_log(fpm[0], line);
+            capped = 0;
+        }
         const bool conv = M >= 1 && (fpm[5] == 1 ? maxres < eps : (k >= 1 && eo < eps));
         if (conv) { info = 0; break; }
         if (M == 0 && k >= 1) { info = 1; break; }
         if (k >= maxloop) { info = 2; break; }
         // residual-inverse pass on (X, Lambda), R = A X - B X Lambda in Y
-        if ((st = h_filter_pass(B, A, Bm, hasB, m0, ne, 1, B.Y, B.X, maxit, tol, &iters, s))) return st;
+        if ((st = h_filter_pass(B, A, Bm, hasB, m0, ne, 1, B.Y, B.X, maxit, tol, &iters, &capped, s))) return st;
     }
     fpm[59] = (int)std::min<long long>(iters, 2147483647LL);
     if (info == 0 && M >= mk) info = 3;
@@ -328,10 +373,18 @@ int h_solve(const HMat& A, const HMat& Bm, bool hasB, int* fpm, double emin, dou
 }  // namespace
 
 // ---------------------------------------------------------------- entry points
+extern "C" size_t feast_hcsr_workspace_bytes(int n, int nnz_a, int nnz_b, int m0, const int* fpm)
+{
+    if (n <= 0 || m0 <= 0 || !fpm) return 0;
+    HBufs B{};
+    float2 *af = nullptr, *bf = nullptr;
+    return h_carve(h_plan(n, nnz_a, nnz_b, m0, fpm), nullptr, B, &af, &bf);
+}
+
 static int h_dev_entry(int n, int nnz_a, const int* d_ia, const int* d_ja, const double* d_a, int nnz_b,
                        const int* d_ib, const int* d_jb, const double* d_b, int* fpm, double emin, double emax,
                        int* m0, double* e, double* d_x, int* m, double* res, double* epsout, int* loop, int* info,
-                       cudaStream_t s)
+                       void* work, size_t work_bytes, cudaStream_t s)
 {
     auto ret = [&](int v) { if (info) *info = v; return v; };
     if (n <= 0) return ret(202);
@@ -352,9 +405,23 @@ static int h_dev_entry(int n, int nnz_a, const int* d_ia, const int* d_ja, const
     if (!res) return ret(-116);
     if (!epsout) return ret(-117);
     if (!loop) return ret(-118);
+    const HPlan P = h_plan(n, nnz_a, hasB ? std::max(nnz_b, 1) : 0, *m0, fpm);
+    HBufs B{};
+    float2 *af = nullptr, *bf = nullptr;
+    const size_t need = h_carve(P, nullptr, B, &af, &bf);
+    if (work && work_bytes < need) return ret(-120);
     clear_last_error();
-    const bool fp64 = fpm[41] == 0;
     HDevMem dm;
+    if (!work) {  // no caller workspace: the library allocates it for this call
+        char* w = nullptr;
+        const cudaError_t ce = dm.alloc(&w, need);
+        if (ce != cudaSuccess) return ret(cuda_error(ce, "workspace"));
+        work = w;
+    }
+    h_carve(P, work, B, &af, &bf);
+    B.fp64 = P.fp64;
+    B.nb = P.nb;
+    B.ks = P.ks;
     HMat A, Bm;
     A.n = n;
     A.nnz = nnz_a;
@@ -370,28 +437,26 @@ static int h_dev_entry(int n, int nnz_a, const int* d_ia, const int* d_ja, const
         Bm.v = (const double2*)d_b;
         Bm.vf = d_b;
     }
-    if (!fp64) {  // complex float copies of the values for the filter
-        float2 *af = nullptr, *bf = nullptr;
-        cudaError_t ce = dm.alloc(&af, (size_t)nnz_a);
-        if (ce != cudaSuccess) return ret(cuda_error(ce, "alloc"));
-        if ((ce = launch_h_cast(A.v, af, nnz_a, false, s)) != cudaSuccess) return ret(cuda_error(ce, "cast"));
+    if (!P.fp64) {  // complex float copies of the values for the filter
+        cudaError_t ce = launch_h_cast(A.v, af, nnz_a, false, s);
+        if (ce != cudaSuccess) return ret(cuda_error(ce, "cast"));
         A.vf = af;
         if (hasB) {
-            if ((ce = dm.alloc(&bf, (size_t)nnz_b)) != cudaSuccess) return ret(cuda_error(ce, "alloc"));
             if ((ce = launch_h_cast(Bm.v, bf, nnz_b, false, s)) != cudaSuccess) return ret(cuda_error(ce, "cast"));
             Bm.vf = bf;
         }
     }
-    return ret(h_solve(A, Bm, hasB, fpm, emin, emax, m0, e, (double2*)d_x, m, res, epsout, loop, s));
+    return ret(h_solve(A, Bm, hasB, fpm, emin, emax, m0, e, (double2*)d_x, m, res, epsout, loop, B, s));
 }
 
 extern "C" int feast_hcsr_solve_dev(int n, int nnz_a, const int* d_ia, const int* d_ja, const double* d_a, int nnz_b,
                                     const int* d_ib, const int* d_jb, const double* d_b, int* fpm, double emin,
                                     double emax, int* m0, double* e, double* d_x, int* m, double* res,
-                                    double* epsout, int* loop, int* info, void* stream)
+                                    double* epsout, int* loop, int* info, void* d_work, size_t work_bytes,
+                                    void* stream)
 {
     return h_dev_entry(n, nnz_a, d_ia, d_ja, d_a, nnz_b, d_ib, d_jb, d_b, fpm, emin, emax, m0, e, d_x, m, res, epsout,
-                       loop, info, (cudaStream_t)stream);
+                       loop, info, d_work, work_bytes, (cudaStream_t)stream);
 }
 
 // Validates a host complex CSR (base ia[0] = 0 or 1; values interleaved
@@ -431,6 +496,31 @@ static int host_hcsr(char uplo, int n, const double* v, const int* ia, const int
             ov.push_back(pr.second);
         }
         oia[i + 1] = (int)oja.size();
+    }
+    // The conjugate-shift shadow system assumes K^H = conj(z) B - A, i.e. a
+    // Hermitian matrix: a real diagonal and, in full storage, a_ji = conj(a_ij)
+    // (relative tolerance 1e-12, duplicate entries summed).  A mirrored
+    // triangle is Hermitian off the diagonal by construction.
+    auto entry = [&](int i, int j) {  // summed value of (i, j); zero if absent
+        const auto first = std::lower_bound(oja.begin() + oia[i], oja.begin() + oia[i + 1], j);
+        double2 sum = make_double2(0.0, 0.0);
+        for (auto it = first; it != oja.begin() + oia[i + 1] && *it == j; ++it) {
+            sum.x += ov[it - oja.begin()].x;
+            sum.y += ov[it - oja.begin()].y;
+        }
+        return sum;
+    };
+    for (int i = 0; i < n; ++i) {
+        const double2 d = entry(i, i);
+        if (std::fabs(d.y) > 16.0 * 2.220446049250313e-16 * std::fabs(d.x)) return -(100 + arg0);
+        if (uplo != 'F') continue;
+        for (int p = oia[i]; p < oia[i + 1]; ++p) {
+            const int j = oja[p];
+            if (j == i) continue;
+            const double2 a = entry(i, j), b = entry(j, i);
+            const double diff = std::hypot(a.x - b.x, a.y + b.y);
+            if (diff > 1e-12 * (std::hypot(a.x, a.y) + std::hypot(b.x, b.y))) return -(100 + arg0);
+        }
     }
     return 0;
 }
@@ -488,7 +578,8 @@ extern "C" int feast_hcsr_solve(char uplo, int n, const double* a, const int* ia
     }
     if (fpm[4] == 1) HK2(cudaMemcpy(d_x, x, sizeof(double2) * (size_t)n * mm0, cudaMemcpyHostToDevice));
     inf = h_dev_entry(n, (int)aja.size(), d_ia, d_ja, (const double*)d_a, hasB ? (int)bja.size() : 0, d_ib, d_jb,
-                      (const double*)d_b, fpm, emin, emax, m0, e, (double*)d_x, m, res, epsout, loop, info, nullptr);
+                      (const double*)d_b, fpm, emin, emax, m0, e, (double*)d_x, m, res, epsout, loop, info, nullptr, 0,
+                      nullptr);
     if (inf >= 0 || inf == -3)
         HK2(cudaMemcpy(x, d_x, sizeof(double2) * (size_t)n * mm0, cudaMemcpyDeviceToHost));
 #undef HK2

@@ -18,7 +18,7 @@ struct HLane {
     double rhn2;    // |rh|^2 of the last iteration
     int active;     // 1 while the lane iterates
     int iters;      // iterations taken
-    int status;     // 0 iterating, 1 converged, 2 breakdown, 3 inactive column
+    int status;     // 0 iterating, 1 converged, 2 breakdown, 3 inactive column, 4 iteration cap
 };
 
 struct HArgs {
@@ -42,7 +42,8 @@ struct HArgs {
     double2* part;  // partial sums [nrbk][2][L]
     double2* Q;     // FP64 quadrature block, n x m complex (row-major)
     double tol2;    // squared relative BiCG tolerance
-    int* nactive;   // lanes still iterating after the last finish_b (device)
+    int* nactive;   // [0]: lanes still iterating after the last finish_b; [1]: lanes stopped by
+                    // the iteration cap since the counter was last cleared (device)
 };
 
 constexpr int kRowsPerItem = 256;

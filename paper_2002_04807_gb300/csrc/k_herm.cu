@@ -50,21 +50,38 @@ template <typename V> __device__ __forceinline__ V from_d2(double2 v);
 template <> __device__ __forceinline__ float2 from_d2<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
 template <> __device__ __forceinline__ double2 from_d2<double2>(double2 v) { return v; }
 
-// y = sum_k a_k x[j_k] over the CSR row (complex values a, complex x with row stride L).
+// y = sum_k a_k x[j_k], yh = sum_k a_k xh[j_k] over the CSR row (complex values
+// a, complex x with row stride L), four entries at a time: their column indices
+// first, then all eight gathers, so they are in flight together.
 template <typename T>
 __device__ __forceinline__ void row_pair(const int* __restrict__ ia, const int* __restrict__ ja,
                                          const c2_t<T>* __restrict__ av, int i, const c2_t<T>* __restrict__ x,
                                          const c2_t<T>* __restrict__ xh, long long L, c2_t<T>& y, c2_t<T>& yh)
 {
     using V = c2_t<T>;
+    constexpr int U = 4;
     y = cmk<V>(T(0), T(0));
     yh = y;
     const int s = __ldg(ia + i), e = __ldg(ia + i + 1);
-    for (int k = s; k < e; ++k) {
-        const long long j = __ldg(ja + k);
-        const V a = av[k];
-        y = cfma(a, x[j * L], y);
-        yh = cfma(a, xh[j * L], yh);
+    for (int k = s; k < e; k += U) {
+        long long j[U];
+        V a[U], xv[U], xhv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool ok = k + u < e;
+            j[u] = ok ? __ldg(ja + k + u) : -1;
+            a[u] = ok ? av[k + u] : cmk<V>(T(0), T(0));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            xv[u] = j[u] >= 0 ? __ldg(x + j[u] * L) : cmk<V>(T(0), T(0));
+            xhv[u] = j[u] >= 0 ? __ldg(xh + j[u] * L) : cmk<V>(T(0), T(0));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            y = cfma(a[u], xv[u], y);
+            yh = cfma(a[u], xhv[u], yh);
+        }
     }
 }
 
@@ -180,8 +197,8 @@ __global__ void __launch_bounds__(kT) h_norms(HArgs a)
     const long long nch = (a.L + 31) / 32, items = (long long)nrbk * nch;
     const V* r = (const V*)a.r;
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
-        const int rb = (int)(it / nch);
-        const long long l = (it % nch) * 32 + lane;
+        const int rb = (int)(it % nrbk);  // lane chunk major: concurrent items sweep one chunk's rows
+        const long long l = (it / nrbk) * 32 + lane;
         const bool ok = l < a.L;
         double acc = 0.0;
         if (ok && a.st[l].active) {
@@ -213,8 +230,8 @@ __global__ void __launch_bounds__(kT) h_step_a(HArgs a)
     const V* av = (const V*)a.av;
     const V* bv = (const V*)a.bv;
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
-        const int rb = (int)(it / nch);
-        const long long l = (it % nch) * 32 + lane;
+        const int rb = (int)(it % nrbk);  // lane chunk major: concurrent items sweep one chunk's rows
+        const long long l = (it / nrbk) * 32 + lane;
         const bool ok = l < L;
         double2 acc = make_double2(0.0, 0.0);
         if (ok && a.st[l].active) {
@@ -277,8 +294,8 @@ __global__ void __launch_bounds__(kT) h_step_b(HArgs a)
     const V* q = (const V*)a.q;
     const V* qh = (const V*)a.qh;
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
-        const int rb = (int)(it / nch);
-        const long long l = (it % nch) * 32 + lane;
+        const int rb = (int)(it % nrbk);  // lane chunk major: concurrent items sweep one chunk's rows
+        const long long l = (it / nrbk) * 32 + lane;
         const bool ok = l < L;
         const bool act = ok && a.st[l].active;
         const int e = (int)(l % nbp), j = (int)(l / nbp);
@@ -408,8 +425,10 @@ __global__ void __launch_bounds__(kT) h_finish_b(HArgs a, int maxit)
         } else if (!isfinite(nr.x) || !isfinite(nr.y) || !(rn.x * rn.x + rn.y * rn.y > 0.0) || !(den > 0.0)) {
             s.active = 0;
             s.status = 2;
-        } else if (s.iters >= maxit) {
+        } else if (s.iters >= maxit) {  // stopped with an inexact solve
             s.active = 0;
+            s.status = 4;
+            atomicAdd(a.nactive + 1, 1);
         } else {  // beta = rho_new / rho
             s.beta = make_double2((rn.x * s.rho.x + rn.y * s.rho.y) / den, (rn.y * s.rho.x - rn.x * s.rho.y) / den);
             s.rho = rn;

@@ -11,11 +11,7 @@ import torch
 import feast_workloads as fw
 import oracle as O
 
-# The Hermitian path had not run on a GPU when these tests were written: a
-# failure is reported (xfailed) without stopping the rest of the GPU suite, a
-# pass shows as xpassed.  The mark goes once the file has passed on a GPU.
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.xfail(reason="first GPU run of the complex Hermitian path", strict=False)]
+pytestmark = pytest.mark.gpu
 EIG_TOL, RES_TOL, ANG_TOL = 1e-10, 1e-10, 1e-8
 
 
@@ -182,6 +178,20 @@ def test_device_entry_point(pkg):
     db = B.to_dense()
     R = A.to_dense() @ X - db @ X * r.E[:15]
     assert np.abs(R).max() < 1e-9 * np.abs(lam).max()
+    # caller workspace: the same kernels in the same order give the same result;
+    # one byte short is rejected before any device work
+    f = fpm_for(pkg, 1)
+    need = pkg.feast_hcsr_workspace_bytes(n, A.nnz, B.nnz, m0, f)
+    work = torch.empty(need, dtype=torch.uint8, device=dev)
+    x2 = torch.as_tensor(np.ascontiguousarray(y0.T)).to(dev)
+    args = (n, t(A.indptr, torch.int32), t(A.indices, torch.int32), t(A.data, torch.complex128))
+    kw = dict(ib=t(B.indptr, torch.int32), jb=t(B.indices, torch.int32), b=t(B.data, torch.complex128), emin=emin,
+              emax=emax, m0=m0)
+    r2 = pkg.feast_hcsr_solve_dev(*args, fpm=f.copy(), x=x2, work=work, **kw)
+    assert r2.info == 0 and np.array_equal(r2.E, r.E)
+    assert torch.equal(x2, x)
+    short = pkg.feast_hcsr_solve_dev(*args, fpm=f.copy(), x=x2.clone(), work=work[: need - 1], **kw)
+    assert short.info == -120
 
 
 def test_gauge_workload_matches_real_spectrum(pkg):
