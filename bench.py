@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--rows-per-item", type=int, default=0, help="fpm(51): rows per work item of the COCG gather "
+                                                                    "step (0: the library's choice)")
     return ap.parse_args()
 
 
@@ -78,12 +80,16 @@ def config_dict(p, extra=None):
     return d
 
 
+ROWS_PER_ITEM = 0
+
+
 def fpm_for(pkg, p, mixed, profile):
     f = pkg.feast_init()
     f[1], f[2], f[3], f[4], f[17] = p.ne, 10, 40, 1, p.ratio
     f[41] = 1 if mixed else 0
     f[44], f[45] = 2, 80
     f[49] = 1  # one contour node per batch: groups of a fast node stop early
+    f[50] = ROWS_PER_ITEM
     f[52] = 1 if profile else 0
     return f
 
@@ -185,34 +191,44 @@ def throughput(conv_per_rank, ms_per_rank, ws):
 
 
 # ---------------------------------------------------------------- CPU baseline (oracle)
-def cpu_baseline(p, seconds, loops_hint):
-    """The FP64 oracle on the host cores, on a bounded sample of the same
-    workload: COCG shifted solves (to 1e-13, the oracle's iterative mode) of
-    `cores` start-block columns at the hardest and at a middle contour node of
-    the full N, extrapolated to all Ne x M0 solves of every filter pass of a
-    full solve (passes = loops_hint + 1).  Returns (eigenpairs/s, sample text,
-    cores)."""
-    import oracle as O
+FULL_SOLVE_RECORD = os.path.join(ROOT, "oracle", "full_solve_laplace3d_64.json")
+COUNT_RECORD = os.path.join(ROOT, "tests", "golden", "laplace3d_64_count.json")
 
-    cores = O.num_threads()
-    z, _ = O.contour_gauss(p.ne, p.emin, p.emax, p.ratio / 100.0)
-    y = p.y0()
-    nodes = [int(np.argmin(z.imag)), p.ne // 2]
-    per = []
-    t_all = time.time()
-    for e in nodes:
-        cols = y[:, :cores]
-        t0 = time.time()
-        O.shifted_solve(p.A, None, z[e], cols, method="cocg", tol=1e-13)
-        per.append((time.time() - t0) / cols.shape[1] * cores)  # wall s per `cores` columns
-        if time.time() - t_all > seconds:
-            break
-    t_cols = float(np.mean(per)) / cores  # wall seconds per (node, column) with all cores busy
-    passes = loops_hint + 1
-    t_full = t_cols * p.ne * p.m0 * passes
-    M_expected = None
-    return t_full, cores, (f"COCG solves of {cores} columns at node(s) {nodes} of N={p.n}, "
-                           f"extrapolated to {p.ne}x{p.m0} solves x {passes} filter passes"), M_expected
+
+def oracle_solve_shape():
+    """Filter passes and eigenvalue count of the oracle's own full solve of the
+    64^3 workload: from the recorded full oracle run (oracle/
+    full_solve_laplace3d_64.py) and the Sylvester-inertia count (tests/golden/
+    make_laplace3d_64_count.py).  Returns (passes, M, record or None)."""
+    rec = None
+    if os.path.exists(FULL_SOLVE_RECORD):
+        rec = json.load(open(FULL_SOLVE_RECORD))
+    M = None
+    if os.path.exists(COUNT_RECORD):
+        M = int(json.load(open(COUNT_RECORD))["count_in_interval"])
+    if rec is not None:
+        return int(rec["filter_passes"]), int(M if M is not None else rec["M"]), rec
+    return 7, (M if M is not None else 100), None
+
+
+def cpu_baseline(p, seconds, passes, M):
+    """The FP64 oracle on the host cores, on a bounded sample of the same
+    workload (oracle/cpu_sample.py: COCG shifted solves of `cores` start-block
+    columns at two contour nodes, extrapolated to every solve of the oracle's
+    own full solve, `passes` filter passes), for its M eigenpairs; scaled by
+    the recorded ratio of a full oracle solve to the same sample on the same
+    kind of host when that record exists.  Returns (eigenpairs/s, cores, text)."""
+    import oracle as O  # noqa: F401
+    from oracle.cpu_sample import sample_solve_seconds
+
+    t_full, cores, text = sample_solve_seconds(p, seconds, passes)
+    _, _, rec = oracle_solve_shape()
+    cal = 1.0
+    if rec is not None and rec.get("calibration"):
+        cal = float(rec["calibration"])
+        text += (f"; x {cal:.3f}, the ratio of a full oracle solve ({rec['wall_s']:.0f} s on {rec['cores']} "
+                 f"{rec['host']} cores, {rec['filter_passes']} passes) to this sample's estimate on that host")
+    return M / (t_full * cal), cores, text + f"; M = {M} (inertia count)"
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -234,7 +250,8 @@ def run_gpu(args):
     y0 = torch.as_tensor(np.ascontiguousarray(p.y0().T)).to(dev)  # column-major n x m0
     x = torch.empty_like(y0)
     stream = torch.cuda.Stream(device=dev)
-    f_mixed = fpm_for(pkg, p, True, True)
+    f_mixed = fpm_for(pkg, p, True, False)  # timed solves: no per-launch event profiling
+    f_prof = fpm_for(pkg, p, True, True)  # one extra solve after the timed region, for the roofline
     work = torch.empty(pkg.feast_scsr_workspace_bytes(p.n, p.A.nnz, 0, p.m0, f_mixed), dtype=torch.uint8,
                        device=dev)
 
@@ -257,25 +274,23 @@ def run_gpu(args):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         ev0.record(stream)
-        conv_total, prof_tot, loops = 0, None, []
+        conv_total, n_launch, loops = 0, 0, []
         t_host0 = time.time()
         for _ in range(args.steps):
             r, conv = solve(f_mixed)
             conv_total += conv
             loops.append(r.loop)
-            pr = pkg.feast_last_profile()
-            if prof_tot is None:
-                prof_tot = dict(pr)
-            else:
-                for k in ("cocg_a_ms", "cocg_b_ms", "cocg_a_launches", "cocg_b_launches", "group_iterations",
-                          "filter_ms", "project_ms", "reduce_ms", "ritz_ms", "launches"):
-                    prof_tot[k] += pr[k]
+            n_launch += int(pkg.feast_last_profile()["launches"])
         ev1.record(stream)
         torch.cuda.synchronize()
         host_s = time.time() - t_host0
         ms = ev0.elapsed_time(ev1)
         clk = clocks.stop()
         barrier(ws)
+        # per-kernel CUDA-event timings from one more solve of the same problem
+        rp, _ = solve(f_prof)
+        prof_tot = dict(pkg.feast_last_profile())
+        torch.cuda.synchronize()
     ms_max = max_over_ranks(ms, ws)
     value = throughput(conv_total, ms, ws)
     M = r.M
@@ -305,7 +320,7 @@ def run_gpu(args):
                 "M": r64.M, "mixed_over_fp64": value / v64,
                 "max_rel_eig_diff_vs_mixed": float(np.max(np.abs(r64.E[:M] - r.E[:M]) / np.abs(r.E[:M])))}
 
-    # roofline of the dominant kernel from the per-launch events of the timed steps
+    # roofline of the dominant kernel from the per-launch events of the profiled solve
     pr = prof_tot
     n, W, mt, sc, G = pr["n"], pr["W"], pr["mt"], pr["complex_bytes"], pr["groups"]
     nbp = W / mt  # node lanes per column in a tile
@@ -342,7 +357,9 @@ def run_gpu(args):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "peak_source": peak_src,
                 "unit": "GB/s", "frac": ach / peak, "traffic": traffic,
                 "cocg_step_a_gbs": gbs_a, "cocg_step_b_gbs": gbs_b,
-                "cocg_share_of_step": (pr["cocg_a_ms"] + pr["cocg_b_ms"]) / ms}
+                "cocg_share_of_step": (pr["cocg_a_ms"] + pr["cocg_b_ms"]) / (ms / args.steps),
+                "timing": "CUDA events around every COCG launch of one extra solve after the timed region "
+                          f"({int(pr['cocg_a_launches'])} step-A launches, {pr['filter_ms']:.0f} ms of filter)"}
 
     # end to end through the host C ABI (pinned host buffers, copies inside the timed region)
     e2e = None
@@ -375,8 +392,9 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        t_full, cores, sample, _ = cpu_baseline(p, args.cpu_sample_seconds, int(np.median(loops)))
-        cpu = {"value": M / t_full, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        passes, Mo, _ = oracle_solve_shape()
+        v_cpu, cores, sample = cpu_baseline(p, args.cpu_sample_seconds, passes, Mo)
+        cpu = {"value": v_cpu, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -385,10 +403,9 @@ def run_gpu(args):
                "data": "synthetic (seeded generator, no dataset)",
                "config": config_dict(p, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                                          "M_found": M, "loops": loops, "precision": "mixed fpm(42)=1"}),
-               "e2e": e2e, "gpu_launches": int(pr["launches"]), "roofline": roofline, "cpu_baseline": cpu,
+               "e2e": e2e, "gpu_launches": n_launch, "roofline": roofline, "cpu_baseline": cpu,
                "fp64": fp64, "clocks": clk,
-               "phases_ms_per_step": {k: pr[k] / args.steps for k in ("filter_ms", "project_ms", "reduce_ms",
-                                                                       "ritz_ms")},
+               "phases_ms_per_solve": {k: pr[k] for k in ("filter_ms", "project_ms", "reduce_ms", "ritz_ms")},
                "host_wall_s": host_s}
         print(json.dumps(out))
     if ws > 1:
@@ -407,21 +424,21 @@ def run_reference(args):
 
     p = workload(args.side)
     O.build()
-    loops_hint = 6
+    passes, Mo, _ = oracle_solve_shape()
     for _ in range(args.warmup):
-        cpu_baseline(p, min(args.cpu_sample_seconds, 5.0), loops_hint)
+        cpu_baseline(p, min(args.cpu_sample_seconds, 5.0), passes, Mo)
     vals, samples = [], ""
     t0 = time.time()
     for _ in range(args.steps):
-        t_full, cores, samples, _ = cpu_baseline(p, args.cpu_sample_seconds / max(1, args.steps), loops_hint)
-        vals.append(100.0 / t_full)
+        v, cores, samples = cpu_baseline(p, args.cpu_sample_seconds / max(1, args.steps), passes, Mo)
+        vals.append(v)
     wall = time.time() - t0
     value = float(np.mean(vals))
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded generator, no dataset)", "impl": "reference",
-           "config": config_dict(p, {"precision": "FP64 oracle", "M_assumed": 100}),
+           "config": config_dict(p, {"precision": "FP64 oracle", "M": Mo, "filter_passes": passes}),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": samples},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -742,6 +759,7 @@ def run_hermitian(args):
 
 if __name__ == "__main__":
     a = parse()
+    ROWS_PER_ITEM = a.rows_per_item
     if a.side is None:
         a.side = 96 if a.workload == "stencil27" else 64
     if a.impl == "reference" and a.workload != "laplace3d":
