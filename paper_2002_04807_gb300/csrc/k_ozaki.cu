@@ -16,9 +16,10 @@
 //     2^(-7 kSlices) relative to 2^(E_a + F_b));
 //   * a level L = s + t has at most kSlices pairs of products below 2^14, so
 //     its sum over 128 rows stays below 2^24 and mma.sync accumulates it in
-//     FP32 without any rounding; every 128 rows the level sums are added into
-//     FP64 accumulators with their weights 2^(-7 L), and at the end the column
-//     scales 2^(E_a + F_b) are applied.
+//     FP32 without any rounding; every 128 rows the level sums are folded,
+//     exactly, into two 64-bit integer accumulators (oz_fold), and at the end
+//     they are turned into FP64 once and the column scales 2^(E_a + F_b) are
+//     applied.
 // With kSlices = 8 the kept part is exact and the truncation error of an
 // element is below 2^-55 |2^E_a| |2^F_b| per row: at FP64 level.
 //
@@ -66,9 +67,6 @@ __global__ void __launch_bounds__(256) oz_colexp(int n, int m, const double* __r
     }
 }
 
-// 2^k for -1022 <= k <= 1023
-__device__ __forceinline__ double pow2i(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
-
 // E_c of the splitting from the exponent field: |x| < 2^E_c, clamped so that
 // 2^-E_c is a normal double.
 __device__ __forceinline__ int oz_scale_exp(int field) { return min(max(field - 1022, -1022), 1022); }
@@ -89,6 +87,29 @@ __device__ __forceinline__ void oz_cut(double x, int E, float (&d)[kSlices])
     const float sg = (b >> 63) ? -1.f : 1.f;
 #pragma unroll
     for (int s = 0; s < kSlices; ++s) d[s] = sg * (float)(unsigned)((F >> (49 - 7 * s)) & 127ull);
+}
+
+// Exact folding of the FP32 level sums into two 64-bit integer accumulators.
+// Level l (weight 2^(-7 (l + 2))) holds an integer below 2^24, so
+//   hi = sum_{l < 4} P_l 2^(7 (3 - l))   in units of 2^-35,
+//   lo = sum_{l >= 4} P_l 2^(7 (7 - l))  in units of 2^-63,
+// are below 2^46 per flush and exact, and so are their running sums (below
+// 2^63 for up to 2^17 flushes).  FP64 (scarce on GB300) is used only once per
+// element at the end: value = hi 2^-35 + lo 2^-63.
+__device__ __forceinline__ void oz_fold(float (&P)[kSlices], long long& hi, long long& lo)
+{
+    long long h = 0, l = 0;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) h += (long long)__float2int_rn(P[s]) * (1LL << (7 * (3 - s)));
+#pragma unroll
+    for (int s = 4; s < kSlices; ++s) l += (long long)__float2int_rn(P[s]) * (1LL << (7 * (7 - s)));
+    hi += h;
+    lo += l;
+}
+
+__device__ __forceinline__ double oz_value(long long hi, long long lo, int e)
+{
+    return ldexp(fma((double)hi, 0x1p-35, (double)lo * 0x1p-63), e);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
@@ -154,24 +175,25 @@ __global__ void __launch_bounds__(kOzThreads, 3) gram_oz(int n, int m, const dou
         for (int j = 0; j < 2; ++j)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[l][j][q] = 0.f;
-    double acc64[2][4];
+    long long ahi[2][4], alo[2][4];
 #pragma unroll
     for (int j = 0; j < 2; ++j)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc64[j][q] = 0.0;
+        for (int q = 0; q < 4; ++q) ahi[j][q] = alo[j][q] = 0;
 
     auto flush = [&]() {
 #pragma unroll
-        for (int l = 0; l < kSlices; ++l) {
-            const double w = pow2i(-7 * (l + 2));
+        for (int j = 0; j < 2; ++j)
 #pragma unroll
-            for (int j = 0; j < 2; ++j)
+            for (int q = 0; q < 4; ++q) {
+                float P[kSlices];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    acc64[j][q] = fma((double)acc[l][j][q], w, acc64[j][q]);
+                for (int l = 0; l < kSlices; ++l) {
+                    P[l] = acc[l][j][q];
                     acc[l][j][q] = 0.f;
                 }
-        }
+                oz_fold(P, ahi[j][q], alo[j][q]);
+            }
     };
 
     int nchunk = 0;
@@ -237,7 +259,7 @@ __global__ void __launch_bounds__(kOzThreads, 3) gram_oz(int n, int m, const dou
             const int col = b0 + wc + nt * 8 + 2 * tq + (q & 1);
             if (row < m && col < m) {
                 const int e = oz_scale_exp(__ldg(exX + row)) + oz_scale_exp(__ldg(exY + col));
-                out[(size_t)row * m + col] = ldexp(acc64[nt][q], e);
+                out[(size_t)row * m + col] = oz_value(ahi[nt][q], alo[nt][q], e);
             }
         }
 }
@@ -246,7 +268,7 @@ size_t gram_oz_partial_doubles(int n, int m, int* ksplit_out, long long* rows_pe
 {
     const int nt = (m + kOzTile - 1) / kOzTile;
     const int tiles = nt * (nt + 1) / 2;
-    int ks = (3 * nsm + tiles - 1) / tiles;  // about three CTAs per SM
+    int ks = (3 * nsm) / tiles;  // one wave of three CTAs per SM
     const int maxk = (n + 255) / 256;        // at least 256 rows per split
     if (ks > maxk) ks = maxk;
     if (ks < 1) ks = 1;
@@ -293,8 +315,9 @@ cudaError_t launch_gram_oz(int n, int m, const double* X, const double* Y, doubl
 // integer grid per output element.  V is cut once into slice planes
 // Vs[slice][column][k-pair] (oz_split_cols); A's rows are cut by the CTAs
 // that use them.  A level's sum over 128 contraction steps stays below 2^24
-// (as for the Gram), so the FP32 level sums are folded into FP64 every 128
-// steps of the contraction and scaled by 2^(E_i + F_c) at the end.
+// (as for the Gram), so the FP32 level sums are folded into the integer
+// accumulators every 128 steps of the contraction and scaled by 2^(E_i + F_c)
+// at the end.
 
 // ex[i] = largest biased exponent field over row i of the row-major n x m A.
 __global__ void __launch_bounds__(256) oz_rowexp(int n, int m, const double* __restrict__ A, int* __restrict__ ex)
@@ -365,11 +388,11 @@ __global__ void __launch_bounds__(kOzThreads, 3) gemm_oz(int n, int m, int k, in
         for (int j = 0; j < 2; ++j)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[l][j][q] = 0.f;
-    double acc64[2][4];
+    long long ahi[2][4], alo[2][4];
 #pragma unroll
     for (int j = 0; j < 2; ++j)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc64[j][q] = 0.0;
+        for (int q = 0; q < 4; ++q) ahi[j][q] = alo[j][q] = 0;
     const int jl = lane & 15;
     int rs[4];  // scale exponents E of the loader's rows
 #pragma unroll
@@ -430,16 +453,17 @@ __global__ void __launch_bounds__(kOzThreads, 3) gemm_oz(int n, int m, int k, in
         }
         if (++nchunk == kOzFlushChunks || a0 + 32 >= mp) {
 #pragma unroll
-            for (int l = 0; l < kSlices; ++l) {
-                const double w = pow2i(-7 * (l + 2));
+            for (int j = 0; j < 2; ++j)
 #pragma unroll
-                for (int j = 0; j < 2; ++j)
+                for (int q = 0; q < 4; ++q) {
+                    float P[kSlices];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        acc64[j][q] = fma((double)acc[l][j][q], w, acc64[j][q]);
+                    for (int l = 0; l < kSlices; ++l) {
+                        P[l] = acc[l][j][q];
                         acc[l][j][q] = 0.f;
                     }
-            }
+                    oz_fold(P, ahi[j][q], alo[j][q]);
+                }
             nchunk = 0;
         }
     }
@@ -451,7 +475,7 @@ __global__ void __launch_bounds__(kOzThreads, 3) gemm_oz(int n, int m, int k, in
             const int col = c0 + wc + nt * 8 + 2 * tq + (q & 1);
             if (row < n && col < k) {
                 const int e = oz_scale_exp(__ldg(exA + row)) + oz_scale_exp(__ldg(exV + col));
-                C[(size_t)row * k + col] = ldexp(acc64[nt][q], e);
+                C[(size_t)row * k + col] = oz_value(ahi[nt][q], alo[nt][q], e);
             }
         }
 }
