@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--node-batch", type=int, default=0, help="fpm(50): contour nodes per inner-solver batch "
+                                                                 "(0: the workload's default)")
     ap.add_argument("--rows-per-item", type=int, default=0, help="fpm(51): rows per work item of the COCG gather "
                                                                     "step (0: the library's choice)")
     return ap.parse_args()
@@ -715,7 +717,8 @@ def run_hermitian(args):
 
     def fpm(mixed):
         f = pkg.feast_init()
-        f[1], f[2], f[3], f[4], f[5], f[17], f[41], f[44], f[45], f[49] = p.ne, 10, 40, 1, 1, p.ratio, mixed, 2, 80, 8
+        f[1], f[2], f[3], f[4], f[5], f[17], f[41], f[44], f[45] = p.ne, 10, 40, 1, 1, p.ratio, mixed, 2, 80
+        f[49] = args.node_batch or 1  # one node per batch: the lanes of a fast node stop early
         return f
 
     def solve(mixed):
@@ -750,7 +753,7 @@ def run_hermitian(args):
                "data": "synthetic (seeded generator, no dataset)",
                "config": {"workload": f"laplace3d_7pt_{args.side}^3_potential_U[0,0.5]_seed1_random_gauge_phases",
                           "N": p.n, "nnz": p.A.nnz, "M0": p.m0, "Ne": p.ne, "contour_ratio_pct": p.ratio,
-                          "interval": [p.emin, round(p.emax, 6)], "node_batch": 8,
+                          "interval": [p.emin, round(p.emax, 6)], "node_batch": args.node_batch or 1,
                           "inner_solver": "BiCG with the conjugate-shift shadow system, 1e-2, 80 steps"},
                "M": r.M, "converged_pairs": conv // args.steps, "max_residual": float(r.res[: r.M].max()),
                "bicg_iterations": int(r.fpm[59]), "fp64": fp64}
