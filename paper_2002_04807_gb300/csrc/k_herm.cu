@@ -200,15 +200,15 @@ __global__ void __launch_bounds__(kT) h_norms(HArgs a)
         const int rb = (int)(it % nrbk);  // lane chunk major: concurrent items sweep one chunk's rows
         const long long l = (it / nrbk) * 32 + lane;
         const bool ok = l < a.L;
-        double acc = 0.0;
+        T acc = T(0);  // per-thread partial in the filter precision (GB300's FP64 ALU is slow)
         if (ok && a.st[l].active) {
             const int i1 = min(a.n, (rb + 1) * kRowsPerItem);
             for (int i = rb * kRowsPerItem + warp; i < i1; i += kT / 32) {
-                const double2 v = to_d2(r[(long long)i * a.L + l]);
+                const V v = r[(long long)i * a.L + l];
                 acc = fma(v.x, v.x, fma(v.y, v.y, acc));
             }
         }
-        item_sum(make_double2(acc, 0.0), sh, a.part + ((long long)rb * 2) * a.L + l, ok);
+        item_sum(make_double2((double)acc, 0.0), sh, a.part + ((long long)rb * 2) * a.L + l, ok);
     }
 }
 
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(kT) h_step_a(HArgs a)
         const int rb = (int)(it % nrbk);  // lane chunk major: concurrent items sweep one chunk's rows
         const long long l = (it / nrbk) * 32 + lane;
         const bool ok = l < L;
-        double2 acc = make_double2(0.0, 0.0);
+        V acc = cmk<V>(T(0), T(0));  // per-thread partial of ph^H q, filter precision
         if (ok && a.st[l].active) {
             const HLane& s = a.st[l];
             const bool first = s.iters == 0;
@@ -268,12 +268,12 @@ __global__ void __launch_bounds__(kT) h_step_a(HArgs a)
                 ph[o] = phn;
                 q[o] = qn;
                 qh[o] = qhn;
-                const double2 u = cmulc(to_d2(phn), to_d2(qn));  // conj(ph) q
+                const V u = cmulc(phn, qn);  // conj(ph) q
                 acc.x += u.x;
                 acc.y += u.y;
             }
         }
-        item_sum(acc, sh, a.part + ((long long)rb * 2) * L + l, ok);
+        item_sum(to_d2(acc), sh, a.part + ((long long)rb * 2) * L + l, ok);
     }
 }
 
@@ -303,47 +303,47 @@ __global__ void __launch_bounds__(kT) h_step_b(HArgs a)
         // aligned group of nbp lanes of this warp)
         unsigned any = act ? 1u : 0u;
         for (int off = 1; off < nbp; off <<= 1) any |= __shfl_xor_sync(0xffffffffu, any, off);
-        V al = cmk<V>(T(0), T(0));
-        double2 ca = make_double2(0.0, 0.0);
+        V al = cmk<V>(T(0), T(0)), ca = al;
         if (act) {
             const double2 alpha = a.st[l].alpha, c = a.st[l].c;
             al = from_d2<V>(alpha);
-            ca = make_double2(c.x * alpha.x - c.y * alpha.y, c.x * alpha.y + c.y * alpha.x);
+            ca = from_d2<V>(make_double2(c.x * alpha.x - c.y * alpha.y, c.x * alpha.y + c.y * alpha.x));
         }
         const V alc = cconj(al);
-        double2 rho = make_double2(0.0, 0.0), nr = make_double2(0.0, 0.0);
+        // per-thread partials in the filter precision (GB300's FP64 ALU is slow);
+        // the item sums and the quadrature block stay FP64
+        V rho = cmk<V>(T(0), T(0));
+        T nr0 = T(0), nr1 = T(0);
         const int i1 = min(a.n, (rb + 1) * kRowsPerItem);
         for (int i = rb * kRowsPerItem + warp; i < i1; i += kT / 32) {  // bounds uniform over the warp
-            double2 d = make_double2(0.0, 0.0);
+            const long long o = (long long)i * L + l;
+            double2* qq = a.Q + (long long)i * a.m + j;
+            const bool writes = ok && any && e == 0 && j < a.m;
+            const double2 qold = writes ? *qq : make_double2(0.0, 0.0);  // issued with the vector loads
+            V d = cmk<V>(T(0), T(0));
             if (act) {
-                const long long o = (long long)i * L + l;
                 const V rn = cfma(cmk<V>(-al.x, -al.y), q[o], r[o]);
                 const V rhn = cfma(cmk<V>(-alc.x, -alc.y), qh[o], rh[o]);
                 r[o] = rn;
                 rh[o] = rhn;
-                const double2 rd = to_d2(rn), rhd = to_d2(rhn);
-                const double2 u = cmulc(rhd, rd);
+                const V u = cmulc(rhn, rn);
                 rho.x += u.x;
                 rho.y += u.y;
-                nr.x = fma(rd.x, rd.x, fma(rd.y, rd.y, nr.x));
-                nr.y = fma(rhd.x, rhd.x, fma(rhd.y, rhd.y, nr.y));
+                nr0 = fma(rn.x, rn.x, fma(rn.y, rn.y, nr0));
+                nr1 = fma(rhn.x, rhn.x, fma(rhn.y, rhn.y, nr1));
                 // (1/2)(c alpha p + conj(c alpha) ph)
-                const double2 pd = to_d2(p[o]), phd = to_d2(ph[o]);
-                d.x = 0.5 * ((ca.x * pd.x - ca.y * pd.y) + (ca.x * phd.x + ca.y * phd.y));
-                d.y = 0.5 * ((ca.x * pd.y + ca.y * pd.x) + (ca.x * phd.y - ca.y * phd.x));
+                const V pd = p[o], phd = ph[o];
+                d.x = T(0.5) * ((ca.x * pd.x - ca.y * pd.y) + (ca.x * phd.x + ca.y * phd.y));
+                d.y = T(0.5) * ((ca.x * pd.y + ca.y * pd.x) + (ca.x * phd.y - ca.y * phd.x));
             }
             for (int off = 1; off < nbp; off <<= 1) {
                 d.x += __shfl_xor_sync(0xffffffffu, d.x, off);
                 d.y += __shfl_xor_sync(0xffffffffu, d.y, off);
             }
-            if (ok && any && e == 0 && j < a.m) {
-                double2* qq = a.Q + (long long)i * a.m + j;
-                const double2 o = *qq;
-                *qq = make_double2(o.x + d.x, o.y + d.y);
-            }
+            if (writes) *qq = make_double2(qold.x + (double)d.x, qold.y + (double)d.y);
         }
-        item_sum(rho, sh, a.part + ((long long)rb * 2) * L + l, ok);
-        item_sum(nr, sh, a.part + ((long long)rb * 2 + 1) * L + l, ok);
+        item_sum(to_d2(rho), sh, a.part + ((long long)rb * 2) * L + l, ok);
+        item_sum(make_double2((double)nr0, (double)nr1), sh, a.part + ((long long)rb * 2 + 1) * L + l, ok);
     }
 }
 
@@ -1057,12 +1057,118 @@ __global__ void h_herm_part(int m, double2* __restrict__ C)
     }
 }
 
+// Cholesky route (the LAPACK hegv family's first step, as on the real path):
+// one CTA factors the scaled Bs = D Bq D = L L^H in the global scratch G
+// (row-major, lower triangle read), inverts X = L^{-1}, and writes the
+// B-orthonormal basis S = D X^H (upper triangular: S[r][c] = d_r conj(X[c][r])).
+// status = 0 when every pivot is positive and ||X||_F^2 <= 1e8, else 1 (then
+// the two-Jacobi route is taken).  After the first loops Bs is close to I, so
+// S^H Aq S is close to diagonal and its Jacobi converges in a few sweeps.
+static constexpr double kHCholCondMax = 1e8;
+
+__global__ void __launch_bounds__(1024) h_rg_cholinv(int m, const double2* __restrict__ Bs, const double2* __restrict__ Bq,
+                                                     double2* __restrict__ G, double* __restrict__ xd,
+                                                     double2* __restrict__ cj, double2* __restrict__ S,
+                                                     int* __restrict__ status, int* __restrict__ mk)
+{
+    __shared__ double red[32];
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    for (long long idx = tid; idx < (long long)m * m; idx += nt) G[idx] = Bs[idx];
+    if (tid == 0) s_ok = 1;
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {  // right-looking: two barriers per column
+        const double dj = G[(size_t)j * m + j].x;
+        if (!(dj > 0.0)) {  // same value in every thread: uniform exit
+            if (tid == 0) *status = 1;
+            return;
+        }
+        const double l = sqrt(dj);
+        for (int i = j + 1 + tid; i < m; i += nt) {
+            const double2 g = G[(size_t)i * m + j];
+            const double2 v = make_double2(g.x / l, g.y / l);
+            G[(size_t)i * m + j] = v;
+            cj[i] = v;
+        }
+        if (tid == 0) xd[j] = l;
+        __syncthreads();
+        for (int i = j + 1 + warp; i < m; i += nw) {  // G[i][k] -= cj[i] conj(cj[k]), j < k <= i
+            const double2 ci = cj[i];
+            for (int k = j + 1 + lane; k <= i; k += 32) {
+                const double2 ck = cj[k];
+                double2& g = G[(size_t)i * m + k];
+                g.x -= ci.x * ck.x + ci.y * ck.y;
+                g.y -= ci.y * ck.x - ci.x * ck.y;
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < m; i += nt) {
+        const double l = xd[i];
+        G[(size_t)i * m + i] = make_double2(l, 0.0);
+        xd[i] = 1.0 / l;
+    }
+    __syncthreads();
+    // X = L^{-1}: warp w owns columns c = w, w + nw, ...; X[i][c] =
+    // -(1/L_ii) sum_{c <= k < i} L[i][k] X[k][c], stored at G[c][i] (c < i)
+    double nrm = 0.0;
+    for (int c = warp; c < m; c += nw) {
+        const double xc = xd[c];
+        if (lane == 0) nrm += xc * xc;
+        for (int i = c + 1; i < m; ++i) {
+            double2 s = make_double2(0.0, 0.0);
+            for (int k = c + lane; k < i; k += 32) {
+                const double2 lik = G[(size_t)i * m + k];
+                const double2 xk = k == c ? make_double2(xc, 0.0) : G[(size_t)c * m + k];
+                s.x += lik.x * xk.x - lik.y * xk.y;
+                s.y += lik.x * xk.y + lik.y * xk.x;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+                s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+            }
+            const double2 v = make_double2(-s.x * xd[i], -s.y * xd[i]);
+            if (lane == 0) {
+                G[(size_t)c * m + i] = v;
+                nrm += v.x * v.x + v.y * v.y;
+            }
+            __syncwarp();
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    if (lane == 0) red[warp] = nrm;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += red[w];
+        s_ok = t <= kHCholCondMax;
+        *status = s_ok ? 0 : 1;
+        if (s_ok) *mk = m;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    for (long long idx = tid; idx < (long long)m * m; idx += nt) {
+        const int r = (int)(idx / m), c = (int)(idx % m);
+        const double br = Bq[(size_t)r * m + r].x;
+        const double dr = br > 0.0 ? 1.0 / sqrt(br) : 0.0;
+        double2 v = make_double2(0.0, 0.0);
+        if (c > r) {
+            const double2 x = G[idx];  // X[c][r]
+            v = make_double2(dr * x.x, -dr * x.y);
+        } else if (c == r) {
+            v = make_double2(dr * xd[r], 0.0);
+        }
+        S[idx] = v;
+    }
+}
+
 size_t h_reduced_work_bytes(int m)
 {
     const size_t mm = (size_t)m * m;
     int ks = 1;
     const size_t gp = h_gram_partial(m, m, &ks);
-    return (8 * mm + gp) * sizeof(double2) + 2 * (size_t)m * sizeof(double) + 256;
+    return (9 * mm + gp + m) * sizeof(double2) + 3 * (size_t)m * sizeof(double) + 512;
 }
 
 int h_reduced_gev(int m, const double2* Aq, const double2* Bq, double* lam, double2* V, int* mk_dev, int* status_dev,
@@ -1082,11 +1188,29 @@ int h_reduced_gev(int m, const double2* Aq, const double2* Bq, double* lam, doub
     double2* W = C + mm;
     double2* gp = W + mm;
     double* d = (double*)(gp + (size_t)ks * mm);
-    cudaError_t e = cudaMemsetAsync(status_dev, 0, sizeof(int), s);
+    double2* G = (double2*)(d + m + (m & 1));  // Cholesky scratch (m x m) and column buffer (m), 16-byte aligned
+    double2* cj = G + mm;
+    double* xd = (double*)(cj + m);
+    cudaError_t e = cudaMemsetAsync(status_dev, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return -4;
     const int blocks = (int)(((long long)mm + 255) / 256 < 1024 ? ((long long)mm + 255) / 256 : 1024);
     h_rg_prep<<<blocks, 256, 0, s>>>(m, Aq, Bq, As, Bs);
-    count_launches(1);
+    h_rg_cholinv<<<1, 1024, 0, s>>>(m, Bs, Bq, G, xd, cj, S, status_dev, mk_dev);
+    count_launches(2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return -4;
+    int chol = 1;
+    if (cudaMemcpyAsync(&chol, status_dev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return -4;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return -4;
+    if (chol == 0) {  // S^H Aq S, one Jacobi, V = S W
+        if ((e = launch_h_gemm(m, m, m, As, S, AS, s)) != cudaSuccess) return -4;
+        if ((e = launch_h_gram(m, m, S, AS, C, gp, ks, s)) != cudaSuccess) return -4;
+        h_herm_part<<<blocks, 256, 0, s>>>(m, C);
+        count_launches(1);
+        if ((e = launch_h_jacobi(m, C, Vw, lam, W, nullptr, status_dev + 1, s)) != cudaSuccess) return -4;
+        if ((e = launch_h_gemm(m, m, m, S, W, V, s)) != cudaSuccess) return -4;
+        return cudaGetLastError() == cudaSuccess ? 0 : -4;
+    }
+    if ((e = cudaMemsetAsync(status_dev, 0, sizeof(int), s)) != cudaSuccess) return -4;
     if ((e = launch_h_jacobi(m, Bs, Vw, d, U, nullptr, status_dev, s)) != cudaSuccess) return -4;
     h_rg_form_s<<<1, 1024, 0, s>>>(m, Bq, d, U, S, mk_dev, status_dev);
     count_launches(1);
