@@ -624,10 +624,13 @@ def run_batched(args):
     for _ in range(args.warmup):
         run(1)
     tt, conv = 0.0, 0
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
     for _ in range(args.steps):
         dt, c, res = run(1)
         tt += dt
         conv += c
+    clk = clocks.stop()
     value = conv / tt
     fp64 = None
     if args.fp64_steps > 0:
@@ -644,7 +647,7 @@ def run_batched(args):
                           "Ne": 8, "contour_ratio_pct": 200, "timing": "host clock around the batched call",
                           "generation_s": t_gen},
                "converged_pairs": conv // args.steps, "max_residual": float(max(r.res[: r.M].max() for r in res)),
-               "fp64": fp64}
+               "fp64": fp64, "clocks": clk}
         print(json.dumps(out))
 
 
@@ -681,10 +684,13 @@ def run_grad(args):
     for _ in range(args.warmup):
         step()
     M, fw_ms, bw_ms = 0, 0.0, 0.0
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
     for _ in range(args.steps):
         M, a, b = step()
         fw_ms += a
         bw_ms += b
+    clk = clocks.stop()
     if rank == 0:
         out = {"metric": METRIC, "value": M * args.steps / ((fw_ms + bw_ms) / 1e3), "unit": UNIT, "n_gpus": ws,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": (fw_ms + bw_ms) / args.steps,
@@ -692,7 +698,7 @@ def run_grad(args):
                "dtype": "c32 solves + f64 Rayleigh-Ritz and backward", "data": "synthetic (seeded generator, no dataset)",
                "config": {"workload": "laplace3d_7pt_48^3_potential_U[0,0.5]_seed4_eigenvalue_loss", "N": p.n,
                           "M0": p.m0, "M": M, "Ne": 8, "contour_ratio_pct": 200, "tol": 1e-12},
-               "forward_ms": fw_ms / args.steps, "backward_ms": bw_ms / args.steps}
+               "forward_ms": fw_ms / args.steps, "backward_ms": bw_ms / args.steps, "clocks": clk}
         print(json.dumps(out))
 
 
@@ -736,10 +742,13 @@ def run_hermitian(args):
     for _ in range(args.warmup):
         solve(1)
     ms, conv = 0.0, 0
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
     for _ in range(args.steps):
         t, c, r = solve(1)
         ms += t
         conv += c
+    clk = clocks.stop()
     value = conv / (ms / 1e3)
     fp64 = None
     if args.fp64_steps > 0:
@@ -756,7 +765,7 @@ def run_hermitian(args):
                           "interval": [p.emin, round(p.emax, 6)], "node_batch": args.node_batch or 1,
                           "inner_solver": "BiCG with the conjugate-shift shadow system, 1e-2, 80 steps"},
                "M": r.M, "converged_pairs": conv // args.steps, "max_residual": float(r.res[: r.M].max()),
-               "bicg_iterations": int(r.fpm[59]), "fp64": fp64}
+               "bicg_iterations": int(r.fpm[59]), "fp64": fp64, "clocks": clk}
         print(json.dumps(out))
 
 
