@@ -38,9 +38,12 @@
  *      fpm(50) contour nodes solved at once (node batch); fpm(51) rows per
  *      inner-solver work item; fpm(52) seed of the random start block;
  *      fpm(53) 1 = record per-kernel timings (see feast_last_profile);
- *      fpm(54) arithmetic of the Rayleigh-Ritz projections: 0 (default) =
+ *      fpm(54) arithmetic of the Rayleigh-Ritz projections and Ritz vectors
+ *      of the single-problem real and Hermitian drivers: 0 (default) =
  *      FP64-accurate sums of exact BF16 slice products on the tensor cores
- *      (feast_gram_oz_dev), 1 = FP64 tensor cores (mma.sync m8n8k4 f64).
+ *      (feast_gram_oz_dev, feast_gemm_oz_dev; complex blocks through their
+ *      real views), 1 = FP64 tensor cores (mma.sync m8n8k4 f64).  The
+ *      batched driver uses the FP64 tensor cores.
  *  - Return value = info (also stored in *info where that argument exists),
  *    codes of the guide's info table (Sec. 3.1): 0 success; warnings 1 (no
  *    eigenvalue in the interval), 2 (no convergence within fpm(4) loops),

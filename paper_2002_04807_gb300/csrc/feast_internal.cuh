@@ -140,10 +140,12 @@ size_t gram_partial_doubles(int n, int m, int* ksplit_out, int nsm);
 cudaError_t launch_gram_reduce(int m, const double* part, int ksplit, double* C, cudaStream_t s);
 // C = X^T Y to FP64 accuracy from exact BF16 slice products (k_ozaki.cu); part:
 // gram_oz_partial_doubles(n, m, ...) doubles, ex: gram_oz_work_bytes(m) bytes.
-size_t gram_oz_partial_doubles(int n, int m, int* ksplit_out, long long* rows_per_split, int nsm);
+// full: every entry of X^T Y (no symmetry assumed) instead of the upper
+// triangle mirrored.
+size_t gram_oz_partial_doubles(int n, int m, int* ksplit_out, long long* rows_per_split, int nsm, bool full = false);
 size_t gram_oz_work_bytes(int m);
 cudaError_t launch_gram_oz(int n, int m, const double* X, const double* Y, double* C, double* part, int* ex,
-                           cudaStream_t s);
+                           cudaStream_t s, bool full = false);
 // C (n x k) = A (n x m) V (m x k), row-major, FP64 accuracy from exact BF16
 // slice products (k_ozaki.cu); work: gemm_oz_work_bytes(n, m, k) bytes.
 size_t gemm_oz_work_bytes(int n, int m, int k);

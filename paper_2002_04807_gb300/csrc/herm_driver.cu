@@ -128,6 +128,7 @@ struct HBufs {
     int ks;    // Gram split
     bool fp64;
     int* nactive_host;  // host copy of the two lane counters
+    void* ozw;          // workspace of the sliced products (nullptr: FP64 DMMA products)
 };
 
 // One contour pass: Q = sum over all nodes (first pass: b = B Y, rii = 0) or
@@ -183,6 +184,7 @@ struct HPlan {
     int n = 0, m0 = 0, ne = 0, nb = 0, nbp = 0, ks = 1, nnz_a = 0, nnz_b = 0;
     long long Lmax = 0;
     bool fp64 = false, hasB = false;
+    bool oz = true;  // fpm(54) = 0: projections and Ritz vectors from sliced BF16 products
 };
 
 HPlan h_plan(int n, int nnz_a, int nnz_b, int m0, const int* fpm)
@@ -200,6 +202,7 @@ HPlan h_plan(int n, int nnz_a, int nnz_b, int m0, const int* fpm)
     while (P.nbp < P.nb) P.nbp <<= 1;
     P.Lmax = (long long)m0 * P.nbp;
     h_gram_partial(n, m0, &P.ks);
+    P.oz = fpm[53] == 0;
     return P;
 }
 
@@ -247,6 +250,7 @@ size_t h_carve(const HPlan& P, void* base, HBufs& B, float2** af, float2** bf)
     B.fa.part = c.take<double2>((size_t)row_blocks(P.n) * 2 * P.Lmax);
     *af = P.fp64 ? nullptr : c.take<float2>(P.nnz_a);
     *bf = (P.fp64 || !P.hasB) ? nullptr : c.take<float2>(P.nnz_b);
+    B.ozw = P.oz ? c.take<char>(h_sliced_work_bytes(P.n, P.m0)) : nullptr;
     return c.off + 256;
 }
 
@@ -297,17 +301,22 @@ int h_solve(const HMat& A, const HMat& Bm, bool hasB, int* fpm, double emin, dou
     for (k = 0;; ++k) {
         // Rayleigh-Ritz: Aq = Q^H A Q, Bq = Q^H B Q
         HCK(launch_h_spmm(n, m0, A.ia, A.ja, A.v, B.Q, B.T, s));
-        HCK(launch_h_gram(n, m0, B.Q, B.T, B.Aq, B.gpart, B.ks, s));
+        auto gram = [&](const double2* Xg, const double2* Yg, double2* Cg) {
+            return B.ozw ? launch_h_gram_sliced(n, m0, Xg, Yg, Cg, B.ozw, s)
+                         : launch_h_gram(n, m0, Xg, Yg, Cg, B.gpart, B.ks, s);
+        };
+        HCK(gram(B.Q, B.T, B.Aq));
         if (hasB) {
             HCK(launch_h_spmm(n, m0, Bm.ia, Bm.ja, Bm.v, B.Q, B.T2, s));
-            HCK(launch_h_gram(n, m0, B.Q, B.T2, B.Bq, B.gpart, B.ks, s));
+            HCK(gram(B.Q, B.T2, B.Bq));
         } else {
-            HCK(launch_h_gram(n, m0, B.Q, B.Q, B.Bq, B.gpart, B.ks, s));
+            HCK(gram(B.Q, B.Q, B.Bq));
         }
         const int rst = h_reduced_gev(m0, B.Aq, B.Bq, B.lam, B.Vr, B.mk, B.status, B.red, s);
         if (rst == -4) return cuda_error(cudaGetLastError(), "reduced Hermitian eigensolver");
         if (rst) return cuda_error(cudaErrorInvalidValue, "reduced Hermitian eigensolver size");
-        HCK(launch_h_gemm(n, m0, m0, B.Q, B.Vr, B.X, s));
+        if (B.ozw) HCK(launch_h_gemm_sliced(n, m0, m0, B.Q, B.Vr, B.X, B.ozw, s));
+        else HCK(launch_h_gemm(n, m0, m0, B.Q, B.Vr, B.X, s));
         HCK(launch_h_residual(n, m0, A.ia, A.ja, A.v, hasB ? Bm.ia : nullptr, hasB ? Bm.ja : nullptr,
                               hasB ? Bm.v : nullptr, B.X, B.lam, B.Y, B.rpart, B.res, alpha, s));
         HCK(cudaMemcpyAsync(lam.data(), B.lam, sizeof(double) * m0, cudaMemcpyDeviceToHost, s));

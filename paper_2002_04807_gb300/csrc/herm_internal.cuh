@@ -72,6 +72,13 @@ cudaError_t launch_h_gram(int n, int m, const double2* X, const double2* Y, doub
                           cudaStream_t s);
 // C (n x k) = A (n x m) V (m x k)
 cudaError_t launch_h_gemm(int n, int m, int k, const double2* A, const double2* V, double2* C, cudaStream_t s);
+// The same two products from exact BF16 slice products on the real views of
+// the complex blocks (k_ozaki.cu kernels); work: h_sliced_work_bytes(n, max(m, k)).
+size_t h_sliced_work_bytes(int n, int m);
+cudaError_t launch_h_gram_sliced(int n, int m, const double2* X, const double2* Y, double2* C, void* work,
+                                 cudaStream_t s);
+cudaError_t launch_h_gemm_sliced(int n, int m, int k, const double2* A, const double2* V, double2* C, void* work,
+                                 cudaStream_t s);
 // res_j = ||A x_j - lam_j B x_j|| / (alpha ||B x_j||); R = A x - lam B x
 size_t h_resid_partial(int n, int m);
 cudaError_t launch_h_residual(int n, int m, const int* ia, const int* ja, const double2* av, const int* ib,

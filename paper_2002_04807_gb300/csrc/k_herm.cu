@@ -29,6 +29,8 @@
 //             breakdown per lane
 // Reductions are deterministic: per row block fixed-order partial sums, then a
 // fixed-order sum over the row blocks.
+#include <algorithm>
+
 #include "feast_internal.cuh"
 #include "herm_internal.cuh"
 
@@ -816,6 +818,102 @@ cudaError_t launch_h_residual(int n, int m, const int* ia, const int* ja, const 
     h_res_cols<<<m, 256, 0, s>>>(n, m, part, alpha, res);
     count_launches(2);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- sliced products through real views
+// A row-major n x m complex block is, viewed as doubles, the real n x 2m block
+// Z = [Re q_1, Im q_1, Re q_2, ...].  Its real Gram G = Z^T Z' (2m x 2m, by the
+// sliced BF16 kernel) holds every product of real and imaginary parts, and
+//   (Q^H Y)[a][b] = (G[2a][2b] + G[2a+1][2b+1]) + i (G[2a][2b+1] - G[2a+1][2b]).
+// Likewise X = Q V is the real product Z W with W[2a][2b] = W[2a+1][2b+1] =
+// Re v_ab, W[2a][2b+1] = Im v_ab, W[2a+1][2b] = -Im v_ab, which leaves X in
+// the same interleaved layout.
+__global__ void h_from_real_gram(int m, const double* __restrict__ G, double2* __restrict__ C)
+{
+    const long long total = (long long)m * m;
+    const size_t ld = 2 * (size_t)m;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(idx / m), b = (int)(idx % m);
+        const double rr = G[(2 * a) * ld + 2 * b], ii = G[(2 * a + 1) * ld + 2 * b + 1];
+        const double ri = G[(2 * a) * ld + 2 * b + 1], ir = G[(2 * a + 1) * ld + 2 * b];
+        C[idx] = make_double2(rr + ii, ri - ir);
+    }
+}
+
+__global__ void h_real_coupling(int m, int k, const double2* __restrict__ V, double* __restrict__ W)
+{
+    const long long total = (long long)m * k;
+    const size_t ld = 2 * (size_t)k;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(idx / k), b = (int)(idx % k);
+        const double2 v = V[idx];
+        W[(2 * a) * ld + 2 * b] = v.x;
+        W[(2 * a) * ld + 2 * b + 1] = v.y;
+        W[(2 * a + 1) * ld + 2 * b] = -v.y;
+        W[(2 * a + 1) * ld + 2 * b + 1] = v.x;
+    }
+}
+
+// split-K partials of either Gram form (the upper-triangle form takes more splits)
+static size_t h_sliced_part_doubles(int n, int m2)
+{
+    return std::max(gram_oz_partial_doubles(n, m2, nullptr, nullptr, num_sms(), true),
+                    gram_oz_partial_doubles(n, m2, nullptr, nullptr, num_sms(), false));
+}
+
+static size_t r256(size_t b) { return (b + 255) / 256 * 256; }
+
+// the pieces of h_sliced_carve, each rounded up to 256 bytes
+size_t h_sliced_work_bytes(int n, int m)
+{
+    const int m2 = 2 * m;
+    return r256(h_sliced_part_doubles(n, m2) * sizeof(double)) + 2 * r256((size_t)m2 * m2 * sizeof(double)) +
+           r256(gram_oz_work_bytes(m2)) + r256(gemm_oz_work_bytes(n, m2, m2)) + 256;
+}
+
+static void h_sliced_carve(int n, int m, void* work, double** part, double** G, double** W, int** ex, void** gw)
+{
+    const int m2 = 2 * m;
+    char* p = (char*)work;
+    auto take = [&](size_t bytes) { char* q = p; p += r256(bytes); return q; };
+    *part = (double*)take(h_sliced_part_doubles(n, m2) * sizeof(double));
+    *G = (double*)take((size_t)m2 * m2 * sizeof(double));
+    *W = (double*)take((size_t)m2 * m2 * sizeof(double));
+    *ex = (int*)take(gram_oz_work_bytes(m2));
+    *gw = take(gemm_oz_work_bytes(n, m2, m2));
+}
+
+cudaError_t launch_h_gram_sliced(int n, int m, const double2* X, const double2* Y, double2* C, void* work,
+                                 cudaStream_t s)
+{
+    double *part, *G, *W;
+    int* ex;
+    void* gw;
+    h_sliced_carve(n, m, work, &part, &G, &W, &ex, &gw);
+    // X = Y: the real Gram is symmetric and its upper triangle suffices
+    cudaError_t e = launch_gram_oz(n, 2 * m, (const double*)X, (const double*)Y, G, part, ex, s, X != Y);
+    if (e != cudaSuccess) return e;
+    const long long mm = (long long)m * m;
+    h_from_real_gram<<<(int)std::min<long long>((mm + 255) / 256, 1024), 256, 0, s>>>(m, G, C);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_h_gemm_sliced(int n, int m, int k, const double2* A, const double2* V, double2* C, void* work,
+                                 cudaStream_t s)
+{
+    double *part, *G, *W;
+    int* ex;
+    void* gw;
+    h_sliced_carve(n, std::max(m, k), work, &part, &G, &W, &ex, &gw);
+    const long long mk = (long long)m * k;
+    h_real_coupling<<<(int)std::min<long long>((mk + 255) / 256, 1024), 256, 0, s>>>(m, k, V, W);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_gemm_oz(n, 2 * m, 2 * k, (const double*)A, W, (double*)C, gw, s);
 }
 
 // ---------------------------------------------------------------- Hermitian Jacobi (one CTA)

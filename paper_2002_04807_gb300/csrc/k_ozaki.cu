@@ -132,13 +132,19 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
 __global__ void __launch_bounds__(kOzThreads, 3) gram_oz(int n, int m, const double* __restrict__ X,
                                                            const double* __restrict__ Y, const int* __restrict__ exX,
                                                            const int* __restrict__ exY, double* __restrict__ part,
-                                                           int ksplit, int ntile, long long rows_per_split)
+                                                           int ksplit, int ntile, long long rows_per_split, int full)
 {
     __shared__ uint32_t sA[kSlices * kOzPlane];
     __shared__ uint32_t sB[kSlices * kOzPlane];
-    int t = blockIdx.x, ta = 0;
-    while (t >= ntile - ta) { t -= ntile - ta; ++ta; }
-    const int tb = ta + t;
+    int ta = 0, tb = 0;
+    if (full) {  // every tile (X^T Y need not be symmetric)
+        ta = blockIdx.x / ntile;
+        tb = blockIdx.x % ntile;
+    } else {  // upper tile triangle
+        int t = blockIdx.x;
+        while (t >= ntile - ta) { t -= ntile - ta; ++ta; }
+        tb = ta + t;
+    }
     const int a0 = ta * kOzTile, b0 = tb * kOzTile;
     const int split = blockIdx.y;
     const int r0 = (int)min((long long)n, split * rows_per_split);
@@ -148,7 +154,7 @@ __global__ void __launch_bounds__(kOzThreads, 3) gram_oz(int n, int m, const dou
     const int g = lane >> 2, tq = lane & 3;
     // a warp's 16 x 16 quarter is needed when it lies inside the m x m matrix
     // and not strictly below the diagonal; the others only help with loads
-    const bool live = a0 + wr < m && b0 + wc < m && !(ta == tb && wr > wc);
+    const bool live = a0 + wr < m && b0 + wc < m && (full || !(ta == tb && wr > wc));
 
     // loader: thread owns column lane of the tile and k-pairs warp + 4 u
     const int ca = a0 + lane, cb = b0 + lane;
@@ -264,10 +270,22 @@ __global__ void __launch_bounds__(kOzThreads, 3) gram_oz(int n, int m, const dou
         }
 }
 
-size_t gram_oz_partial_doubles(int n, int m, int* ksplit_out, long long* rows_per_split, int nsm)
+// C[i][j] = sum over splits of part[s][i][j], in split order (full product).
+__global__ void gram_reduce_full(int m, const double* __restrict__ part, int ksplit, double* __restrict__ C)
+{
+    const long long total = (long long)m * m;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int s = 0; s < ksplit; ++s) v += part[(size_t)s * total + idx];
+        C[idx] = v;
+    }
+}
+
+size_t gram_oz_partial_doubles(int n, int m, int* ksplit_out, long long* rows_per_split, int nsm, bool full)
 {
     const int nt = (m + kOzTile - 1) / kOzTile;
-    const int tiles = nt * (nt + 1) / 2;
+    const int tiles = full ? nt * nt : nt * (nt + 1) / 2;
     int ks = (3 * nsm) / tiles;  // one wave of three CTAs per SM
     const int maxk = (n + 255) / 256;        // at least 256 rows per split
     if (ks > maxk) ks = maxk;
@@ -284,12 +302,12 @@ size_t gram_oz_partial_doubles(int n, int m, int* ksplit_out, long long* rows_pe
 size_t gram_oz_work_bytes(int m) { return (size_t)2 * m * sizeof(int) + 256; }
 
 cudaError_t launch_gram_oz(int n, int m, const double* X, const double* Y, double* C, double* part, int* ex,
-                           cudaStream_t s)
+                           cudaStream_t s, bool full)
 {
     if (m <= 0 || n <= 0) return cudaSuccess;
     int ks = 1;
     long long rps = 0;
-    gram_oz_partial_doubles(n, m, &ks, &rps, num_sms());
+    gram_oz_partial_doubles(n, m, &ks, &rps, num_sms(), full);
     int* exX = ex;
     int* exY = ex + m;
     cudaError_t e = cudaMemsetAsync(ex, 0, sizeof(int) * 2 * (size_t)m, s);
@@ -300,11 +318,15 @@ cudaError_t launch_gram_oz(int n, int m, const double* X, const double* Y, doubl
     if (Y != X) oz_colexp<<<blocks, 256, 0, s>>>(n, m, Y, exY);
     else if ((e = cudaMemcpyAsync(exY, exX, sizeof(int) * m, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
     const int nt = (m + kOzTile - 1) / kOzTile;
-    dim3 grid(nt * (nt + 1) / 2, ks);
-    gram_oz<<<grid, kOzThreads, 0, s>>>(n, m, X, Y, exX, exY, part, ks, nt, rps);
+    dim3 grid(full ? nt * nt : nt * (nt + 1) / 2, ks);
+    gram_oz<<<grid, kOzThreads, 0, s>>>(n, m, X, Y, exX, exY, part, ks, nt, rps, full ? 1 : 0);
     count_launches(Y != X ? 4 : 3);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return launch_gram_reduce(m, part, ks, C, s);
+    if (!full) return launch_gram_reduce(m, part, ks, C, s);
+    const int rblocks = (int)std::min<long long>(((long long)m * m + 255) / 256, 2048);
+    gram_reduce_full<<<rblocks, 256, 0, s>>>(m, part, ks, C);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- C = A V

@@ -205,3 +205,25 @@ def test_gauge_workload_matches_real_spectrum(pkg):
     assert r.info == 0 and r.M == 20
     assert np.abs(r.E[:20] - lam[:20]).max() < EIG_TOL * np.abs(lam).max()
     assert r.res[:20].max() < RES_TOL
+
+
+def test_gauge_workload_wide_subspace_both_projection_arithmetics(pkg):
+    """The gauge workload at 16^3 with M0 = 150 (the bench's subspace width):
+    the projections split over several row blocks (the sliced products' two
+    Gram forms take different split counts), with the sliced BF16 products
+    (fpm(54) = 0) and with the FP64 tensor cores (1); both against the real
+    problem's dense spectrum."""
+    p = fw.laplace3d_gauge(side=16, count=100, m0=150, ratio=200)
+    lam = np.linalg.eigvalsh(p.notes["real_problem"].A.to_dense())
+    emax = 0.5 * (lam[99] + lam[100])
+    Es = []
+    for arith in (0, 1):
+        f = fpm_for(pkg, 1, ratio=200)
+        f[53] = arith
+        r = pkg.feast_hcsr_solve("F", p.n, p.A.data, p.A.indptr, p.A.indices, fpm=f, emin=p.emin, emax=emax,
+                                 m0=150, x0=p.y0())
+        assert r.info == 0 and r.M == 100, (arith, r.info, r.M)
+        assert np.abs(r.E[:100] - lam[:100]).max() < EIG_TOL * np.abs(lam[:100]).max()
+        assert r.res[:100].max() < RES_TOL
+        Es.append(r.E[:100])
+    assert np.abs(Es[0] - Es[1]).max() < 1e-12 * np.abs(lam[:100]).max()
