@@ -1371,6 +1371,26 @@ int host_csr(char uplo, int n, const double* v, const int* ia, const int* ja, in
     for (int i = 0; i < n; ++i)
         if (ia[i + 1] < ia[i]) return -(100 + arg0 + 1);
     const long long nnz = (long long)ia[n] - base;
+    if (uplo == 'F') {  // full storage: validate and copy in one pass while the rows are sorted
+        oia.resize((size_t)n + 1);
+        oja.resize((size_t)nnz);
+        ov.resize((size_t)nnz);
+        bool sorted = true;
+        for (int i = 0; i <= n; ++i) oia[i] = ia[i] - base;
+        for (int i = 0; i < n && sorted; ++i) {
+            int prev = -1;
+            for (int p = oia[i]; p < oia[i + 1]; ++p) {
+                const int j = ja[p] - base;
+                if (j < 0 || j >= n) return -(100 + arg0 + 2);
+                if (!std::isfinite(v[p])) return -(100 + arg0);
+                if (j <= prev) { sorted = false; break; }  // unsorted or repeated: general path below
+                prev = j;
+                oja[p] = j;
+                ov[p] = v[p];
+            }
+        }
+        if (sorted) return 0;
+    }
     std::vector<std::vector<std::pair<int, double>>> rows(n);
     for (int i = 0; i < n; ++i)
         for (int p = ia[i] - base; p < ia[i + 1] - base; ++p) {
