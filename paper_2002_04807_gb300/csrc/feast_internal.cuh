@@ -175,6 +175,8 @@ int jacobi_eig_dev(int m, double* A, double* lam, double* V, void* work, cudaStr
                    int* sweeps_host);
 // Reduced generalized problem; see k_eig.cu.  work: reduced_work_bytes(m).
 size_t reduced_work_bytes(int m);
+// spin limit (SM clock cycles) of the library's bounded grid barriers (feast_set_wait_limit)
+long long wait_limit_cycles();
 int reduced_gev_dev(int m, const double* Aq, const double* Bq, double* lam, double* V, int* mk,
                     void* work, cudaStream_t s);
 

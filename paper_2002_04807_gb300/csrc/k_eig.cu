@@ -55,6 +55,7 @@ struct JacWork {
 // 2 GHz); feast_set_wait_limit changes it for the launches that follow.
 static constexpr long long kDefaultSpinCycles = 4000000000LL;
 static std::atomic<long long> g_spin_cycles{kDefaultSpinCycles};
+long long wait_limit_cycles() { return g_spin_cycles.load(); }
 
 // Bounded grid barrier for a cooperative launch: each CTA adds one arrival to
 // a counter that only grows, then waits until the counter reaches the end of

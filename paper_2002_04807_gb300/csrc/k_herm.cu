@@ -1090,6 +1090,250 @@ cudaError_t launch_h_jacobi(int m, double2* A, double2* Vw, double* lam, double2
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- Hermitian Jacobi (many CTAs)
+// The same rotations as h_jacobi, spread over the CTAs of one cooperative
+// launch with one grid barrier per round (GB300's FP64 rate per SM is low, so
+// one CTA is slow): every CTA computes all rotations of the round (identical
+// inputs and code, so identical angles) into shared memory, then updates its
+// share of the 2 x 2 blocks from the current copy of A into the other copy,
+// so no CTA writes what another still reads.  Block (k, l) holds rows p_k, q_k
+// and columns p_l, q_l; with J_k = D_k R_k (columns (c, -s conj e) and
+// (s, c conj e)) it becomes J_k^H A J_l; a diagonal block becomes
+// diag(a_pp - t |a_pq|, a_qq + t |a_pq|).  The barrier spins at most
+// wait_limit_cycles() cycles, then every CTA returns and *err is set.
+struct HJWork {
+    unsigned long long count;  // barrier arrivals since launch; never reset
+    int err;
+    int sweeps;
+    int status;
+    int pad;
+    double fro;
+};
+
+__device__ __forceinline__ bool h_grid_sync(HJWork* w, long long limit)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int good = (*(volatile int*)&w->err == 0);
+        if (good) {
+            unsigned long long old;
+            asm volatile("atom.add.release.gpu.u64 %0, [%1], 1;" : "=l"(old) : "l"(&w->count) : "memory");
+            const unsigned long long target = (old / gridDim.x + 1) * gridDim.x;
+            const long long t0 = clock64();
+            for (;;) {
+                unsigned long long cur;
+                asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(cur) : "l"(&w->count) : "memory");
+                if (cur >= target) break;
+                if (*(volatile int*)&w->err) { good = 0; break; }
+                if (clock64() - t0 > limit) {
+                    atomicExch(&w->err, 1);
+                    good = 0;
+                    break;
+                }
+            }
+        }
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__global__ void __launch_bounds__(256) h_jacobi_coop(int m, double2* __restrict__ A, double2* __restrict__ A2,
+                                                     double2* __restrict__ Vw, double* __restrict__ lam,
+                                                     double2* __restrict__ Vout, HJWork* __restrict__ w,
+                                                     long long limit)
+{
+    __shared__ double s_c[kHJMax / 2], s_s[kHJMax / 2], s_t[kHJMax / 2];
+    __shared__ double2 s_e[kHJMax / 2];
+    __shared__ int s_p[kHJMax / 2], s_q[kHJMax / 2];
+    __shared__ double s_red[8];
+    __shared__ int s_any;
+    const int N = (m + 1) & ~1, half = N / 2;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+    for (long long idx = gtid; idx < (long long)m * m; idx += gsz)
+        Vw[idx] = make_double2(idx / m == idx % m ? 1.0 : 0.0, 0.0);
+    if (blockIdx.x == 0) {  // Frobenius norm, fixed order
+        double f = 0.0;
+        for (long long idx = threadIdx.x; idx < (long long)m * m; idx += blockDim.x) {
+            const double2 v = A[idx];
+            f = fma(v.x, v.x, fma(v.y, v.y, f));
+        }
+        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = f;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s_red[i];
+            w->fro = sqrt(t);
+        }
+    }
+    if (!h_grid_sync(w, limit)) return;
+    const double absfloor = 1e-18 * *(volatile double*)&w->fro;
+    double2* cur = A;
+    double2* nxt = A2;
+    int sweep = 0;
+    bool more = m > 1;
+    while (more && sweep < kHJSweeps) {
+        if (threadIdx.x == 0) s_any = 0;
+        __syncthreads();
+        for (int r = 0; r < N - 1; ++r) {
+            for (int k = threadIdx.x; k < half; k += blockDim.x) {
+                int p, q;
+                if (k == 0) {
+                    p = r;
+                    q = N - 1;
+                } else {
+                    p = (r + k) % (N - 1);
+                    q = (r - k + (N - 1)) % (N - 1);
+                }
+                if (p > q) { const int t = p; p = q; q = t; }
+                double c = 1.0, s = 0.0, tt = 0.0;
+                double2 e = make_double2(1.0, 0.0);
+                if (q < m) {
+                    const double2 apq = __ldcg(cur + (size_t)p * m + q);
+                    const double mag = hypot(apq.x, apq.y);
+                    const double app = __ldcg(cur + (size_t)p * m + p).x, aqq = __ldcg(cur + (size_t)q * m + q).x;
+                    const double thr = fmax(1.1e-16 * sqrt(fabs(app * aqq)), absfloor);
+                    if (mag > thr) {
+                        e = make_double2(apq.x / mag, apq.y / mag);
+                        const double tau = (aqq - app) / (2.0 * mag);
+                        tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + tt * tt);
+                        s = tt * c;
+                        s_any = 1;
+                    }
+                }
+                s_c[k] = c;
+                s_s[k] = s;
+                s_t[k] = tt;
+                s_e[k] = e;
+                s_p[k] = p;
+                s_q[k] = q;
+            }
+            __syncthreads();
+            for (long long idx = gtid; idx < (long long)half * half; idx += gsz) {
+                const int k = (int)(idx / half), l = (int)(idx % half);
+                const int p = s_p[k], q = s_q[k], pp = s_p[l], qq = s_q[l];
+                const bool qv = q < m, qqv = qq < m;
+                if (k == l) {
+                    const double2 app = __ldcg(cur + (size_t)p * m + p);
+                    if (!qv) {
+                        nxt[(size_t)p * m + p] = make_double2(app.x, 0.0);
+                        continue;
+                    }
+                    const double2 apq = __ldcg(cur + (size_t)p * m + q), aqq = __ldcg(cur + (size_t)q * m + q);
+                    if (s_s[k] == 0.0) {
+                        nxt[(size_t)p * m + p] = make_double2(app.x, 0.0);
+                        nxt[(size_t)q * m + q] = make_double2(aqq.x, 0.0);
+                        nxt[(size_t)p * m + q] = apq;
+                        nxt[(size_t)q * m + p] = __ldcg(cur + (size_t)q * m + p);
+                    } else {
+                        const double mag = hypot(apq.x, apq.y);
+                        nxt[(size_t)p * m + p] = make_double2(app.x - s_t[k] * mag, 0.0);
+                        nxt[(size_t)q * m + q] = make_double2(aqq.x + s_t[k] * mag, 0.0);
+                        nxt[(size_t)p * m + q] = make_double2(0.0, 0.0);
+                        nxt[(size_t)q * m + p] = make_double2(0.0, 0.0);
+                    }
+                    continue;
+                }
+                const double ck = s_c[k], sk = s_s[k], cl = s_c[l], sl = s_s[l];
+                const double2 ek = s_e[k], el = s_e[l];
+                const double2 z = make_double2(0.0, 0.0);
+                const double2 x00 = __ldcg(cur + (size_t)p * m + pp);
+                const double2 x01 = qqv ? __ldcg(cur + (size_t)p * m + qq) : z;
+                const double2 x10 = qv ? __ldcg(cur + (size_t)q * m + pp) : z;
+                const double2 x11 = (qv && qqv) ? __ldcg(cur + (size_t)q * m + qq) : z;
+                // rows (J_k^H): y0 = c x0 - s e x1, y1 = s x0 + c e x1
+                const double2 ex10 = make_double2(ek.x * x10.x - ek.y * x10.y, ek.x * x10.y + ek.y * x10.x);
+                const double2 ex11 = make_double2(ek.x * x11.x - ek.y * x11.y, ek.x * x11.y + ek.y * x11.x);
+                const double2 y00 = make_double2(ck * x00.x - sk * ex10.x, ck * x00.y - sk * ex10.y);
+                const double2 y01 = make_double2(ck * x01.x - sk * ex11.x, ck * x01.y - sk * ex11.y);
+                const double2 y10 = make_double2(sk * x00.x + ck * ex10.x, sk * x00.y + ck * ex10.y);
+                const double2 y11 = make_double2(sk * x01.x + ck * ex11.x, sk * x01.y + ck * ex11.y);
+                // columns (J_l): col p' = c y.0 - s conj(e) y.1, col q' = s y.0 + c conj(e) y.1
+                const double2 ec = make_double2(el.x, -el.y);
+                const double2 ey01 = make_double2(ec.x * y01.x - ec.y * y01.y, ec.x * y01.y + ec.y * y01.x);
+                const double2 ey11 = make_double2(ec.x * y11.x - ec.y * y11.y, ec.x * y11.y + ec.y * y11.x);
+                nxt[(size_t)p * m + pp] = make_double2(cl * y00.x - sl * ey01.x, cl * y00.y - sl * ey01.y);
+                if (qqv) nxt[(size_t)p * m + qq] = make_double2(sl * y00.x + cl * ey01.x, sl * y00.y + cl * ey01.y);
+                if (qv) nxt[(size_t)q * m + pp] = make_double2(cl * y10.x - sl * ey11.x, cl * y10.y - sl * ey11.y);
+                if (qv && qqv)
+                    nxt[(size_t)q * m + qq] = make_double2(sl * y10.x + cl * ey11.x, sl * y10.y + cl * ey11.y);
+            }
+            for (long long idx = gtid; idx < (long long)m * half; idx += gsz) {  // V <- V J
+                const int i = (int)(idx / half), k = (int)(idx % half);
+                const double sk = s_s[k];
+                if (sk == 0.0) continue;
+                const double ck = s_c[k];
+                const double2 ec = make_double2(s_e[k].x, -s_e[k].y);
+                const int p = s_p[k], q = s_q[k];
+                const double2 vp = Vw[(size_t)i * m + p], vq = Vw[(size_t)i * m + q];
+                const double2 evq = make_double2(ec.x * vq.x - ec.y * vq.y, ec.x * vq.y + ec.y * vq.x);
+                Vw[(size_t)i * m + p] = make_double2(ck * vp.x - sk * evq.x, ck * vp.y - sk * evq.y);
+                Vw[(size_t)i * m + q] = make_double2(sk * vp.x + ck * evq.x, sk * vp.y + ck * evq.y);
+            }
+            if (!h_grid_sync(w, limit)) return;
+            double2* tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
+        more = s_any != 0;  // same decision in every CTA
+        ++sweep;
+    }
+    for (int i = gtid; i < m; i += gsz) {  // ascending order: rank by value, ties by index
+        const double li = __ldcg(cur + (size_t)i * m + i).x;
+        int rk = 0;
+        for (int j = 0; j < m; ++j) {
+            const double lj = __ldcg(cur + (size_t)j * m + j).x;
+            rk += (lj < li) || (lj == li && j < i);
+        }
+        lam[rk] = li;
+        for (int row = 0; row < m; ++row) Vout[(size_t)row * m + rk] = Vw[(size_t)row * m + i];
+    }
+    if (gtid == 0) {
+        w->sweeps = sweep;
+        w->status = more ? -1 : 0;
+    }
+}
+
+size_t h_jacobi_coop_bytes(int m) { return 2 * (size_t)m * m * sizeof(double2) + sizeof(HJWork) + 512; }
+
+// A (m x m) is overwritten; V gets the eigenvectors in ascending order of
+// lam.  *status_dev: 0, -1 (sweep limit) or -2 (grid barrier timed out).
+// Returns a CUDA error, cudaSuccess otherwise.
+__global__ void h_coop_status(const HJWork* w, int* status) { *status = w->err ? -2 : w->status; }
+
+static cudaError_t launch_h_jacobi_coop(int m, double2* A, double* lam, double2* V, void* work, int* status_dev,
+                                        cudaStream_t s)
+{
+    char* p = (char*)work;
+    HJWork* w = (HJWork*)p;
+    double2* A2 = (double2*)(p + 256);
+    double2* Vw = A2 + (size_t)m * m;
+    cudaError_t e = cudaMemsetAsync(w, 0, sizeof(HJWork), s);
+    if (e != cudaSuccess) return e;
+    static const int per_sm = [] {
+        int v = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, h_jacobi_coop, 256, 0);
+        return v > 0 ? v : 1;
+    }();
+    const int half = (m + 1) / 2;
+    long long blocks = ((long long)m * half + 255) / 256;
+    const long long cap = std::min<long long>((long long)num_sms() * per_sm, num_sms());
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    long long limit = wait_limit_cycles();
+    void* args[] = {&m, &A, &A2, &Vw, &lam, &V, &w, &limit};
+    e = cudaLaunchCooperativeKernel((void*)h_jacobi_coop, dim3((unsigned)blocks), dim3(256), args, 0, s);
+    count_launches(1);
+    if (e != cudaSuccess) return e;
+    // status: -2 when the barrier gave up, -1 at the sweep limit, else 0
+    h_coop_status<<<1, 1, 0, s>>>(w, status_dev);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- reduced generalized problem
 // Aq v = lambda Bq v, both symmetrised as (M + M^H)/2.  Scaling D =
 // diag(Bq)^{-1/2}; Jacobi on D Bq D = U diag(d) U^H; keep d > 1e-14 max d
@@ -1266,7 +1510,7 @@ size_t h_reduced_work_bytes(int m)
     const size_t mm = (size_t)m * m;
     int ks = 1;
     const size_t gp = h_gram_partial(m, m, &ks);
-    return (9 * mm + gp + m) * sizeof(double2) + 3 * (size_t)m * sizeof(double) + 512;
+    return (9 * mm + gp + m) * sizeof(double2) + 3 * (size_t)m * sizeof(double) + 512 + h_jacobi_coop_bytes(m) + 256;
 }
 
 int h_reduced_gev(int m, const double2* Aq, const double2* Bq, double* lam, double2* V, int* mk_dev, int* status_dev,
@@ -1289,6 +1533,7 @@ int h_reduced_gev(int m, const double2* Aq, const double2* Bq, double* lam, doub
     double2* G = (double2*)(d + m + (m & 1));  // Cholesky scratch (m x m) and column buffer (m), 16-byte aligned
     double2* cj = G + mm;
     double* xd = (double*)(cj + m);
+    void* jw = (void*)(((uintptr_t)(xd + m) + 255) & ~(uintptr_t)255);  // cooperative Jacobi work
     cudaError_t e = cudaMemsetAsync(status_dev, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return -4;
     const int blocks = (int)(((long long)mm + 255) / 256 < 1024 ? ((long long)mm + 255) / 256 : 1024);
@@ -1304,12 +1549,12 @@ int h_reduced_gev(int m, const double2* Aq, const double2* Bq, double* lam, doub
         if ((e = launch_h_gram(m, m, S, AS, C, gp, ks, s)) != cudaSuccess) return -4;
         h_herm_part<<<blocks, 256, 0, s>>>(m, C);
         count_launches(1);
-        if ((e = launch_h_jacobi(m, C, Vw, lam, W, nullptr, status_dev + 1, s)) != cudaSuccess) return -4;
+        if ((e = launch_h_jacobi_coop(m, C, lam, W, jw, status_dev + 1, s)) != cudaSuccess) return -4;
         if ((e = launch_h_gemm(m, m, m, S, W, V, s)) != cudaSuccess) return -4;
         return cudaGetLastError() == cudaSuccess ? 0 : -4;
     }
     if ((e = cudaMemsetAsync(status_dev, 0, sizeof(int), s)) != cudaSuccess) return -4;
-    if ((e = launch_h_jacobi(m, Bs, Vw, d, U, nullptr, status_dev, s)) != cudaSuccess) return -4;
+    if ((e = launch_h_jacobi_coop(m, Bs, d, U, jw, status_dev, s)) != cudaSuccess) return -4;
     h_rg_form_s<<<1, 1024, 0, s>>>(m, Bq, d, U, S, mk_dev, status_dev);
     count_launches(1);
     if ((e = launch_h_gemm(m, m, m, As, S, AS, s)) != cudaSuccess) return -4;
