@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--cpu-sample-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--inner-tol", type=int, default=2, help="fpm(45): inner solves to 10^-k relative residual")
+    ap.add_argument("--inner-maxit", type=int, default=80, help="fpm(46): inner-solver iteration cap")
     ap.add_argument("--node-batch", type=int, default=0, help="fpm(50): contour nodes per inner-solver batch "
                                                                  "(0: the workload's default)")
     ap.add_argument("--rows-per-item", type=int, default=0, help="fpm(51): rows per work item of the COCG gather "
@@ -75,7 +77,8 @@ def config_dict(p, extra=None):
     d = {"workload": f"laplace3d_7pt_{round(p.n ** (1 / 3))}^3_potential_U[0,0.5]_seed1",
          "N": p.n, "nnz": p.A.nnz, "M0": p.m0, "Ne": p.ne, "contour_ratio_pct": p.ratio,
          "interval": [p.emin, round(p.emax, 6)], "B": "identity", "tol": RES_TOL,
-         "inner_solver": "COCG, fpm(45)=2 (1e-2), fpm(46)=80, one node per batch (fpm(50)=1)",
+         "inner_solver": f"COCG, fpm(45)={INNER[0]} (1e-{INNER[0]}), fpm(46)={INNER[1]}, one node per batch "
+                         "(fpm(50)=1)",
          "l2": "inputs larger than L2 (each filter block vector 2.5 GB)"}
     if extra:
         d.update(extra)
@@ -83,13 +86,14 @@ def config_dict(p, extra=None):
 
 
 ROWS_PER_ITEM = 0
+INNER = (2, 80)  # fpm(45), fpm(46) of the 64^3 workload
 
 
 def fpm_for(pkg, p, mixed, profile):
     f = pkg.feast_init()
     f[1], f[2], f[3], f[4], f[17] = p.ne, 10, 40, 1, p.ratio
     f[41] = 1 if mixed else 0
-    f[44], f[45] = 2, 80
+    f[44], f[45] = INNER
     f[49] = 1  # one contour node per batch: groups of a fast node stop early
     f[50] = ROWS_PER_ITEM
     f[52] = 1 if profile else 0
@@ -772,6 +776,7 @@ def run_hermitian(args):
 if __name__ == "__main__":
     a = parse()
     ROWS_PER_ITEM = a.rows_per_item
+    INNER = (a.inner_tol, a.inner_maxit)
     if a.side is None:
         a.side = 96 if a.workload == "stencil27" else 64
     if a.impl == "reference" and a.workload != "laplace3d":
