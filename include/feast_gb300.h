@@ -36,7 +36,11 @@
  *      fpm(60) output: total number of inner (COCG) iterations
  *    Library options in reserved slots (0 = automatic):
  *      fpm(50) contour nodes solved at once (node batch); fpm(51) rows per
- *      inner-solver work item; fpm(52) seed of the random start block;
+ *      inner-solver work item (0: the single-problem drivers stage the rows
+ *      each item gathers in shared memory, 64 or 32 rows per item, when the
+ *      matrix's row blocks read few contiguous column ranges and B is the
+ *      identity or diagonal; else 256; > 0: that many rows, gathered through
+ *      the caches); fpm(52) seed of the random start block;
  *      fpm(53) 1 = record per-kernel timings (see feast_last_profile);
  *      fpm(54) arithmetic of the Rayleigh-Ritz projections and Ritz vectors
  *      of the single-problem real and Hermitian drivers: 0 (default) =
@@ -112,13 +116,17 @@ int feast_contour_nodes_rule(int rule, int ne, double emin, double emax, int rat
 /* Timings of the last solve entry point (feast_scsr_solve*, feast_scsr_extreme*)
  * of the calling thread run with fpm(53) = 1 (all zero otherwise; an
  * extreme-eigenvalue search reports the totals of its solves), measured with CUDA events
- * on the solve's stream.  out (host, 16 doubles): [0] ms in COCG step A
+ * on the solve's stream.  out (host, 20 doubles): [0] ms in COCG step A
  * launches, [1] ms in COCG step B launches, [2] step A launches, [3] step B
  * launches, [4] group-iterations (column groups x COCG steps done), [5] ms in
  * filter passes, [6] ms projecting (A Q, Q^T A Q, Q^T B Q), [7] ms in the
  * reduced eigensolver, [8] ms forming Ritz vectors and residuals, [9] tile
  * width W, [10] columns per group mt, [11] n, [12] bytes per complex value,
- * [13] column groups, [14] refinement loops, [15] kernel launches issued.
+ * [13] column groups, [14] refinement loops, [15] kernel launches issued,
+ * [16] rows per step-A work item, [17] 1 when step A stages the rows it
+ * gathers in shared memory (windows of r copied by the bulk-copy engine),
+ * 0 when it gathers through the caches, [18] step A CTAs (staged variant),
+ * [19] staged rows per CTA (staged variant).
  * Library extension (the guide reports phase timings only as a text log).
  * Returns 0. */
 int feast_last_profile(double* out);

@@ -135,11 +135,12 @@ def _dev(t, dtype):
 # ---------------------------------------------------------------- host-side helpers
 PROFILE_KEYS = ["cocg_a_ms", "cocg_b_ms", "cocg_a_launches", "cocg_b_launches", "group_iterations",
                 "filter_ms", "project_ms", "reduce_ms", "ritz_ms", "W", "mt", "n", "complex_bytes", "groups",
-                "loops", "launches"]
+                "loops", "launches", "step_a_rows_per_item", "step_a_staged", "step_a_grid",
+                "step_a_staged_rows"]
 
 
 def feast_last_profile() -> dict:
-    out = np.zeros(16)
+    out = np.zeros(20)
     library().feast_last_profile(_ptr(out))
     return dict(zip(PROFILE_KEYS, out.tolist()))
 

@@ -328,6 +328,7 @@ struct Plan {
     int nnzA = 0, nnzB = 0;
     int ksplit = 1;
     bool oz = true;  // projections from exact BF16 slice products (fpm(54) = 0) or FP64 DMMA (1)
+    bool win = false;  // try the staged-window step A (rows per item automatic, fpm(51) = 0)
     int nslot = 1;  // partial-sum slots per group (item slots + bucket slots)
     int nbk = 1;    // bucket counters per group
     size_t gpart = 0, rpart = 0;
@@ -348,6 +349,16 @@ struct Bufs {
     int *app = nullptr, *bpp = nullptr;   // padded row pointers
     void* bd = nullptr;                   // diagonal of B (filter precision) when B is diagonal
     int bmode = 0;
+    // step A work items chosen at setup: RB rows per item (plan's RB, or the
+    // staged-window variant's wrb rows when wrb > 0)
+    int RB = 0, nrb = 0;
+    long long nitems = 0;
+    int wrb = 0, wgrid = 0, wcapr = 0;
+    size_t wsmem = 0;
+    int4* whdr = nullptr;  // staged-window tables (k_filter.cu win_build)
+    int2* wwin = nullptr;
+    void* wpk = nullptr;
+    int* wstat = nullptr;
     void* dQ = nullptr;                   // per-pass quadrature accumulator (filter precision)
     double* zw = nullptr;
     double *Y = nullptr, *Q = nullptr, *X = nullptr, *T = nullptr, *T2 = nullptr;
@@ -387,8 +398,11 @@ Plan make_plan(int n, int nnzA, int nnzB, int m0, const int* fpm, bool filter_on
     P.RBb = 512;
     P.nrb_b = (n + P.RBb - 1) / P.RBb;
     P.nitems_b = (long long)P.G * P.nrb_b;
-    P.nslot = std::max(part_slots(P.nrb), part_slots(P.nrb_b));
-    P.nbk = std::max(part_buckets(P.nrb), part_buckets(P.nrb_b));
+    // the staged-window step A publishes one slot per CTA (at most 4 per SM)
+    P.win = fpm[50] == 0;
+    const int wslots = P.win ? num_sms() * 4 : 0;
+    P.nslot = std::max({part_slots(P.nrb), part_slots(P.nrb_b), part_slots(wslots)});
+    P.nbk = std::max({part_buckets(P.nrb), part_buckets(P.nrb_b), part_buckets(wslots)});
     if (!filter_only) {
         P.oz = fpm[53] == 0;
         P.gpart = P.oz ? gram_oz_partial_doubles(n, m0, nullptr, nullptr, num_sms())
@@ -425,7 +439,7 @@ size_t carve(const Plan& P, void* base, Bufs& B, bool filter_only = false)
     B.bk_count = c.take<unsigned>((size_t)P.G * P.nbk);
     B.grp_done = c.take<int>(P.G);
     B.iter_max = c.take<int>(P.nbatch);
-    B.groups_left = c.take<int>(1);
+    B.groups_left = c.take<int>(2);  // [0] groups still iterating, [1] staged-row wait error
     B.work = c.take<unsigned long long>(1);
     B.probs = c.take<FiltProb>(1);
     const size_t pk = P.fp64 ? 16 : 8;
@@ -435,6 +449,13 @@ size_t carve(const Plan& P, void* base, Bufs& B, bool filter_only = false)
         B.bpp = c.take<int>((size_t)P.n + 1);
         B.bpk = c.take<char>(((size_t)P.nnzB + 7 * (size_t)P.n) * pk);
         B.bd = c.take<double>((size_t)P.n);
+    }
+    if (P.win) {
+        const size_t nrb32 = ((size_t)P.n + 31) / 32;
+        B.wpk = c.take<char>(((size_t)P.nnzA + 7 * (size_t)P.n) * pk);
+        B.whdr = c.take<int4>(nrb32);
+        B.wwin = c.take<int2>(nrb32 * kWinMax);
+        B.wstat = c.take<int>(4);
     }
     B.dQ = c.take<char>((size_t)P.G * P.mt * P.n * (P.fp64 ? 8 : 4));
     B.zw = c.take<double>(4 * (size_t)P.ne);
@@ -588,7 +609,7 @@ struct Prof {
     size_t used = 0;
     std::vector<std::pair<size_t, size_t>> a, b;  // cocg_step_a / cocg_step_b launches
     std::vector<std::pair<int, std::pair<size_t, size_t>>> phase;
-    double out[16] = {0};
+    double out[20] = {0};
     cudaEvent_t ev()
     {
         if (used == pool.size()) {
@@ -647,13 +668,13 @@ int filter_pass(const Plan& P, Bufs& B, int rii, const double* R, const double* 
     memset(&fa, 0, sizeof(fa));
     fa.probs = B.probs;
     fa.nprob = 1;
-    fa.nitems = P.nitems;
+    fa.nitems = B.nitems;
     fa.nitems_b = P.nitems_b;
     fa.RBb = P.RBb;
     fa.W = P.W;
     fa.nbp = P.nbp;
     fa.mt = P.mt;
-    fa.RB = P.RB;
+    fa.RB = B.RB;
     fa.hasB = P.hasB ? 1 : 0;
     fa.bmode = B.bmode;
     fa.r = B.r;
@@ -670,13 +691,29 @@ int filter_pass(const Plan& P, Bufs& B, int rii, const double* R, const double* 
     fa.tol2 = tol * tol;
     fa.groups_left = B.groups_left;
     fa.work = B.work;
+    fa.whdr = B.whdr;
+    fa.wwin = B.wwin;
+    fa.wpk = B.wpk;
+    fa.wcapr = B.wcapr;
+    fa.werr = B.groups_left + 1;
+    fa.wlimit = wait_limit_cycles();
     int grid_a = 1, grid_b = 1;
     filter_grids(P.fp64, P.W, &grid_a, &grid_b);
-    grid_a = (int)std::min<long long>(grid_a, P.nitems);
+    grid_a = B.wrb ? B.wgrid : (int)std::min<long long>(grid_a, B.nitems);
     grid_b = (int)std::min<long long>(grid_b, P.nitems_b);
     const int grid = std::max(grid_a, grid_b);  // filter_init
     fa.nslot = P.nslot;
     CK(cudaMemsetAsync(B.iter_max, 0, sizeof(int) * P.nbatch, s));
+    CK(cudaMemsetAsync(B.groups_left + 1, 0, sizeof(int), s));
+    auto step_a = [&](int k) -> cudaError_t {
+        return B.wrb ? launch_cocg_step_aw(fa, P.fp64, B.wrb, k, grid_a, B.wsmem, s)
+                     : launch_cocg_step_a(fa, P.fp64, k, grid_a, s);
+    };
+    // a CTA of the staged-window step A that gave up waiting for its copies
+    auto wait_failed = [&](int werr) -> int {
+        g_err = "COCG step A: staged-row copies did not complete within the wait limit";
+        return werr ? -4 : 0;
+    };
     int left = P.G;
     for (int b = 0; b < P.nbatch; ++b) {
         fa.iter_max = B.iter_max + b;
@@ -689,26 +726,33 @@ int filter_pass(const Plan& P, Bufs& B, int rii, const double* R, const double* 
         for (int k = 0; k < maxit; ++k) {
             if (g_prof.on) {
                 const size_t e0 = g_prof.mark(s);
-                CK(launch_cocg_step_a(fa, P.fp64, k, grid_a, s));
+                CK(step_a(k));
                 const size_t e1 = g_prof.mark(s);
                 CK(launch_cocg_step_b(fa, P.fp64, k, grid_b, s));
                 const size_t e2 = g_prof.mark(s);
                 g_prof.a.push_back({e0, e1});
                 g_prof.b.push_back({e1, e2});
             } else {
-                CK(launch_cocg_step_a(fa, P.fp64, k, grid_a, s));
+                CK(step_a(k));
                 CK(launch_cocg_step_b(fa, P.fp64, k, grid_b, s));
             }
             // every few steps: stop launching once no group iterates any more
             if ((k & 7) == 7 && k + 1 < maxit) {
-                int h = 1;
-                CK(cudaMemcpyAsync(&h, B.groups_left, sizeof(int), cudaMemcpyDeviceToHost, s));
+                int h[2] = {1, 0};
+                CK(cudaMemcpyAsync(h, B.groups_left, sizeof(h), cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
-                if (h <= 0) break;
+                if (h[1]) return wait_failed(h[1]);
+                if (h[0] <= 0) break;
             }
         }
     }
     CK(launch_fold_dq(fa, (long long)P.n * P.m0, P.fp64, s));
+    if (B.wrb) {
+        int werr = 0;
+        CK(cudaMemcpyAsync(&werr, B.groups_left + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (werr) return wait_failed(werr);
+    }
     return 0;
 }
 
@@ -746,6 +790,41 @@ int pack_matrix(const Csr& M, bool fp64, bool allow_diag, int* d_pp, void* d_pk,
     return 0;
 }
 
+// Work items of step A: the staged-window variant with 64, else 32 rows per
+// item when the matrix's row blocks fit (windows, shared memory, two CTAs per
+// SM) and B is the identity or diagonal; otherwise the plan's rows per item
+// with the gather through the caches.
+int choose_step_a(const Plan& P, Bufs& B, cudaStream_t s)
+{
+    B.RB = P.RB;
+    B.nrb = P.nrb;
+    B.nitems = P.nitems;
+    B.wrb = 0;
+    if (!P.win || B.bmode == 2) return 0;
+    for (const int rbw : {64, 32}) {
+        int st4[4] = {0, 0, 0, 0};
+        CK(cudaMemsetAsync(B.wstat, 0, sizeof(st4), s));
+        CK(launch_win_build(P.n, rbw, B.app, B.apk, P.fp64, B.wpk, B.whdr, B.wwin, B.wstat, s));
+        CK(cudaMemcpyAsync(st4, B.wstat, sizeof(st4), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (st4[3]) return 0;  // column indices outside [0, n): leave the matrix to the general path
+        if (st4[2]) continue;
+        const size_t smem = win_smem_bytes(P.fp64, P.W, st4[0], st4[1]);
+        const int occ = std::min(4, win_occupancy(P.fp64, P.W, B.bmode, rbw, smem));
+        if (occ < 2) continue;
+        const int nrbw = (P.n + rbw - 1) / rbw;
+        B.wrb = rbw;
+        B.wsmem = smem;
+        B.wcapr = st4[0];
+        B.wgrid = std::min(num_sms() * occ, nrbw);
+        B.RB = rbw;
+        B.nrb = nrbw;
+        B.nitems = (long long)P.G * nrbw;
+        return 0;
+    }
+    return 0;
+}
+
 int setup_filter(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, const std::vector<double>& zw,
                  const double* lam, const int* mk, cudaStream_t s)
 {
@@ -758,12 +837,14 @@ int setup_filter(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, const std:
         st = pack_matrix(Bm, P.fp64, true, B.bpp, B.bpk, B.bd, &B.bmode, s);
         if (st) return st;
     }
+    st = choose_step_a(P, B, s);
+    if (st) return st;
     FiltProb fp;
     memset(&fp, 0, sizeof(fp));
     fp.n = P.n;
     fp.m0 = P.m0;
     fp.G = P.G;
-    fp.nrb = P.nrb;
+    fp.nrb = B.nrb;
     fp.item0 = 0;
     fp.nrb_b = P.nrb_b;
     fp.item0_b = 0;
@@ -1012,6 +1093,10 @@ int run_feast(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, int* fpm, dou
         o[12] = (double)cplx_bytes(P);
         o[13] = (double)P.G;
         o[14] = (double)k;
+        o[16] = (double)B.RB;
+        o[17] = B.wrb ? 1.0 : 0.0;
+        o[18] = (double)(B.wrb ? B.wgrid : 0);
+        o[19] = (double)(B.wrb ? B.wcapr : 0);
     }
     return info;
 }
@@ -1887,7 +1972,7 @@ extern "C" int feast_scsr_grad(char uplo, int n, const int* ia, const int* ja, c
 
 extern "C" int feast_last_profile(double* out)
 {
-    for (int i = 0; i < 16; ++i) out[i] = g_prof.out[i];
+    for (int i = 0; i < 20; ++i) out[i] = g_prof.out[i];
     return 0;
 }
 

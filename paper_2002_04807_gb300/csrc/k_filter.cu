@@ -42,6 +42,8 @@
 // order.  No CTA has to read more than 64 slots, so no single CTA carries a
 // long reduction at the end of a launch.
 #include "feast_internal.cuh"
+#include <climits>
+#include <algorithm>
 
 namespace feast {
 
@@ -560,6 +562,345 @@ __global__ void __launch_bounds__(kThreads, FEAST_MINB_B) cocg_step_b(FilterArgs
     }
 }
 
+// ---------------------------------------------------------------- staged-window gather
+// Step A's rows read r at the columns of their entries.  For matrices whose
+// row blocks touch a few contiguous column ranges (stencils and other
+// locally numbered problems), a work item of RBW rows copies exactly those
+// ranges ("windows") of the group tile into shared memory with bulk
+// asynchronous copies -- one instruction per window, no registers held while
+// the bytes are in flight -- and gathers from shared memory.  The entries'
+// column indices are rewritten once per matrix into positions within the row
+// block's staged windows (win_build).  A CTA accumulates its partial sums over
+// all its items of a group and publishes them once per group, so the
+// publication cost (a fence and a counter) is paid per CTA, not per item.
+static constexpr int kWinGap = 4;      // column gaps up to this many rows are staged rather than split
+static constexpr int kWinKeys = 4096;  // sort capacity per row block (entries + own rows)
+
+__device__ __forceinline__ void mbar_init(unsigned addr, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned addr, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned addr, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase with the given parity: false after `limit` SM
+// clock cycles without completion.
+__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity, long long limit)
+{
+    const long long t0 = clock64();
+    while (!mbar_try(addr, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+// Bulk copy global -> shared (TMA engine), completion counted on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Ascending bitonic sort of key[0, P2) in shared memory (P2 a power of two);
+// all threads of the CTA take part.
+__device__ void block_bitonic(int* key, int P2)
+{
+    for (int k = 2; k <= P2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < P2; t += blockDim.x) {
+                const int u = t ^ j;
+                if (u > t) {
+                    const int a = key[t], b = key[u];
+                    if ((a > b) == ((t & k) == 0)) {
+                        key[t] = b;
+                        key[u] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// One CTA per row block (grid-stride): the distinct columns of its entries
+// and its own rows, sorted and merged into windows; entries rewritten with
+// staged positions (window base + column - window start).
+template <typename PK>
+__global__ void __launch_bounds__(256) win_build(int n, int rbw, int nrbw, const int* __restrict__ pp,
+                                                 const PK* __restrict__ pk, PK* __restrict__ lpk,
+                                                 int4* __restrict__ hdr, int2* __restrict__ win, int* stat)
+{
+    __shared__ int key[kWinKeys];
+    __shared__ int ws[kWinMax], we[kWinMax], wb[kWinMax];
+    __shared__ int s_kv, s_nw, s_ok;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int rb = blockIdx.x; rb < nrbw; rb += gridDim.x) {
+        const int row0 = rb * rbw, row1 = min(n, row0 + rbw), rows = row1 - row0;
+        const int e0 = pp[row0], cnt = pp[row1] - e0;
+        const int K = cnt + rows;
+        if (K > kWinKeys) {
+            if (tid == 0) atomicAdd(stat + 2, 1);
+            continue;
+        }
+        int P2 = 1;
+        while (P2 < K) P2 <<= 1;
+        int bad = 0;
+        for (int t = tid; t < P2; t += blockDim.x) {
+            int kv = INT_MAX;
+            if (t < cnt) {
+                const int j = pk[e0 + t].x;
+                if (j < -1 || j >= n) bad = 1;
+                else if (j >= 0) kv = j;
+            } else if (t < K) {
+                kv = row0 + (t - cnt);
+            }
+            key[t] = kv;
+        }
+        if (tid == 0) s_kv = 0;
+        if (__syncthreads_or(bad)) {
+            if (tid == 0) atomicAdd(stat + 3, 1);
+            continue;
+        }
+        block_bitonic(key, P2);
+        for (int t = tid; t < P2; t += blockDim.x)
+            if (key[t] != INT_MAX && (t + 1 == P2 || key[t + 1] == INT_MAX)) s_kv = t + 1;
+        __syncthreads();
+        if (tid < 32) {  // windows: runs of keys with gaps <= kWinGap
+            const int kv = s_kv;
+            int nw = 0;
+            for (int base = 0; base < kv; base += 32) {
+                const int t = base + lane;
+                const int k = t < kv ? key[t] : 0;
+                const bool st = t < kv && (t == 0 || k - key[t - 1] > kWinGap);
+                const bool en = t < kv && (t + 1 == kv || key[t + 1] - k > kWinGap);
+                const unsigned m = __ballot_sync(0xffffffffu, st);
+                if (st) {
+                    const int w = nw + __popc(m & ((1u << lane) - 1u));
+                    if (w < kWinMax) ws[w] = k;
+                }
+                if (en) {
+                    const int w = nw + __popc(m & ((2u << lane) - 1u)) - 1;
+                    if (w < kWinMax) we[w] = k + 1;
+                }
+                nw += __popc(m);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                int ok = nw <= kWinMax, total = 0, own = 0;
+                if (ok) {
+                    for (int w = 0; w < nw; ++w) {
+                        wb[w] = total;
+                        if (ws[w] <= row0 && row0 < we[w]) own = total + row0 - ws[w];
+                        win[(size_t)rb * kWinMax + w] = make_int2(ws[w], we[w] - ws[w]);
+                        total += we[w] - ws[w];
+                    }
+                    hdr[rb] = make_int4(nw, total, own, cnt);
+                    atomicMax(stat + 0, total);
+                    atomicMax(stat + 1, cnt);
+                } else {
+                    atomicAdd(stat + 2, 1);
+                }
+                s_nw = nw;
+                s_ok = ok;
+            }
+        }
+        __syncthreads();
+        if (s_ok) {
+            const int nw = s_nw;
+            for (int t = tid; t < cnt; t += blockDim.x) {
+                PK e = pk[e0 + t];
+                if (e.x >= 0) {
+                    int w = 0;
+                    while (w + 1 < nw && e.x >= ws[w + 1]) ++w;
+                    e.x = wb[w] + e.x - ws[w];
+                }
+                lpk[e0 + t] = e;
+            }
+        }
+        __syncthreads();  // shared tables are rewritten by the next row block
+    }
+}
+
+// Step A on staged windows: same arithmetic as cocg_step_a (s = (zB - A) r,
+// p = r + beta p, q = s + beta q, partial sums of p^T q and, at k = 0,
+// ||r||^2), single problem, B the identity (BM 0) or diagonal (BM 1).  The
+// launch grid must not exceed the row blocks per group, so that every CTA
+// has items in every group and each group's partial sums arrive from exactly
+// gridDim.x CTAs (slot = blockIdx.x).
+template <typename T, int W, int BM, int RBW>
+__global__ void __launch_bounds__(kThreads, 2) cocg_step_aw(FilterArgs a, int kk)
+{
+    const int k = a.kdev ? *a.kdev : kk;
+    using V = c2_t<T>;
+    constexpr int RPP = kThreads / W;   // rows per pass of the CTA
+    constexpr int RPT = RBW / RPP;      // rows per thread per item
+    static_assert(RBW % RPP == 0, "row block must be a whole number of passes");
+    constexpr unsigned ROWB = W * sizeof(V);                // bytes per tile row
+    constexpr unsigned ENTB = sizeof(T) == 4 ? 8u : 16u;    // bytes per packed entry
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ double sm[kThreads * 3];
+    __shared__ double red[W * kPartStride];
+    __shared__ int flag;
+    __shared__ int s_pp[RBW + 1];
+    __shared__ __align__(8) unsigned long long mbar;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int cl = tid % W, rowslot = tid / W;
+    const bool first = (k == 0);
+    // staged rows from a 128-byte boundary of the dynamic shared memory (bulk
+    // copies need 16-byte aligned destinations; the request includes the pad)
+    const unsigned dsm_sh = (unsigned)__cvta_generic_to_shared(dsm);
+    const unsigned xs_sh = (dsm_sh + 127u) & ~127u;
+    const unsigned ent_sh = xs_sh + (unsigned)a.wcapr * ROWB;
+    const V* xs = (const V*)(dsm + (xs_sh - dsm_sh));
+    const int4* sent = (const int4*)(dsm + (ent_sh - dsm_sh));
+    const unsigned mb = (unsigned)__cvta_generic_to_shared(&mbar);
+    if (tid == 0) {
+        mbar_init(mb, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    unsigned parity = 0;
+
+    const FiltProb& P = a.probs[0];
+    const int n = P.n, nrb = P.nrb;
+    const V zero = cmk<V>(T(0), T(0));
+    int cur = -1;
+    bool skip = false, use_p = false;
+    V z = zero, beta = zero;
+    const V* rl_ = nullptr;
+    V *pl_ = nullptr, *ql_ = nullptr;
+    const char* rtile = nullptr;
+    double accd[3] = {0.0, 0.0, 0.0};
+    for (long long item = blockIdx.x;; item += gridDim.x) {
+        const bool have = item < a.nitems;
+        const int g = have ? (int)(item / nrb) : -1;
+        if (g != cur) {
+            if (cur >= 0 && !skip) {  // publish this CTA's sums over its items of group cur
+                const int gi = P.grp_off + cur;
+                double* gslots = a.part + (size_t)gi * a.nslot * kPartStride * W;
+                item_partials<W, 3>(accd, sm, gslots + (size_t)blockIdx.x * kPartStride * W);
+                if (tree_arrive<W, 3>(gslots, gridDim.x, blockIdx.x, a.bk_count + (size_t)gi * a.nbk,
+                                      a.grp_count + gi, sm, red, &flag))
+                    finish_group_a<W>(a.cs + P.col_off + (size_t)cur * W, first, red);
+            }
+            if (!have) break;
+            cur = g;
+            skip = a.grp_done[P.grp_off + g] != 0;
+            accd[0] = accd[1] = accd[2] = 0.0;
+            const ColState* csg = a.cs + P.col_off + (size_t)g * W;
+            const int active = csg[cl].active;
+            const double2 zd = csg[cl].z, bd = csg[cl].beta;
+            z = cmk<V>((T)zd.x, (T)zd.y);
+            beta = cmk<V>((T)bd.x, (T)bd.y);
+            use_p = !first && active;
+            const size_t tile = (size_t)P.vec_off + (size_t)g * n * W;
+            rl_ = (const V*)a.r + tile;
+            rtile = (const char*)rl_;
+            pl_ = (V*)a.p0 + tile + cl;
+            ql_ = (V*)a.p1 + tile + cl;
+        }
+        if (skip) continue;
+        const int rb = (int)(item - (long long)g * nrb);
+        const int row0 = rb * RBW, row1 = min(n, row0 + RBW);
+        const int4 h = __ldg(a.whdr + rb);  // windows, staged rows, own position, entries
+        const int e0 = __ldg(P.app + row0);
+        if (tid < 32) {  // one lane per window issues its bulk copy; lane 31 copies the entries
+            int2 wv = make_int2(0, 0);
+            if (lane < h.x) wv = __ldg(a.wwin + (size_t)rb * kWinMax + lane);
+            int pos = wv.y;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, pos, o);
+                if (lane >= o) pos += t;
+            }
+            pos -= wv.y;
+            fence_proxy_async_smem();
+            if (lane == 0) mbar_expect_tx(mb, (unsigned)h.y * ROWB + (unsigned)h.w * ENTB);
+            __syncwarp();
+            if (lane < h.x)
+                bulk_g2s(xs_sh + (unsigned)pos * ROWB, rtile + (size_t)wv.x * ROWB, (unsigned)wv.y * ROWB, mb);
+            if (lane == 31 && h.w > 0)
+                bulk_g2s(ent_sh, (const char*)a.wpk + (size_t)e0 * ENTB, (unsigned)h.w * ENTB, mb);
+        }
+        // own-row streams while the windows are in flight
+        V po[RPT], qo[RPT];
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            const int i = row0 + rowslot + u * RPP;
+            po[u] = zero;
+            qo[u] = zero;
+            if (use_p && i < row1) {
+                po[u] = pl_[(size_t)i * W];
+                qo[u] = ql_[(size_t)i * W];
+            }
+        }
+        for (int t = tid; t <= row1 - row0; t += kThreads) s_pp[t] = __ldg(P.app + row0 + t) - e0;
+        __syncthreads();
+        const bool ok = mbar_wait(mb, parity, a.wlimit);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(a.werr, 1);
+            mbar_wait(mb, parity, a.wlimit);  // let copies still in flight land before the CTA exits
+            return;
+        }
+        parity ^= 1u;
+        T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            const int i = row0 + rowslot + u * RPP;
+            if (i < row1) {
+                const int c0 = s_pp[i - row0], c1 = s_pp[i - row0 + 1];
+                V ar = zero;
+                for (int c = c0; c < c1; c += kChunk) {
+                    int j[kChunk];
+                    T av[kChunk];
+                    load_chunk<T, true>(sent, c, j, av);
+                    V xv[kChunk];
+#pragma unroll
+                    for (int v = 0; v < kChunk; ++v) xv[v] = j[v] >= 0 ? xs[(size_t)j[v] * W + cl] : zero;
+#pragma unroll
+                    for (int v = 0; v < kChunk; ++v) {
+                        ar.x = fma(av[v], xv[v].x, ar.x);
+                        ar.y = fma(av[v], xv[v].y, ar.y);
+                    }
+                }
+                const V ri = xs[(size_t)(h.z + i - row0) * W + cl];
+                V bx = ri;
+                if (BM == 1) {
+                    const T b = ((const T*)P.bd)[i];
+                    bx = cmk<V>(b * ri.x, b * ri.y);
+                }
+                V pi_ = ri, qi = csub(cmul(z, bx), ar);  // (zB - A) r
+                if (use_p) {
+                    pi_ = cfma(beta, po[u], pi_);
+                    qi = cfma(beta, qo[u], qi);
+                }
+                pl_[(size_t)i * W] = pi_;
+                ql_[(size_t)i * W] = qi;
+                acc[0] = fma(pi_.x, qi.x, fma(-pi_.y, qi.y, acc[0]));
+                acc[1] = fma(pi_.x, qi.y, fma(pi_.y, qi.x, acc[1]));
+                if (first) acc[2] = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[2]));
+            }
+        }
+        accd[0] += (double)acc[0];
+        accd[1] += (double)acc[1];
+        accd[2] += (double)acc[2];
+        __syncthreads();  // staged rows and entries are free for the next item's copies
+    }
+}
+
 // ---------------------------------------------------------------- init
 // Column states for one node batch: node e = node0 + (lane % nbp) of the
 // problem's Ne nodes, subspace column m; coefficient c = w_e (first pass) or
@@ -830,6 +1171,93 @@ cudaError_t launch_cocg_step_a(const FilterArgs& a, bool fp64, int k, int grid, 
 cudaError_t launch_cocg_step_b(const FilterArgs& a, bool fp64, int k, int grid, cudaStream_t s)
 {
     FEAST_DISPATCH_B(cocg_step_b, a, k);
+}
+
+// ---------------------------------------------------------------- staged-window launchers
+cudaError_t launch_win_build(int n, int rbw, const int* pp, const void* pk, bool fp64, void* lpk, int4* hdr,
+                             int2* win, int* stat, cudaStream_t s)
+{
+    if (n <= 0 || rbw <= 0) return cudaSuccess;
+    const int nrbw = (n + rbw - 1) / rbw;
+    const int grid = std::min(nrbw, num_sms() * 8);
+    if (fp64)
+        win_build<int4><<<grid, 256, 0, s>>>(n, rbw, nrbw, pp, (const int4*)pk, (int4*)lpk, hdr, win, stat);
+    else
+        win_build<int2><<<grid, 256, 0, s>>>(n, rbw, nrbw, pp, (const int2*)pk, (int2*)lpk, hdr, win, stat);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+size_t win_smem_bytes(bool fp64, int W, int capr, int cape)
+{
+    const size_t cb = fp64 ? 16 : 8;  // complex element, and packed entry, bytes
+    return 128 + (size_t)capr * W * cb + (size_t)cape * cb;  // + alignment pad of the staged rows
+}
+
+// Allows the variant the largest dynamic shared memory the device gives a CTA
+// (idempotent), then returns its resident CTAs per SM at `smem` bytes.
+template <typename T, int W, int BM, int RBW>
+static int aw_occupancy(size_t smem)
+{
+    auto kern = cocg_step_aw<T, W, BM, RBW>;
+    cudaFuncAttributes fa;
+    int dev = 0, optin = 0;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const long long room = (long long)optin - (long long)fa.sharedSizeBytes;
+    if (room <= 0 || (long long)smem > room) return 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)room) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return o;
+}
+
+template <typename T, int W>
+static int aw_occupancy_tw(int bmode, int rbw, size_t smem)
+{
+    if (bmode == 0 && rbw == 64) return aw_occupancy<T, W, 0, 64>(smem);
+    if (bmode == 0 && rbw == 32) return aw_occupancy<T, W, 0, 32>(smem);
+    if (bmode == 1 && rbw == 64) return aw_occupancy<T, W, 1, 64>(smem);
+    if (bmode == 1 && rbw == 32) return aw_occupancy<T, W, 1, 32>(smem);
+    return 0;
+}
+
+// Variants built: complex FP32 with 32 lanes, complex FP64 with 16 lanes (a
+// 256-byte tile row each); B the identity or diagonal; 32 or 64 rows per item.
+int win_occupancy(bool fp64, int W, int bmode, int rbw, size_t smem)
+{
+    if (!fp64 && W == 32) return aw_occupancy_tw<float, 32>(bmode, rbw, smem);
+    if (fp64 && W == 16) return aw_occupancy_tw<double, 16>(bmode, rbw, smem);
+    return 0;
+}
+
+template <typename T, int W>
+static cudaError_t aw_launch_tw(const FilterArgs& a, int rbw, int k, int grid, size_t smem, cudaStream_t s)
+{
+    if (a.bmode == 0 && rbw == 64) cocg_step_aw<T, W, 0, 64><<<grid, kThreads, smem, s>>>(a, k);
+    else if (a.bmode == 0 && rbw == 32) cocg_step_aw<T, W, 0, 32><<<grid, kThreads, smem, s>>>(a, k);
+    else if (a.bmode == 1 && rbw == 64) cocg_step_aw<T, W, 1, 64><<<grid, kThreads, smem, s>>>(a, k);
+    else if (a.bmode == 1 && rbw == 32) cocg_step_aw<T, W, 1, 32><<<grid, kThreads, smem, s>>>(a, k);
+    else return cudaErrorInvalidValue;
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cocg_step_aw(const FilterArgs& a, bool fp64, int rbw, int k, int grid, size_t smem,
+                                cudaStream_t s)
+{
+    if (!fp64 && a.W == 32) return aw_launch_tw<float, 32>(a, rbw, k, grid, smem, s);
+    if (fp64 && a.W == 16) return aw_launch_tw<double, 16>(a, rbw, k, grid, smem, s);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_filter_init(const FilterArgs& a, bool fp64, const double* R, const double* X, int rii,

@@ -363,3 +363,79 @@ def test_bench_workload_properties(pkg):
     assert full.info == 0 and full.M == M
     assert (np.abs(mixed.E[:M] - full.E[:M]) / mixed.E[:M]).max() <= EIG_TOL
     assert cluster_angles(mixed.E[:M], X, full.E[:M], full.X[:, :M], p.emax) <= ANG_TOL
+
+
+def _scattered_spd(n, per_row, seed):
+    """SPD matrix whose rows read columns spread over the whole range (random
+    symmetric off-diagonal pattern, diagonally dominant): its row blocks read
+    far more than 16 separate column ranges."""
+    rng = np.random.default_rng(seed)
+    r = np.repeat(np.arange(n), per_row)
+    c = rng.integers(0, n, size=n * per_row)
+    keep = r != c
+    r, c = r[keep], c[keep]
+    v = -rng.uniform(0.1, 1.0, size=r.size)
+    rows = np.concatenate([r, c])
+    cols = np.concatenate([c, r])
+    vals = np.concatenate([v, v])
+    off = fw.csr_from_coo(n, rows, cols, vals)
+    diag = np.zeros(n)
+    np.add.at(diag, off.indices, 0.0)
+    for i in range(n):
+        diag[i] = -off.data[off.indptr[i]:off.indptr[i + 1]].sum() + rng.uniform(0.0, 1.0)
+    i = np.arange(n)
+    return fw.csr_from_coo(n, np.concatenate([rows, i]), np.concatenate([cols, i]), np.concatenate([vals, diag]))
+
+
+def _step_a_problems():
+    rng = np.random.default_rng(7)
+    s27 = fw.stencil27_spd(12, rng)
+    bd = fw.diagonal_csr(rng.uniform(1.0, 2.0, s27.n))
+    ev = np.linalg.eigvalsh(np.diag(1 / np.sqrt(bd.data)) @ s27.to_dense() @ np.diag(1 / np.sqrt(bd.data)))
+    p27 = fw.Problem("s27", s27, bd, 0.0, 0.5 * (ev[29] + ev[30]), 48, 8, 100, 3)
+    sc = _scattered_spd(1200, 4, 11)
+    evs = np.linalg.eigvalsh(sc.to_dense())
+    k = 8 + int(np.argmax(np.diff(evs[8:26])))  # interval edge in the widest gap after the 9th eigenvalue
+    psc = fw.Problem("scattered", sc, None, evs[0] - 1e-3, 0.5 * (evs[k] + evs[k + 1]), k + 12, 8, 100, 5)
+    return {"laplace3d": (fw.laplace3d_potential(side=14, count=24, m0=40, seed=7), 1),
+            "stencil27_diag_b": (p27, 1),
+            "scattered": (psc, 0)}
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+@pytest.mark.parametrize("name", ["laplace3d", "stencil27_diag_b", "scattered"])
+def test_step_a_staged_and_cached_gathers_agree(pkg, name, mixed):
+    """COCG step A either stages the rows of r each work item reads (windows
+    copied into shared memory by the bulk-copy engine; default when the row
+    blocks read few contiguous column ranges) or gathers through the caches
+    (fpm(51) > 0, and matrices whose rows scatter).  Both give the oracle's
+    eigenpairs, and each choice is the one the profile reports."""
+    p, staged = _step_a_problems()[name]
+    if name == "scattered":  # dense reference (the oracle's COCG converges slowly on this pattern)
+        ev, V = np.linalg.eigh(p.A.to_dense())
+        sel = (ev >= p.emin) & (ev <= p.emax)
+        ref = {"M": int(sel.sum()), "E": ev[sel], "X": V[:, sel]}
+    else:
+        ref = O.feast_scsr(p.A, p.B, p.emin, p.emax, p.m0, Y0=p.y0(), ne=p.ne, ratio=p.ratio, tol_exp=10)
+        assert ref["info"] == 0
+    out = []
+    for rows in (0, 256):
+        fpm = pkg.feast_init()
+        fpm[1], fpm[2], fpm[3], fpm[4], fpm[17], fpm[41] = p.ne, 10, 30, 1, p.ratio, mixed
+        fpm[44], fpm[45], fpm[50], fpm[52] = 2, 200, rows, 1
+        kw = {} if p.B is None else dict(b=p.B.data, ib=p.B.indptr, jb=p.B.indices)
+        r = pkg.feast_scsr_solve("F", p.n, p.A.data, p.A.indptr, p.A.indices, fpm=fpm, emin=p.emin,
+                                 emax=p.emax, m0=p.m0, x0=p.y0(), **kw)
+        prof = pkg.feast_last_profile()
+        check_against(r, ref, max(abs(p.emax), abs(p.emin)), B=p.B)
+        want = staged if rows == 0 else 0
+        assert int(prof["step_a_staged"]) == want, prof
+        if want:
+            assert int(prof["step_a_rows_per_item"]) in (32, 64)
+            assert 1 <= int(prof["step_a_grid"]) <= -(-p.n // int(prof["step_a_rows_per_item"]))
+        else:
+            assert int(prof["step_a_rows_per_item"]) == 256
+        out.append(r)
+    M = out[0].M
+    assert out[1].M == M
+    assert np.abs(out[0].E[:M] - out[1].E[:M]).max() <= 1e-11 * max(abs(p.emax), abs(p.emin))
