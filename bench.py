@@ -89,6 +89,26 @@ ROWS_PER_ITEM = 0
 INNER = (2, 80)  # fpm(45), fpm(46) of the 64^3 workload
 
 
+def cocg_rates(pr, p):
+    """Algorithmic GB/s of the two COCG launches of a profiled solve (per-launch
+    CUDA events): step A gathers r and reads and writes p, q; step B reads r,
+    p, q, writes r and updates the quadrature accumulator.  Padded lanes and
+    the matrix's padding entries are not counted."""
+    n, W, mt, sc, G = pr["n"], pr["W"], pr["mt"], pr["complex_bytes"], pr["groups"]
+    nbp = W / mt  # node lanes per column in a tile
+    live = (p.m0 * min(nbp, p.ne)) / (G * W)
+    mat = p.A.nnz * (4 + (4 if sc == 8 else 8)) + (p.n + 1) * 4
+    if p.B is not None:
+        mat += p.n * (sc // 2)  # diagonal of B in the filter precision
+    tile = n * W * sc * live
+    qb = 4 if sc == 8 else 8  # quadrature accumulator: FP32 in mixed precision
+    bytes_a = pr["group_iterations"] * 5 * tile + pr["cocg_a_launches"] * mat
+    bytes_b = pr["group_iterations"] * (4 * tile + n * mt * 2 * qb * live)
+    gbs_a = bytes_a / (pr["cocg_a_ms"] / 1e3) / 1e9
+    gbs_b = bytes_b / (pr["cocg_b_ms"] / 1e3) / 1e9
+    return gbs_a, gbs_b
+
+
 def fpm_for(pkg, p, mixed, profile):
     f = pkg.feast_init()
     f[1], f[2], f[3], f[4], f[17] = p.ne, 10, 40, 1, p.ratio
@@ -328,17 +348,7 @@ def run_gpu(args):
 
     # roofline of the dominant kernel from the per-launch events of the profiled solve
     pr = prof_tot
-    n, W, mt, sc, G = pr["n"], pr["W"], pr["mt"], pr["complex_bytes"], pr["groups"]
-    nbp = W / mt  # node lanes per column in a tile
-    live = (p.m0 * min(nbp, p.ne)) / (G * W)  # padded lanes are not algorithmic work
-    mat = p.A.nnz * (4 + (4 if sc == 8 else 8)) + (p.n + 1) * 4
-    tile = n * W * sc * live
-    # step A: r (gathered) + p, q read + p, q written; step B: r, p, q read + r written + accumulator
-    bytes_a = pr["group_iterations"] * 5 * tile + pr["cocg_a_launches"] * mat
-    qb = 4 if sc == 8 else 8  # quadrature accumulator: FP32 in mixed precision
-    bytes_b = pr["group_iterations"] * (4 * tile + n * mt * 2 * qb * live)
-    gbs_a = bytes_a / (pr["cocg_a_ms"] / 1e3) / 1e9
-    gbs_b = bytes_b / (pr["cocg_b_ms"] / 1e3) / 1e9
+    gbs_a, gbs_b = cocg_rates(pr, p)
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak, peak_src = FALLBACK_HBM_GBS, "fallback"
     if os.path.exists(peaks_path):
@@ -351,18 +361,21 @@ def run_gpu(args):
         except (ValueError, OSError):
             pass
     dom = "cocg_step_a" if pr["cocg_a_ms"] >= pr["cocg_b_ms"] else "cocg_step_b"
-    ach = gbs_a if dom == "cocg_step_a" else gbs_b
+    ach = gbs_b if dom == "cocg_step_b" else gbs_a
     import hashlib
 
     src = os.path.join(ROOT, "paper_2002_04807_gb300", "csrc", "k_filter.cu")
     traffic = None
-    if hashlib.sha1(open(src, "rb").read()).hexdigest() == NCU_TRAFFIC["source_sha1"] and args.side == 64:
+    if (hashlib.sha1(open(src, "rb").read()).hexdigest() == NCU_TRAFFIC["source_sha1"] and args.side == 64
+            and dom in NCU_TRAFFIC):
         launches = pr["cocg_a_launches"] if dom == "cocg_step_a" else pr["cocg_b_launches"]
         # per launch, averaged like `achieved`: per-group traffic x active groups per launch
         traffic = NCU_TRAFFIC[dom] * pr["group_iterations"] / max(launches, 1)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "peak_source": peak_src,
                 "unit": "GB/s", "frac": ach / peak, "traffic": traffic,
                 "cocg_step_a_gbs": gbs_a, "cocg_step_b_gbs": gbs_b,
+                "step_a_staged": int(pr.get("step_a_staged", 0)),
+                "step_a_rows_per_item": int(pr.get("step_a_rows_per_item", 0)),
                 "cocg_share_of_step": (pr["cocg_a_ms"] + pr["cocg_b_ms"]) / (ms / args.steps),
                 "timing": "CUDA events around every COCG launch of one extra solve after the timed region "
                           f"({int(pr['cocg_a_launches'])} step-A launches, {pr['filter_ms']:.0f} ms of filter)"}
@@ -551,12 +564,7 @@ def run_stencil27(args):
     res = np.linalg.norm(AX - BX * E[None, :], axis=0) / (alpha * np.linalg.norm(BX, axis=0))
     checks = {"M": M, "wanted": k, "max_residual_cpu_fp64": float(res.max()),
               "max_abs_XtBX_minus_I": float(np.abs(X.T @ BX - np.eye(M)).max())}
-    n, W, mt, sc = pr["n"], pr["W"], pr["mt"], pr["complex_bytes"]
-    live = (p.m0 * min(W / mt, p.ne)) / (pr["groups"] * W)
-    tile = n * W * sc * live
-    mat = p.A.nnz * (4 + (4 if sc == 8 else 8)) + (p.n + 1) * 4
-    gbs_a = (pr["group_iterations"] * 5 * tile + pr["cocg_a_launches"] * mat) / (pr["cocg_a_ms"] / 1e3) / 1e9
-    gbs_b = pr["group_iterations"] * (4 * tile + n * mt * 2 * 4 * live) / (pr["cocg_b_ms"] / 1e3) / 1e9
+    gbs_a, gbs_b = cocg_rates(pr, p)
     peak = FALLBACK_HBM_GBS
     try:
         peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
@@ -573,7 +581,8 @@ def run_stencil27(args):
                           "interval_from": "feast_scsr_extreme_dev, fpm(40)=-1, M0 = 2 x 200",
                           "interval_search_s": t_search, "loops": r.loop, "precision": "mixed fpm(42)=1"},
                "fp64": fp64, "checks": checks, "clocks": clk,
-               "cocg_gbs": {"step_a": gbs_a, "step_b": gbs_b, "peak": peak},
+               "cocg_gbs": {"step_a": gbs_a, "step_b": gbs_b, "peak": peak,
+                            "step_a_staged": int(pr.get("step_a_staged", 0))},
                "phases_ms_per_step": {kk: pr[kk] / args.steps for kk in ("filter_ms", "project_ms", "reduce_ms",
                                                                           "ritz_ms")},
                "gpu_launches": int(pr["launches"])}

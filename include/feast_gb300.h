@@ -126,7 +126,7 @@ int feast_contour_nodes_rule(int rule, int ne, double emin, double emax, int rat
  * [16] rows per step-A work item, [17] 1 when step A stages the rows it
  * gathers in shared memory (windows of r copied by the bulk-copy engine),
  * 0 when it gathers through the caches, [18] step A CTAs (staged variant),
- * [19] staged rows per CTA (staged variant).
+ * [19] staged rows per row block (staged variant).
  * Library extension (the guide reports phase timings only as a text log).
  * Returns 0. */
 int feast_last_profile(double* out);

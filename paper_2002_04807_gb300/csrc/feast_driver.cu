@@ -801,7 +801,10 @@ int choose_step_a(const Plan& P, Bufs& B, cudaStream_t s)
     B.nitems = P.nitems;
     B.wrb = 0;
     if (!P.win || B.bmode == 2) return 0;
-    for (const int rbw : {64, 32}) {
+#ifndef FEAST_WIN_RB_FIRST
+#define FEAST_WIN_RB_FIRST 64  // rows per staged item tried first (then the other of 64, 32)
+#endif
+    for (const int rbw : {FEAST_WIN_RB_FIRST, 96 - FEAST_WIN_RB_FIRST}) {
         int st4[4] = {0, 0, 0, 0};
         CK(cudaMemsetAsync(B.wstat, 0, sizeof(st4), s));
         CK(launch_win_build(P.n, rbw, B.app, B.apk, P.fp64, B.wpk, B.whdr, B.wwin, B.wstat, s));
@@ -809,14 +812,14 @@ int choose_step_a(const Plan& P, Bufs& B, cudaStream_t s)
         CK(cudaStreamSynchronize(s));
         if (st4[3]) return 0;  // column indices outside [0, n): leave the matrix to the general path
         if (st4[2]) continue;
+        const int nrbw = (P.n + rbw - 1) / rbw;
         const size_t smem = win_smem_bytes(P.fp64, P.W, st4[0], st4[1]);
         const int occ = std::min(4, win_occupancy(P.fp64, P.W, B.bmode, rbw, smem));
         if (occ < 2) continue;
-        const int nrbw = (P.n + rbw - 1) / rbw;
-        B.wrb = rbw;
         B.wsmem = smem;
-        B.wcapr = st4[0];
         B.wgrid = std::min(num_sms() * occ, nrbw);
+        B.wrb = rbw;
+        B.wcapr = st4[0];
         B.RB = rbw;
         B.nrb = nrbw;
         B.nitems = (long long)P.G * nrbw;

@@ -170,6 +170,7 @@ int h_filter_pass(HBufs& B, const HMat& A, const HMat& Bm, bool hasB, int m, int
         *iters += it;
         *capped += B.nactive_host[1];
     }
+    HCK(launch_h_fold(a, s));
     return 0;
 }
 
@@ -246,6 +247,7 @@ size_t h_carve(const HPlan& P, void* base, HBufs& B, float2** af, float2** bf)
     B.red = c.take<char>(h_reduced_work_bytes(P.m0));
     void** fv[6] = {&B.fa.r, &B.fa.rh, &B.fa.p, &B.fa.ph, &B.fa.q, &B.fa.qh};
     for (void** v : fv) *v = c.take<char>((size_t)P.n * P.Lmax * vb);
+    B.fa.dQ = P.fp64 ? nullptr : c.take<float2>(blk);
     B.fa.st = c.take<HLane>(P.Lmax);
     B.fa.part = c.take<double2>((size_t)row_blocks(P.n) * 2 * P.Lmax);
     *af = P.fp64 ? nullptr : c.take<float2>(P.nnz_a);

@@ -41,6 +41,8 @@ struct HArgs {
     HLane* st;      // lane state [L]
     double2* part;  // partial sums [nrbk][2][L]
     double2* Q;     // FP64 quadrature block, n x m complex (row-major)
+    void* dQ;       // complex FP32 accumulator of one contour pass, n x m (row-major), folded
+                    // into Q after the pass (mixed precision); nullptr: steps add to Q
     double tol2;    // squared relative BiCG tolerance
     int* nactive;   // [0]: lanes still iterating after the last finish_b; [1]: lanes stopped by
                     // the iteration cap since the counter was last cleared (device)
@@ -59,6 +61,8 @@ cudaError_t launch_h_init(const HArgs& a, bool fp64, const double2* b, const dou
                           const double* lam, int rii, int ne_all, const double* zw_all, int init_q, cudaStream_t s);
 // One BiCG step (four launches); *a.nactive = lanes still iterating after it.
 cudaError_t launch_h_step(const HArgs& a, bool fp64, int maxit, cudaStream_t s);
+// Q += dQ (n x m complex) after a contour pass
+cudaError_t launch_h_fold(const HArgs& a, cudaStream_t s);
 // complex CSR values: double2 -> float2 (mixed precision) or copy
 cudaError_t launch_h_cast(const double2* src, void* dst, long long n, bool fp64, cudaStream_t s);
 

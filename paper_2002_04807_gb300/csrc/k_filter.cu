@@ -60,6 +60,9 @@ static constexpr int kMaxRB = 512;  // rows per work item, at most
 #ifndef FEAST_MINB_B
 #define FEAST_MINB_B 5
 #endif
+#ifndef FEAST_AW_MINB
+#define FEAST_AW_MINB 2  // resident CTAs per SM the staged step A is compiled for
+#endif
 
 __device__ __forceinline__ int find_prob(const FiltProb* probs, int nprob, long long item)
 {
@@ -193,26 +196,41 @@ __device__ __forceinline__ bool stage_rows(const int* __restrict__ pp, const voi
 // written to the work item's slot.  A slot holds kPartStride rows of W
 // doubles (slot[q * W + cl]), so one value of every lane is one coalesced
 // row.  Fixed order.
+// The sums run in the values' own type and only the W results are widened:
+// GB300 issues FP64 arithmetic and conversions at a small fraction of the FP32
+// rate, so per-thread FP64 work in a per-item reduction costs more than the item.
 template <int W, int NV, typename T>
 __device__ __forceinline__ void item_partials(T (&v)[NV], double* sm, double* slot)
 {
     constexpr int SEGS = kThreads / W;
     const int tid = threadIdx.x;
     const int cl = tid % W, seg = tid / W;
+    T* st = reinterpret_cast<T*>(sm);
 #pragma unroll
-    for (int q = 0; q < NV; ++q) sm[(seg * W + cl) * NV + q] = (double)v[q];
+    for (int q = 0; q < NV; ++q) st[(seg * W + cl) * NV + q] = v[q];
     __syncthreads();
     if (tid < W) {
-        double s[NV];
+        T s[NV];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) s[q] = 0.0;
+        for (int q = 0; q < NV; ++q) s[q] = T(0);
         for (int g = 0; g < SEGS; ++g)
 #pragma unroll
-            for (int q = 0; q < NV; ++q) s[q] += sm[(g * W + tid) * NV + q];
+            for (int q = 0; q < NV; ++q) s[q] += st[(g * W + tid) * NV + q];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) slot[(size_t)q * W + tid] = s[q];
+        for (int q = 0; q < NV; ++q) slot[(size_t)q * W + tid] = (double)s[q];
     }
     __syncthreads();
+}
+
+// Compensated (Kahan) running sum in the filter precision: s - c carries the
+// sum of the added values to about one rounding of the type.
+template <typename T>
+__device__ __forceinline__ void kahan_add(T& s, T& c, T x)
+{
+    const T y = x - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
 }
 
 // Sum of `count` consecutive slots starting at `base`, per lane, in a fixed
@@ -741,7 +759,7 @@ __global__ void __launch_bounds__(256) win_build(int n, int rbw, int nrbw, const
 // has items in every group and each group's partial sums arrive from exactly
 // gridDim.x CTAs (slot = blockIdx.x).
 template <typename T, int W, int BM, int RBW>
-__global__ void __launch_bounds__(kThreads, 2) cocg_step_aw(FilterArgs a, int kk)
+__global__ void __launch_bounds__(kThreads, FEAST_AW_MINB) cocg_step_aw(FilterArgs a, int kk)
 {
     const int k = a.kdev ? *a.kdev : kk;
     using V = c2_t<T>;
@@ -755,6 +773,7 @@ __global__ void __launch_bounds__(kThreads, 2) cocg_step_aw(FilterArgs a, int kk
     __shared__ double red[W * kPartStride];
     __shared__ int flag;
     __shared__ int s_pp[RBW + 1];
+    __shared__ int2 s_meta;
     __shared__ __align__(8) unsigned long long mbar;
     const int tid = threadIdx.x, lane = tid & 31;
     const int cl = tid % W, rowslot = tid / W;
@@ -783,7 +802,10 @@ __global__ void __launch_bounds__(kThreads, 2) cocg_step_aw(FilterArgs a, int kk
     const V* rl_ = nullptr;
     V *pl_ = nullptr, *ql_ = nullptr;
     const char* rtile = nullptr;
-    double accd[3] = {0.0, 0.0, 0.0};
+    T accs[3] = {T(0), T(0), T(0)}, accc[3] = {T(0), T(0), T(0)};  // this CTA's run sums (compensated)
+    int4 mh = make_int4(0, 0, 0, 0);  // warp 0: table rows of row block mrb
+    int2 mwv = make_int2(0, 0);
+    int me0 = 0, mrb = -1;
     for (long long item = blockIdx.x;; item += gridDim.x) {
         const bool have = item < a.nitems;
         const int g = have ? (int)(item / nrb) : -1;
@@ -791,6 +813,9 @@ __global__ void __launch_bounds__(kThreads, 2) cocg_step_aw(FilterArgs a, int kk
             if (cur >= 0 && !skip) {  // publish this CTA's sums over its items of group cur
                 const int gi = P.grp_off + cur;
                 double* gslots = a.part + (size_t)gi * a.nslot * kPartStride * W;
+                double accd[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) accd[q] = (double)accs[q] - (double)accc[q];
                 item_partials<W, 3>(accd, sm, gslots + (size_t)blockIdx.x * kPartStride * W);
                 if (tree_arrive<W, 3>(gslots, gridDim.x, blockIdx.x, a.bk_count + (size_t)gi * a.nbk,
                                       a.grp_count + gi, sm, red, &flag))
@@ -799,7 +824,8 @@ __global__ void __launch_bounds__(kThreads, 2) cocg_step_aw(FilterArgs a, int kk
             if (!have) break;
             cur = g;
             skip = a.grp_done[P.grp_off + g] != 0;
-            accd[0] = accd[1] = accd[2] = 0.0;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) accs[q] = accc[q] = T(0);
             const ColState* csg = a.cs + P.col_off + (size_t)g * W;
             const int active = csg[cl].active;
             const double2 zd = csg[cl].z, bd = csg[cl].beta;
@@ -815,11 +841,15 @@ __global__ void __launch_bounds__(kThreads, 2) cocg_step_aw(FilterArgs a, int kk
         if (skip) continue;
         const int rb = (int)(item - (long long)g * nrb);
         const int row0 = rb * RBW, row1 = min(n, row0 + RBW);
-        const int4 h = __ldg(a.whdr + rb);  // windows, staged rows, own position, entries
-        const int e0 = __ldg(P.app + row0);
         if (tid < 32) {  // one lane per window issues its bulk copy; lane 31 copies the entries
-            int2 wv = make_int2(0, 0);
-            if (lane < h.x) wv = __ldg(a.wwin + (size_t)rb * kWinMax + lane);
+            if (mrb != rb) {  // the table rows were not prefetched (first item, or skipped groups)
+                mh = __ldg(a.whdr + rb);
+                mwv = __ldg(a.wwin + (size_t)rb * kWinMax + (lane & (kWinMax - 1)));
+                me0 = __ldg(P.app + row0);
+            }
+            const int4 h = mh;
+            const int2 wv = lane < h.x ? mwv : make_int2(0, 0);
+            const int e0 = me0;
             int pos = wv.y;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -828,12 +858,24 @@ __global__ void __launch_bounds__(kThreads, 2) cocg_step_aw(FilterArgs a, int kk
             }
             pos -= wv.y;
             fence_proxy_async_smem();
-            if (lane == 0) mbar_expect_tx(mb, (unsigned)h.y * ROWB + (unsigned)h.w * ENTB);
+            if (lane == 0) {
+                mbar_expect_tx(mb, (unsigned)h.y * ROWB + (unsigned)h.w * ENTB);
+                s_meta = make_int2(h.z, e0);
+            }
             __syncwarp();
             if (lane < h.x)
                 bulk_g2s(xs_sh + (unsigned)pos * ROWB, rtile + (size_t)wv.x * ROWB, (unsigned)wv.y * ROWB, mb);
             if (lane == 31 && h.w > 0)
                 bulk_g2s(ent_sh, (const char*)a.wpk + (size_t)e0 * ENTB, (unsigned)h.w * ENTB, mb);
+            // the next item's table rows load while this item computes
+            const long long nx = item + gridDim.x;
+            mrb = -1;
+            if (nx < a.nitems) {
+                mrb = (int)(nx % nrb);
+                mh = __ldg(a.whdr + mrb);
+                mwv = __ldg(a.wwin + (size_t)mrb * kWinMax + (lane & (kWinMax - 1)));
+                me0 = __ldg(P.app + mrb * RBW);
+            }
         }
         // own-row streams while the windows are in flight
         V po[RPT], qo[RPT];
@@ -847,8 +889,9 @@ __global__ void __launch_bounds__(kThreads, 2) cocg_step_aw(FilterArgs a, int kk
                 qo[u] = ql_[(size_t)i * W];
             }
         }
-        for (int t = tid; t <= row1 - row0; t += kThreads) s_pp[t] = __ldg(P.app + row0 + t) - e0;
+        for (int t = tid; t <= row1 - row0; t += kThreads) s_pp[t] = __ldg(P.app + row0 + t);
         __syncthreads();
+        const int own0 = s_meta.x, e0 = s_meta.y;  // staged position of row0, first entry of the item
         const bool ok = mbar_wait(mb, parity, a.wlimit);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(a.werr, 1);
@@ -861,7 +904,7 @@ __global__ void __launch_bounds__(kThreads, 2) cocg_step_aw(FilterArgs a, int kk
         for (int u = 0; u < RPT; ++u) {
             const int i = row0 + rowslot + u * RPP;
             if (i < row1) {
-                const int c0 = s_pp[i - row0], c1 = s_pp[i - row0 + 1];
+                const int c0 = s_pp[i - row0] - e0, c1 = s_pp[i - row0 + 1] - e0;
                 V ar = zero;
                 for (int c = c0; c < c1; c += kChunk) {
                     int j[kChunk];
@@ -876,7 +919,7 @@ __global__ void __launch_bounds__(kThreads, 2) cocg_step_aw(FilterArgs a, int kk
                         ar.y = fma(av[v], xv[v].y, ar.y);
                     }
                 }
-                const V ri = xs[(size_t)(h.z + i - row0) * W + cl];
+                const V ri = xs[(size_t)(own0 + i - row0) * W + cl];
                 V bx = ri;
                 if (BM == 1) {
                     const T b = ((const T*)P.bd)[i];
@@ -894,9 +937,8 @@ __global__ void __launch_bounds__(kThreads, 2) cocg_step_aw(FilterArgs a, int kk
                 if (first) acc[2] = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[2]));
             }
         }
-        accd[0] += (double)acc[0];
-        accd[1] += (double)acc[1];
-        accd[2] += (double)acc[2];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) kahan_add(accs[q], accc[q], acc[q]);
         __syncthreads();  // staged rows and entries are free for the next item's copies
     }
 }

@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(kT) h_vec_init(HArgs a, const double2* __restr
                 qv = make_double2(f * x.x, f * x.y);
             }
             a.Q[i * a.m + j] = qv;
+            if (a.dQ) ((float2*)a.dQ)[i * a.m + j] = make_float2(0.f, 0.f);
         }
     }
 }
@@ -317,11 +318,19 @@ __global__ void __launch_bounds__(kT) h_step_b(HArgs a)
         V rho = cmk<V>(T(0), T(0));
         T nr0 = T(0), nr1 = T(0);
         const int i1 = min(a.n, (rb + 1) * kRowsPerItem);
+        // mixed precision: the pass's quadrature sum accumulates in complex FP32
+        // (dQ, folded into Q once per pass); FP64 solves add to Q directly
+        float2* const dq = (float2*)a.dQ;
         for (int i = rb * kRowsPerItem + warp; i < i1; i += kT / 32) {  // bounds uniform over the warp
             const long long o = (long long)i * L + l;
-            double2* qq = a.Q + (long long)i * a.m + j;
+            const long long qi = (long long)i * a.m + j;
             const bool writes = ok && any && e == 0 && j < a.m;
-            const double2 qold = writes ? *qq : make_double2(0.0, 0.0);  // issued with the vector loads
+            double2 qold = make_double2(0.0, 0.0);
+            float2 dold = make_float2(0.f, 0.f);
+            if (writes) {  // issued with the vector loads
+                if (dq) dold = dq[qi];
+                else qold = a.Q[qi];
+            }
             V d = cmk<V>(T(0), T(0));
             if (act) {
                 const V rn = cfma(cmk<V>(-al.x, -al.y), q[o], r[o]);
@@ -342,7 +351,10 @@ __global__ void __launch_bounds__(kT) h_step_b(HArgs a)
                 d.x += __shfl_xor_sync(0xffffffffu, d.x, off);
                 d.y += __shfl_xor_sync(0xffffffffu, d.y, off);
             }
-            if (writes) *qq = make_double2(qold.x + (double)d.x, qold.y + (double)d.y);
+            if (writes) {
+                if (dq) dq[qi] = make_float2(dold.x + (float)d.x, dold.y + (float)d.y);
+                else a.Q[qi] = make_double2(qold.x + (double)d.x, qold.y + (double)d.y);
+            }
         }
         item_sum(to_d2(rho), sh, a.part + ((long long)rb * 2) * L + l, ok);
         item_sum(make_double2((double)nr0, (double)nr1), sh, a.part + ((long long)rb * 2 + 1) * L + l, ok);
@@ -439,6 +451,17 @@ __global__ void __launch_bounds__(kT) h_finish_b(HArgs a, int maxit)
     }
 }
 
+__global__ void h_fold(long long total, const float2* __restrict__ dQ, double2* __restrict__ Q)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const float2 d = dQ[t];
+        double2 q = Q[t];
+        q.x += (double)d.x;
+        q.y += (double)d.y;
+        Q[t] = q;
+    }
+}
+
 // ---------------------------------------------------------------- filter launchers
 static int item_grid(const HArgs& a)
 {
@@ -463,6 +486,18 @@ cudaError_t launch_h_init(const HArgs& a, bool fp64, const double2* b, const dou
     else h_norms<float><<<item_grid(a), kT, 0, s>>>(a);
     h_finish_norms<<<lane_grid(a), kT, 0, s>>>(a);
     count_launches(4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_h_fold(const HArgs& a, cudaStream_t s)
+{
+    const long long total = (long long)a.n * a.m;
+    if (!a.dQ || total <= 0) return cudaSuccess;
+    long long blocks = (total + 255) / 256;
+    const long long cap = (long long)num_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    h_fold<<<(int)blocks, 256, 0, s>>>(total, (const float2*)a.dQ, a.Q);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -403,3 +403,37 @@ def test_jacobi_barrier_time_limit_returns_error_and_recovers(pkg):
     ref = O.feast_scsr(p.A, None, p.emin, p.emax, p.m0, Y0=p.y0(), ne=8, ratio=100, tol_exp=10)
     assert r.info == 0 and r.M == ref["M"]
     assert np.abs(r.E[: r.M] - ref["E"][: r.M]).max() <= 1e-10 * p.emax
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+@pytest.mark.parametrize("rows", [0, 256])
+@pytest.mark.parametrize("cap", [1, 6])
+def test_filter_iteration_cap_matches_capped_cocg(pkg, mixed, rows, cap):
+    """With the inner tolerance out of reach, every column stops at the
+    iteration cap fpm(46): the filter must equal the quadrature sum of the
+    oracle's COCG iterates after exactly `cap` steps, with step A staging its
+    gathered rows (fpm(51) = 0) or gathering through the caches (256)."""
+    p = _filter_case()
+    n, m = p.n, p.m0
+    Y = p.y0()
+    fpm = pkg.feast_init()
+    fpm[1], fpm[17], fpm[41] = 8, 100, mixed
+    fpm[44], fpm[45], fpm[50] = 16, cap, rows
+    ia, ja, av = dcsr(p.A)
+    R = dev(Y)
+    Q = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+    it = pkg.feast_filter_dev(n, ia, ja, av, None, None, None, m, R, R, dev(np.zeros(m)), 0, fpm, p.emin, p.emax, Q)
+    assert it == cap
+    z, w = O.contour_gauss(8, p.emin, p.emax, 1.0)
+    ref = np.zeros((n, m))
+    scale = np.zeros((n, m))
+    for ze, we in zip(z, w):
+        Ye, its = O.shifted_solve(p.A, None, complex(ze), Y, method="cocg", tol=0.0, maxit=cap)
+        assert (its == cap).all()
+        ref += np.real(we * Ye)
+        scale += np.abs(we * Ye)
+    # relative to the size of the quadrature terms: after one step the sum is
+    # the filter value at each column's Rayleigh quotient, far outside the
+    # interval, and cancels to a tiny fraction of its terms
+    err = np.abs(Q.cpu().numpy() - ref).max() / scale.max()
+    assert err < (1e-12 if not mixed else 1e-4), err
