@@ -36,8 +36,8 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per group-iteration of each COCG step from one ncu
 # capture (profiles/cocg_steps_laplace3d_64cube.md), valid only for the kernel
 # source they were measured on.
-NCU_TRAFFIC = {"source_sha1": "6d1775636ac28d280b8236a3d26b24929a8a59fc",
-               "cocg_step_a": (1.248958e9 + 0.638676e9) / 5, "cocg_step_b": (1.178770e9 + 0.465578e9) / 5}
+NCU_TRAFFIC = {"source_sha1": "b5d86387a4f437d88bd20ea86a3464f06fb45b88",
+               "cocg_step_a": (1.119055e9 + 0.629053e9) / 5, "cocg_step_b": (1.178847e9 + 0.465558e9) / 5}
 
 
 def parse():
