@@ -357,7 +357,9 @@ struct Bufs {
     size_t wsmem = 0;
     int4* whdr = nullptr;  // staged-window tables (k_filter.cu win_build)
     int2* wwin = nullptr;
+    int* wlpp = nullptr;
     void* wpk = nullptr;
+    int wcape = 0;
     int* wstat = nullptr;
     void* dQ = nullptr;                   // per-pass quadrature accumulator (filter precision)
     double* zw = nullptr;
@@ -455,6 +457,8 @@ size_t carve(const Plan& P, void* base, Bufs& B, bool filter_only = false)
         B.wpk = c.take<char>(((size_t)P.nnzA + 7 * (size_t)P.n) * pk);
         B.whdr = c.take<int4>(nrb32);
         B.wwin = c.take<int2>(nrb32 * kWinMax);
+        // (rows per item + 4) ints per row block: 32-row (36 ints) and 64-row (68 ints) blocks
+        B.wlpp = c.take<int>(nrb32 * 36 + 68);
         B.wstat = c.take<int>(4);
     }
     B.dQ = c.take<char>((size_t)P.G * P.mt * P.n * (P.fp64 ? 8 : 4));
@@ -695,6 +699,8 @@ int filter_pass(const Plan& P, Bufs& B, int rii, const double* R, const double* 
     fa.wwin = B.wwin;
     fa.wpk = B.wpk;
     fa.wcapr = B.wcapr;
+    fa.wcape = B.wcape;
+    fa.wlpp = B.wlpp;
     fa.werr = B.groups_left + 1;
     fa.wlimit = wait_limit_cycles();
     int grid_a = 1, grid_b = 1;
@@ -807,19 +813,21 @@ int choose_step_a(const Plan& P, Bufs& B, cudaStream_t s)
     for (const int rbw : {FEAST_WIN_RB_FIRST, 96 - FEAST_WIN_RB_FIRST}) {
         int st4[4] = {0, 0, 0, 0};
         CK(cudaMemsetAsync(B.wstat, 0, sizeof(st4), s));
-        CK(launch_win_build(P.n, rbw, B.app, B.apk, P.fp64, B.wpk, B.whdr, B.wwin, B.wstat, s));
+        CK(launch_win_build(P.n, rbw, B.app, B.apk, P.fp64, B.wpk, B.whdr, B.wwin, B.wlpp, B.wstat, s));
         CK(cudaMemcpyAsync(st4, B.wstat, sizeof(st4), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (st4[3]) return 0;  // column indices outside [0, n): leave the matrix to the general path
         if (st4[2]) continue;
         const int nrbw = (P.n + rbw - 1) / rbw;
-        const size_t smem = win_smem_bytes(P.fp64, P.W, st4[0], st4[1]);
+        if ((long long)P.G * nrbw >= (1ll << 31)) continue;  // items counted in 32-bit ints
+        const size_t smem = win_smem_bytes(P.fp64, P.W, rbw, st4[0], st4[1]);
         const int occ = std::min(4, win_occupancy(P.fp64, P.W, B.bmode, rbw, smem));
         if (occ < 2) continue;
         B.wsmem = smem;
         B.wgrid = std::min(num_sms() * occ, nrbw);
         B.wrb = rbw;
         B.wcapr = st4[0];
+        B.wcape = st4[1];
         B.RB = rbw;
         B.nrb = nrbw;
         B.nitems = (long long)P.G * nrbw;
@@ -2173,6 +2181,12 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
         nslot = std::max(nslot, std::max(part_slots(nrb_max), part_slots(fpv[p].nrb_b)));
         nbk = std::max(nbk, std::max(part_buckets(nrb_max), part_buckets(fpv[p].nrb_b)));
     }
+    // work items of the two COCG steps at the smallest row block (problem lookup tables)
+    long long items_a_max = 0, items_b = 0;
+    for (int p = 0; p < np; ++p) {
+        items_a_max += (long long)G[p] * ((probs[p].n + rb_min - 1) / rb_min);
+        items_b += (long long)G[p] * fpv[p].nrb_b;
+    }
     // ---- device memory: one allocation carved in place
     DevMem dm;
     Bump bump;
@@ -2215,6 +2229,8 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
         (void)bump.take<double>(gpo);
         (void)bump.take<double>((size_t)res_b * 128 * 2);
         (void)bump.take<double>(wo);
+        (void)bump.take<int>(items_a_max);
+        (void)bump.take<int>(items_b);
         if (pass == 0) {
             cudaError_t e = dm.alloc(&base, bump.off + 4096);
             if (e != cudaSuccess) return cuda_fail(e, "batched workspace");
@@ -2264,6 +2280,8 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
     double* d_gpart = bump.take<double>(gpo);
     double* d_rpart = bump.take<double>((size_t)res_b * 128 * 2);
     double* d_rwork = bump.take<double>(wo);
+    int* d_itp = bump.take<int>(items_a_max);
+    int* d_itpb = bump.take<int>(items_b);
     cudaStream_t s = nullptr;
     CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     struct StreamGuard {
@@ -2354,9 +2372,14 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
     // ---- filter tables for a given rows-per-item choice
     long long nitems = 0, nitems_b = 0;
     int RB = 128;
+    // problem of every work item (a lookup instead of a binary search of the
+    // problem table in every item of every COCG launch)
+    std::vector<int> itp, itpb;
     auto build_tables = [&](int rb) -> int {
         RB = rb;
         long long it = 0, itb = 0;
+        itp.clear();
+        itpb.clear();
         for (int p = 0; p < np; ++p) {
             FiltProb& f = fpv[p];
             f.nrb = (f.n + RB - 1) / RB;
@@ -2364,10 +2387,15 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
             f.item0_b = itb;
             it += (long long)f.G * f.nrb;
             itb += (long long)f.G * f.nrb_b;
+            itp.insert(itp.end(), (size_t)f.G * f.nrb, p);
+            itpb.insert(itpb.end(), (size_t)f.G * f.nrb_b, p);
         }
         nitems = it;
         nitems_b = itb;
+        if (it > items_a_max || itb > items_b) return -4;
         CK(cudaMemcpyAsync(d_fp, fpv.data(), sizeof(FiltProb) * np, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_itp, itp.data(), sizeof(int) * itp.size(), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_itpb, itpb.data(), sizeof(int) * itpb.size(), cudaMemcpyHostToDevice, s));
         return 0;
     };
     FilterArgs fa;
@@ -2397,6 +2425,8 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
     fa.work = d_work;
     fa.kdev = d_k;
     fa.iter_max = d_itmax;
+    fa.item_prob = d_itp;
+    fa.item_prob_b = d_itpb;
     int st = build_tables(fpm[50] > 0 ? std::min(fpm[50], 512) : 256);
     if (st) return st;
     auto grids = [&](int& g_a, int& g_b, int& g_i) {
@@ -2470,7 +2500,7 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
             CK(cudaEventCreate(&e0));
             CK(cudaEventCreate(&e1));
             for (int cand : {128, 256, 512}) {
-                build_tables(cand);
+                { const int bt = build_tables(cand); if (bt) return bt; }
                 int g_a, g_b, g_i;
                 grids(g_a, g_b, g_i);
                 fa.kdev = nullptr;
@@ -2491,7 +2521,7 @@ extern "C" int feast_scsr_solve_batched(int np, const feast_problem* probs, int*
             std::lock_guard<std::mutex> lock(g_rb_mu);
             g_rb_cache.push_back({key, best_rb});
         }
-        build_tables(cached);
+        { const int bt = build_tables(cached); if (bt) return bt; }
         // the timing runs reset Q: start again from the start blocks
         CK(cudaMemcpyAsync(d_Q, d_Y, sizeof(double) * qo, cudaMemcpyDeviceToDevice, s));
     }

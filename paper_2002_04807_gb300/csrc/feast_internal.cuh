@@ -108,11 +108,15 @@ struct FilterArgs {
     int* groups_left;  // per-problem number of groups still iterating
     unsigned long long* work;  // group-iterations done (one per group per COCG step)
     const int* kdev;  // if set, the COCG step index is read from here (graph replay)
+    const int* item_prob;    // several problems: problem of each gathering-step item (else nullptr)
+    const int* item_prob_b;  // and of each streaming-step item
     // staged-window gather of step A (single problem; see win_build in k_filter.cu)
     const int4* whdr;   // per row block: (windows, staged rows, staged position of its first row, entries)
     const int2* wwin;   // per row block: kWinMax windows (first row, rows)
     const void* wpk;    // packed entries with staged positions instead of columns
     int wcapr;          // staged rows per CTA (largest over the row blocks)
+    int wcape;          // staged entries per CTA (largest over the row blocks)
+    const int* wlpp;    // per row block: local row pointers and own position (rows per item + 4 ints)
     int* werr;          // set to 1 when a CTA gave up waiting for its staged rows
     long long wlimit;   // that wait's limit in SM clock cycles
 };
@@ -142,8 +146,8 @@ cudaError_t launch_cast_diag(int n, const int* ia, const double* av, bool fp64, 
 // staged rows and cape entries; win_occupancy: resident CTAs per SM of that
 // step A variant (0 when it does not exist or does not fit).
 cudaError_t launch_win_build(int n, int rbw, const int* pp, const void* pk, bool fp64, void* lpk, int4* hdr,
-                             int2* win, int* stat, cudaStream_t s);
-size_t win_smem_bytes(bool fp64, int W, int capr, int cape);
+                             int2* win, int* lpp, int* stat, cudaStream_t s);
+size_t win_smem_bytes(bool fp64, int W, int rbw, int capr, int cape);
 int win_occupancy(bool fp64, int W, int bmode, int rbw, size_t smem);
 cudaError_t launch_cocg_step_aw(const FilterArgs& a, bool fp64, int rbw, int k, int grid, size_t smem,
                                 cudaStream_t s);

@@ -63,6 +63,9 @@ static constexpr int kMaxRB = 512;  // rows per work item, at most
 #ifndef FEAST_AW_MINB
 #define FEAST_AW_MINB 2  // resident CTAs per SM the staged step A is compiled for
 #endif
+#ifndef FEAST_B_ROWS
+#define FEAST_B_ROWS 2  // streaming step: rows per thread whose loads are issued together
+#endif
 
 __device__ __forceinline__ int find_prob(const FiltProb* probs, int nprob, long long item)
 {
@@ -311,7 +314,7 @@ struct ItemInfo {
 __device__ __forceinline__ ItemInfo item_info(const FilterArgs& a, long long item)
 {
     ItemInfo t;
-    t.pi = a.nprob == 1 ? 0 : find_prob(a.probs, a.nprob, item);
+    t.pi = a.nprob == 1 ? 0 : (a.item_prob ? a.item_prob[item] : find_prob(a.probs, a.nprob, item));
     const long long local = item - a.probs[t.pi].item0;
     const int nrb = a.probs[t.pi].nrb;
     t.g = (int)(local / nrb);
@@ -334,7 +337,7 @@ __device__ __forceinline__ int find_prob_b(const FiltProb* probs, int nprob, lon
 __device__ __forceinline__ ItemInfo item_info_b(const FilterArgs& a, long long item)
 {
     ItemInfo t;
-    t.pi = a.nprob == 1 ? 0 : find_prob_b(a.probs, a.nprob, item);
+    t.pi = a.nprob == 1 ? 0 : (a.item_prob_b ? a.item_prob_b[item] : find_prob_b(a.probs, a.nprob, item));
     const long long local = item - a.probs[t.pi].item0_b;
     const int nrb = a.probs[t.pi].nrb_b;
     t.g = (int)(local / nrb);
@@ -540,13 +543,16 @@ __global__ void __launch_bounds__(kThreads, FEAST_MINB_B) cocg_step_b(FilterArgs
         T acc[3] = {T(0), T(0), T(0)};  // rho.re, rho.im, ||r||^2
         const int row0 = it.rb * a.RBb;
         const int row1 = min(n, row0 + a.RBb);
-        // two rows per thread per pass, every load issued before any use
-        for (int i0 = row0 + rowslot; i0 < row1; i0 += 2 * RPP) {
-            const int ii[2] = {i0, i0 + RPP};
-            V rv[2], pv[2], qv[2];
-            T dq[2];
+        // FEAST_B_ROWS rows per thread per pass, every load issued before any use
+        constexpr int U = FEAST_B_ROWS;
+        for (int i0 = row0 + rowslot; i0 < row1; i0 += U * RPP) {
+            int ii[U];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < U; ++u) ii[u] = i0 + u * RPP;
+            V rv[U], pv[U], qv[U];
+            T dq[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
                 const bool ok = ii[u] < row1;
                 const size_t o = (size_t)(ok ? ii[u] : i0) * W;
                 rv[u] = ok ? r[o] : cmk<V>(T(0), T(0));
@@ -555,7 +561,7 @@ __global__ void __launch_bounds__(kThreads, FEAST_MINB_B) cocg_step_b(FilterArgs
                 dq[u] = (ok && writes_q) ? dQt[(size_t)(ok ? ii[u] : i0) * a.mt] : T(0);
             }
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const bool ok = ii[u] < row1;
                 V ri = rv[u];
                 T qc = T(0);
@@ -656,10 +662,14 @@ __device__ void block_bitonic(int* key, int P2)
 // One CTA per row block (grid-stride): the distinct columns of its entries
 // and its own rows, sorted and merged into windows; entries rewritten with
 // staged positions (window base + column - window start).
+// lpp[rb * (rbw + 4) + t]: the row block's row pointers relative to its first
+// entry (t = 0..rbw; rows past the end repeat the last), then its own rows'
+// staged position at t = rbw + 1: staged with the block's windows.
 template <typename PK>
 __global__ void __launch_bounds__(256) win_build(int n, int rbw, int nrbw, const int* __restrict__ pp,
                                                  const PK* __restrict__ pk, PK* __restrict__ lpk,
-                                                 int4* __restrict__ hdr, int2* __restrict__ win, int* stat)
+                                                 int4* __restrict__ hdr, int2* __restrict__ win, int* __restrict__ lpp,
+                                                 int* stat)
 {
     __shared__ int key[kWinKeys];
     __shared__ int ws[kWinMax], we[kWinMax], wb[kWinMax];
@@ -726,6 +736,9 @@ __global__ void __launch_bounds__(256) win_build(int n, int rbw, int nrbw, const
                         total += we[w] - ws[w];
                     }
                     hdr[rb] = make_int4(nw, total, own, cnt);
+                    lpp[(size_t)rb * (rbw + 4) + rbw + 1] = own;
+                    lpp[(size_t)rb * (rbw + 4) + rbw + 2] = 0;
+                    lpp[(size_t)rb * (rbw + 4) + rbw + 3] = 0;
                     atomicMax(stat + 0, total);
                     atomicMax(stat + 1, cnt);
                 } else {
@@ -738,6 +751,7 @@ __global__ void __launch_bounds__(256) win_build(int n, int rbw, int nrbw, const
         __syncthreads();
         if (s_ok) {
             const int nw = s_nw;
+            for (int t = tid; t <= rbw; t += blockDim.x) lpp[(size_t)rb * (rbw + 4) + t] = pp[min(row0 + t, row1)] - e0;
             for (int t = tid; t < cnt; t += blockDim.x) {
                 PK e = pk[e0 + t];
                 if (e.x >= 0) {
@@ -757,7 +771,8 @@ __global__ void __launch_bounds__(256) win_build(int n, int rbw, int nrbw, const
 // ||r||^2), single problem, B the identity (BM 0) or diagonal (BM 1).  The
 // launch grid must not exceed the row blocks per group, so that every CTA
 // has items in every group and each group's partial sums arrive from exactly
-// gridDim.x CTAs (slot = blockIdx.x).
+// gridDim.x CTAs (slot = blockIdx.x).  Work items are counted in 32-bit ints
+// (checked by the host).
 template <typename T, int W, int BM, int RBW>
 __global__ void __launch_bounds__(kThreads, FEAST_AW_MINB) cocg_step_aw(FilterArgs a, int kk)
 {
@@ -766,25 +781,27 @@ __global__ void __launch_bounds__(kThreads, FEAST_AW_MINB) cocg_step_aw(FilterAr
     constexpr int RPP = kThreads / W;   // rows per pass of the CTA
     constexpr int RPT = RBW / RPP;      // rows per thread per item
     static_assert(RBW % RPP == 0, "row block must be a whole number of passes");
+    constexpr int LPP = RBW + 4;        // local row pointers + own position, per row block
     constexpr unsigned ROWB = W * sizeof(V);                // bytes per tile row
     constexpr unsigned ENTB = sizeof(T) == 4 ? 8u : 16u;    // bytes per packed entry
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ double sm[kThreads * 3];
     __shared__ double red[W * kPartStride];
     __shared__ int flag;
-    __shared__ int s_pp[RBW + 1];
-    __shared__ int2 s_meta;
     __shared__ __align__(8) unsigned long long mbar;
     const int tid = threadIdx.x, lane = tid & 31;
     const int cl = tid % W, rowslot = tid / W;
     const bool first = (k == 0);
-    // staged rows from a 128-byte boundary of the dynamic shared memory (bulk
-    // copies need 16-byte aligned destinations; the request includes the pad)
+    // dynamic shared memory from a 128-byte boundary (bulk copies need 16-byte
+    // aligned destinations; the request includes the pad): staged rows, the
+    // row block's entries, its local row pointers
     const unsigned dsm_sh = (unsigned)__cvta_generic_to_shared(dsm);
     const unsigned xs_sh = (dsm_sh + 127u) & ~127u;
     const unsigned ent_sh = xs_sh + (unsigned)a.wcapr * ROWB;
+    const unsigned lpp_sh = ent_sh + (unsigned)a.wcape * ENTB;
     const V* xs = (const V*)(dsm + (xs_sh - dsm_sh));
     const int4* sent = (const int4*)(dsm + (ent_sh - dsm_sh));
+    const int* lp = (const int*)(dsm + (lpp_sh - dsm_sh));
     const unsigned mb = (unsigned)__cvta_generic_to_shared(&mbar);
     if (tid == 0) {
         mbar_init(mb, 1);
@@ -794,21 +811,21 @@ __global__ void __launch_bounds__(kThreads, FEAST_AW_MINB) cocg_step_aw(FilterAr
     unsigned parity = 0;
 
     const FiltProb& P = a.probs[0];
-    const int n = P.n, nrb = P.nrb;
+    const int n = P.n, nrb = P.nrb, nitems = (int)a.nitems;
+    const int* __restrict__ app = P.app;
     const V zero = cmk<V>(T(0), T(0));
     int cur = -1;
     bool skip = false, use_p = false;
     V z = zero, beta = zero;
-    const V* rl_ = nullptr;
     V *pl_ = nullptr, *ql_ = nullptr;
     const char* rtile = nullptr;
     T accs[3] = {T(0), T(0), T(0)}, accc[3] = {T(0), T(0), T(0)};  // this CTA's run sums (compensated)
     int4 mh = make_int4(0, 0, 0, 0);  // warp 0: table rows of row block mrb
     int2 mwv = make_int2(0, 0);
     int me0 = 0, mrb = -1;
-    for (long long item = blockIdx.x;; item += gridDim.x) {
-        const bool have = item < a.nitems;
-        const int g = have ? (int)(item / nrb) : -1;
+    for (int item = blockIdx.x;; item += gridDim.x) {
+        const bool have = item < nitems;
+        const int g = have ? item / nrb : -1;
         if (g != cur) {
             if (cur >= 0 && !skip) {  // publish this CTA's sums over its items of group cur
                 const int gi = P.grp_off + cur;
@@ -833,23 +850,21 @@ __global__ void __launch_bounds__(kThreads, FEAST_AW_MINB) cocg_step_aw(FilterAr
             beta = cmk<V>((T)bd.x, (T)bd.y);
             use_p = !first && active;
             const size_t tile = (size_t)P.vec_off + (size_t)g * n * W;
-            rl_ = (const V*)a.r + tile;
-            rtile = (const char*)rl_;
+            rtile = (const char*)((const V*)a.r + tile);
             pl_ = (V*)a.p0 + tile + cl;
             ql_ = (V*)a.p1 + tile + cl;
         }
         if (skip) continue;
-        const int rb = (int)(item - (long long)g * nrb);
+        const int rb = item - g * nrb;
         const int row0 = rb * RBW, row1 = min(n, row0 + RBW);
-        if (tid < 32) {  // one lane per window issues its bulk copy; lane 31 copies the entries
+        if (tid < 32) {  // one lane per window issues its bulk copy; lanes 31, 30: entries, row pointers
             if (mrb != rb) {  // the table rows were not prefetched (first item, or skipped groups)
                 mh = __ldg(a.whdr + rb);
                 mwv = __ldg(a.wwin + (size_t)rb * kWinMax + (lane & (kWinMax - 1)));
-                me0 = __ldg(P.app + row0);
+                me0 = __ldg(app + row0);
             }
             const int4 h = mh;
             const int2 wv = lane < h.x ? mwv : make_int2(0, 0);
-            const int e0 = me0;
             int pos = wv.y;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -858,23 +873,21 @@ __global__ void __launch_bounds__(kThreads, FEAST_AW_MINB) cocg_step_aw(FilterAr
             }
             pos -= wv.y;
             fence_proxy_async_smem();
-            if (lane == 0) {
-                mbar_expect_tx(mb, (unsigned)h.y * ROWB + (unsigned)h.w * ENTB);
-                s_meta = make_int2(h.z, e0);
-            }
+            if (lane == 0) mbar_expect_tx(mb, (unsigned)h.y * ROWB + (unsigned)h.w * ENTB + LPP * 4u);
             __syncwarp();
             if (lane < h.x)
                 bulk_g2s(xs_sh + (unsigned)pos * ROWB, rtile + (size_t)wv.x * ROWB, (unsigned)wv.y * ROWB, mb);
             if (lane == 31 && h.w > 0)
-                bulk_g2s(ent_sh, (const char*)a.wpk + (size_t)e0 * ENTB, (unsigned)h.w * ENTB, mb);
+                bulk_g2s(ent_sh, (const char*)a.wpk + (size_t)me0 * ENTB, (unsigned)h.w * ENTB, mb);
+            if (lane == 30) bulk_g2s(lpp_sh, a.wlpp + (size_t)rb * LPP, LPP * 4u, mb);
             // the next item's table rows load while this item computes
-            const long long nx = item + gridDim.x;
+            const int nx = item + gridDim.x;
             mrb = -1;
-            if (nx < a.nitems) {
-                mrb = (int)(nx % nrb);
+            if (nx < nitems) {
+                mrb = nx % nrb;
                 mh = __ldg(a.whdr + mrb);
                 mwv = __ldg(a.wwin + (size_t)mrb * kWinMax + (lane & (kWinMax - 1)));
-                me0 = __ldg(P.app + mrb * RBW);
+                me0 = __ldg(app + mrb * RBW);
             }
         }
         // own-row streams while the windows are in flight
@@ -889,9 +902,6 @@ __global__ void __launch_bounds__(kThreads, FEAST_AW_MINB) cocg_step_aw(FilterAr
                 qo[u] = ql_[(size_t)i * W];
             }
         }
-        for (int t = tid; t <= row1 - row0; t += kThreads) s_pp[t] = __ldg(P.app + row0 + t);
-        __syncthreads();
-        const int own0 = s_meta.x, e0 = s_meta.y;  // staged position of row0, first entry of the item
         const bool ok = mbar_wait(mb, parity, a.wlimit);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(a.werr, 1);
@@ -899,12 +909,13 @@ __global__ void __launch_bounds__(kThreads, FEAST_AW_MINB) cocg_step_aw(FilterAr
             return;
         }
         parity ^= 1u;
+        const int own0 = lp[RBW + 1];  // staged position of row0
         T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
         for (int u = 0; u < RPT; ++u) {
             const int i = row0 + rowslot + u * RPP;
             if (i < row1) {
-                const int c0 = s_pp[i - row0] - e0, c1 = s_pp[i - row0 + 1] - e0;
+                const int c0 = lp[i - row0], c1 = lp[i - row0 + 1];
                 V ar = zero;
                 for (int c = c0; c < c1; c += kChunk) {
                     int j[kChunk];
@@ -1217,23 +1228,24 @@ cudaError_t launch_cocg_step_b(const FilterArgs& a, bool fp64, int k, int grid, 
 
 // ---------------------------------------------------------------- staged-window launchers
 cudaError_t launch_win_build(int n, int rbw, const int* pp, const void* pk, bool fp64, void* lpk, int4* hdr,
-                             int2* win, int* stat, cudaStream_t s)
+                             int2* win, int* lpp, int* stat, cudaStream_t s)
 {
     if (n <= 0 || rbw <= 0) return cudaSuccess;
     const int nrbw = (n + rbw - 1) / rbw;
     const int grid = std::min(nrbw, num_sms() * 8);
     if (fp64)
-        win_build<int4><<<grid, 256, 0, s>>>(n, rbw, nrbw, pp, (const int4*)pk, (int4*)lpk, hdr, win, stat);
+        win_build<int4><<<grid, 256, 0, s>>>(n, rbw, nrbw, pp, (const int4*)pk, (int4*)lpk, hdr, win, lpp, stat);
     else
-        win_build<int2><<<grid, 256, 0, s>>>(n, rbw, nrbw, pp, (const int2*)pk, (int2*)lpk, hdr, win, stat);
+        win_build<int2><<<grid, 256, 0, s>>>(n, rbw, nrbw, pp, (const int2*)pk, (int2*)lpk, hdr, win, lpp, stat);
     count_launches(1);
     return cudaGetLastError();
 }
 
-size_t win_smem_bytes(bool fp64, int W, int capr, int cape)
+size_t win_smem_bytes(bool fp64, int W, int rbw, int capr, int cape)
 {
     const size_t cb = fp64 ? 16 : 8;  // complex element, and packed entry, bytes
-    return 128 + (size_t)capr * W * cb + (size_t)cape * cb;  // + alignment pad of the staged rows
+    // + alignment pad of the staged rows; the local row pointers last
+    return 128 + (size_t)capr * W * cb + (size_t)cape * cb + (size_t)(rbw + 4) * 4;
 }
 
 // Allows the variant the largest dynamic shared memory the device gives a CTA
