@@ -36,8 +36,8 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per group-iteration of each COCG step from one ncu
 # capture (profiles/cocg_steps_laplace3d_64cube.md), valid only for the kernel
 # source they were measured on.
-NCU_TRAFFIC = {"source_sha1": "b5d86387a4f437d88bd20ea86a3464f06fb45b88",
-               "cocg_step_a": (1.119055e9 + 0.629053e9) / 5, "cocg_step_b": (1.178847e9 + 0.465558e9) / 5}
+NCU_TRAFFIC = {"source_sha1": "89a43ee85654717cd2c6a26edead138abfd4dff7",
+               "cocg_step_a": (1.108600e9 + 0.627256e9) / 5, "cocg_step_b": (1.182058e9 + 0.467139e9) / 5}
 
 
 def parse():

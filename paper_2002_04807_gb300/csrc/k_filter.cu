@@ -58,13 +58,13 @@ static constexpr int kMaxRB = 512;  // rows per work item, at most
 #define FEAST_MINB 5
 #endif
 #ifndef FEAST_MINB_B
-#define FEAST_MINB_B 5
+#define FEAST_MINB_B 4
 #endif
 #ifndef FEAST_AW_MINB
 #define FEAST_AW_MINB 2  // resident CTAs per SM the staged step A is compiled for
 #endif
 #ifndef FEAST_B_ROWS
-#define FEAST_B_ROWS 2  // streaming step: rows per thread whose loads are issued together
+#define FEAST_B_ROWS 4  // streaming step: rows per thread whose loads are issued together
 #endif
 
 __device__ __forceinline__ int find_prob(const FiltProb* probs, int nprob, long long item)
