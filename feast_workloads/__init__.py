@@ -120,11 +120,12 @@ def laplacian_3d(side: int, potential=None) -> CSR:
     return _grid_laplacian((side, side, side), pot)
 
 
-def stencil27_spd(side: int, rng: np.random.Generator) -> CSR:
+def stencil27_spd(side: int, rng: np.random.Generator, shape=None) -> CSR:
     """27-point SPD stencil: off-diagonals -U[0.5,1.5] drawn once per undirected
-    edge (so the matrix is symmetric), diagonal = row-abs-sum + U[0.1,1]."""
-    shape = (side, side, side)
-    n = side ** 3
+    edge (so the matrix is symmetric), diagonal = row-abs-sum + U[0.1,1].  The
+    grid is side^3, or `shape` = (nz, ny, nx) with x fastest."""
+    shape = (side, side, side) if shape is None else tuple(shape)
+    n = int(np.prod(shape))
     idx = np.arange(n).reshape(shape)
     rows, cols = [], []
     # each undirected edge once: offsets with the first nonzero component > 0
@@ -135,8 +136,8 @@ def stencil27_spd(side: int, rng: np.random.Generator) -> CSR:
                 first = next((o for o in off if o != 0), 0)
                 if first <= 0:
                     continue
-                src = [slice(max(0, -o), side - max(0, o)) for o in off]
-                dst = [slice(max(0, o), side - max(0, -o)) for o in off]
+                src = [slice(max(0, -o), m - max(0, o)) for o, m in zip(off, shape)]
+                dst = [slice(max(0, o), m - max(0, -o)) for o, m in zip(off, shape)]
                 rows.append(idx[tuple(src)].ravel())
                 cols.append(idx[tuple(dst)].ravel())
     r = np.concatenate(rows)

@@ -37,7 +37,7 @@
  *    Library options in reserved slots (0 = automatic):
  *      fpm(50) contour nodes solved at once (node batch); fpm(51) rows per
  *      inner-solver work item (0: the single-problem drivers stage the rows
- *      each item gathers in shared memory, 64 or 32 rows per item, when the
+ *      each item gathers in shared memory, 32 to 64 rows per item, when the
  *      matrix's row blocks read few contiguous column ranges and B is the
  *      identity or diagonal; else 256; > 0: that many rows, gathered through
  *      the caches); fpm(52) seed of the random start block;
@@ -123,10 +123,11 @@ int feast_contour_nodes_rule(int rule, int ne, double emin, double emax, int rat
  * reduced eigensolver, [8] ms forming Ritz vectors and residuals, [9] tile
  * width W, [10] columns per group mt, [11] n, [12] bytes per complex value,
  * [13] column groups, [14] refinement loops, [15] kernel launches issued,
- * [16] rows per step-A work item, [17] 1 when step A stages the rows it
- * gathers in shared memory (windows of r copied by the bulk-copy engine),
- * 0 when it gathers through the caches, [18] step A CTAs (staged variant),
- * [19] staged rows per row block (staged variant).
+ * [16] rows per step-A work item, [17] 0 when step A gathers through the
+ * caches, 1 when it stages the rows it gathers in shared memory (windows of r
+ * copied by the bulk-copy engine), 2 for the staged form with a producer warp
+ * and two stages (one CTA per SM), [18] step A CTAs (staged forms), [19]
+ * staged rows per row block (staged forms).
  * Library extension (the guide reports phase timings only as a text log).
  * Returns 0. */
 int feast_last_profile(double* out);

@@ -360,6 +360,7 @@ struct Bufs {
     int* wlpp = nullptr;
     void* wpk = nullptr;
     int wcape = 0;
+    bool wws = false;  // staged step A in its warp-specialized form (cocg_step_ws)
     int* wstat = nullptr;
     void* dQ = nullptr;                   // per-pass quadrature accumulator (filter precision)
     double* zw = nullptr;
@@ -712,6 +713,7 @@ int filter_pass(const Plan& P, Bufs& B, int rii, const double* R, const double* 
     CK(cudaMemsetAsync(B.iter_max, 0, sizeof(int) * P.nbatch, s));
     CK(cudaMemsetAsync(B.groups_left + 1, 0, sizeof(int), s));
     auto step_a = [&](int k) -> cudaError_t {
+        if (B.wws) return launch_cocg_step_ws(fa, B.wrb, k, grid_a, B.wsmem, s);
         return B.wrb ? launch_cocg_step_aw(fa, P.fp64, B.wrb, k, grid_a, B.wsmem, s)
                      : launch_cocg_step_a(fa, P.fp64, k, grid_a, s);
     };
@@ -806,7 +808,43 @@ int choose_step_a(const Plan& P, Bufs& B, cudaStream_t s)
     B.nrb = P.nrb;
     B.nitems = P.nitems;
     B.wrb = 0;
+    B.wws = false;
     if (!P.win || B.bmode == 2) return 0;
+#ifndef FEAST_STEP_A_WS
+#define FEAST_STEP_A_WS 1  // 0: never the warp-specialized form
+#endif
+    // warp-specialized form (one CTA per SM, the next item's rows staged while the
+    // current one computes), 48 then 32 rows per item, for matrices whose row blocks
+    // stage many rows per row; with few (a 7-point stencil stages 5 rows per row),
+    // two CTAs per SM each issuing their own copies are faster.  Measured on GB300:
+    // 7-point 64^3 4,240 (two CTAs) vs 3,830 GB/s; 27-point 96^3 (9.6 staged rows
+    // per row) 2,158 vs 2,362 GB/s.
+    constexpr double kWsMinStagedPerRow = 7.0;
+    for (const int rbw : {48, 32}) {
+        if (!FEAST_STEP_A_WS || P.fp64 || P.W != 32) break;
+        int st4[4] = {0, 0, 0, 0};
+        CK(cudaMemsetAsync(B.wstat, 0, sizeof(st4), s));
+        CK(launch_win_build(P.n, rbw, B.app, B.apk, P.fp64, B.wpk, B.whdr, B.wwin, B.wlpp, B.wstat, s));
+        CK(cudaMemcpyAsync(st4, B.wstat, sizeof(st4), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (st4[3]) return 0;  // column indices outside [0, n): leave the matrix to the general path
+        if (st4[2]) continue;
+        const int nrbw = (P.n + rbw - 1) / rbw;
+        if ((long long)P.G * nrbw >= (1ll << 31)) continue;
+        if ((double)st4[0] < kWsMinStagedPerRow * rbw) break;
+        const size_t smem = ws_smem_bytes(P.W, rbw, st4[0], st4[1]);
+        if (ws_occupancy(P.fp64, P.W, B.bmode, rbw, P.G, smem) < 1) continue;
+        B.wws = true;
+        B.wsmem = smem;
+        B.wgrid = std::min(num_sms(), nrbw);
+        B.wrb = rbw;
+        B.wcapr = st4[0];
+        B.wcape = st4[1];
+        B.RB = rbw;
+        B.nrb = nrbw;
+        B.nitems = (long long)P.G * nrbw;
+        return 0;
+    }
 #ifndef FEAST_WIN_RB_FIRST
 #define FEAST_WIN_RB_FIRST 64  // rows per staged item tried first (then the other of 64, 32)
 #endif
@@ -1105,7 +1143,7 @@ int run_feast(const Plan& P, Bufs& B, const Csr& A, const Csr& Bm, int* fpm, dou
         o[13] = (double)P.G;
         o[14] = (double)k;
         o[16] = (double)B.RB;
-        o[17] = B.wrb ? 1.0 : 0.0;
+        o[17] = B.wws ? 2.0 : (B.wrb ? 1.0 : 0.0);
         o[18] = (double)(B.wrb ? B.wgrid : 0);
         o[19] = (double)(B.wrb ? B.wcapr : 0);
     }

@@ -151,6 +151,12 @@ size_t win_smem_bytes(bool fp64, int W, int rbw, int capr, int cape);
 int win_occupancy(bool fp64, int W, int bmode, int rbw, size_t smem);
 cudaError_t launch_cocg_step_aw(const FilterArgs& a, bool fp64, int rbw, int k, int grid, size_t smem,
                                 cudaStream_t s);
+// Warp-specialized form of the staged step A (one CTA per SM: 16 consumer
+// warps and a producer warp, two stages; complex FP32 with 32 lanes): dynamic
+// shared memory, resident CTAs per SM (0: variant missing or too large), launch.
+size_t ws_smem_bytes(int W, int rbw, int capr, int cape);
+int ws_occupancy(bool fp64, int W, int bmode, int rbw, int groups, size_t smem);
+cudaError_t launch_cocg_step_ws(const FilterArgs& a, int rbw, int k, int grid, size_t smem, cudaStream_t s);
 // persistent grid size of the COCG kernels: SMs x resident CTAs per SM
 int filter_grid(bool fp64, int W);
 void filter_grids(bool fp64, int W, int* grid_a, int* grid_b);

@@ -195,6 +195,17 @@ __device__ __forceinline__ bool stage_rows(const int* __restrict__ pp, const voi
 }
 
 // ---------------------------------------------------------------- reductions
+// Barrier policies: the whole CTA, or the NT threads of named barrier ID (the
+// consumer warps of a warp-specialized kernel, whose producer warp does not
+// take part).
+struct CtaSync {
+    static __device__ __forceinline__ void sync() { __syncthreads(); }
+};
+template <int ID, int NT>
+struct NamedSync {
+    static __device__ __forceinline__ void sync() { asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(NT) : "memory"); }
+};
+
 // Block-wide reduction of NV per-thread values for each of the W lane columns,
 // written to the work item's slot.  A slot holds kPartStride rows of W
 // doubles (slot[q * W + cl]), so one value of every lane is one coalesced
@@ -202,16 +213,16 @@ __device__ __forceinline__ bool stage_rows(const int* __restrict__ pp, const voi
 // The sums run in the values' own type and only the W results are widened:
 // GB300 issues FP64 arithmetic and conversions at a small fraction of the FP32
 // rate, so per-thread FP64 work in a per-item reduction costs more than the item.
-template <int W, int NV, typename T>
+template <int W, int NV, typename T, int NT = kThreads, typename SY = CtaSync>
 __device__ __forceinline__ void item_partials(T (&v)[NV], double* sm, double* slot)
 {
-    constexpr int SEGS = kThreads / W;
+    constexpr int SEGS = NT / W;
     const int tid = threadIdx.x;
     const int cl = tid % W, seg = tid / W;
     T* st = reinterpret_cast<T*>(sm);
 #pragma unroll
     for (int q = 0; q < NV; ++q) st[(seg * W + cl) * NV + q] = v[q];
-    __syncthreads();
+    SY::sync();
     if (tid < W) {
         T s[NV];
 #pragma unroll
@@ -222,7 +233,7 @@ __device__ __forceinline__ void item_partials(T (&v)[NV], double* sm, double* sl
 #pragma unroll
         for (int q = 0; q < NV; ++q) slot[(size_t)q * W + tid] = (double)s[q];
     }
-    __syncthreads();
+    SY::sync();
 }
 
 // Compensated (Kahan) running sum in the filter precision: s - c carries the
@@ -238,10 +249,10 @@ __device__ __forceinline__ void kahan_add(T& s, T& c, T x)
 
 // Sum of `count` consecutive slots starting at `base`, per lane, in a fixed
 // order, into red[cl * kPartStride + q] (shared).  All threads of the CTA.
-template <int W, int NV>
+template <int W, int NV, int NT = kThreads, typename SY = CtaSync>
 __device__ __forceinline__ void sum_slots(const double* base, int count, double* sm, double* red)
 {
-    constexpr int SEGS = kThreads / W;
+    constexpr int SEGS = NT / W;
     const int tid = threadIdx.x;
     const int cl = tid % W, seg = tid / W;
     double s[NV];
@@ -253,7 +264,7 @@ __device__ __forceinline__ void sum_slots(const double* base, int count, double*
         for (int q = 0; q < NV; ++q) s[q] += __ldcg(base + ((size_t)b * kPartStride + q) * W + cl);
 #pragma unroll
     for (int q = 0; q < NV; ++q) sm[(seg * W + cl) * NV + q] = s[q];
-    __syncthreads();
+    SY::sync();
     if (tid < W) {
         double t[NV];
 #pragma unroll
@@ -264,19 +275,20 @@ __device__ __forceinline__ void sum_slots(const double* base, int count, double*
 #pragma unroll
         for (int q = 0; q < NV; ++q) red[tid * kPartStride + q] = t[q];
     }
-    __syncthreads();
+    SY::sync();
 }
 
 // Returns true in every thread of the CTA whose arrival is the total-th.
+template <typename SY = CtaSync>
 __device__ __forceinline__ bool arrive_count(unsigned* counter, int total, int* flag_sm)
 {
     __threadfence();
-    __syncthreads();
+    SY::sync();
     if (threadIdx.x == 0) {
         unsigned prev = atomicAdd(counter, 1u);
         *flag_sm = (prev == (unsigned)(total - 1));
     }
-    __syncthreads();
+    SY::sync();
     const bool last = *flag_sm != 0;
     if (last) __threadfence();
     return last;
@@ -286,23 +298,23 @@ __device__ __forceinline__ bool arrive_count(unsigned* counter, int total, int* 
 // bucket into its bucket slot; the CTA completing the group's last bucket sums
 // the bucket slots into red[] and returns true (all its threads).  Counters
 // are reset by the CTA that completes them.
-template <int W, int NV>
+template <int W, int NV, int NT = kThreads, typename SY = CtaSync>
 __device__ __forceinline__ bool tree_arrive(double* gslots, int nrb, int rb, unsigned* bk_count, unsigned* grp_count,
                                             double* sm, double* red, int* flag_sm)
 {
     const int nbk = part_buckets(nrb);
     const int bk = rb / kPartBucket;
     const int bsz = min(kPartBucket, nrb - bk * kPartBucket);
-    if (!arrive_count(bk_count + bk, bsz, flag_sm)) return false;
-    sum_slots<W, NV>(gslots + (size_t)bk * kPartBucket * kPartStride * W, bsz, sm, red);
+    if (!arrive_count<SY>(bk_count + bk, bsz, flag_sm)) return false;
+    sum_slots<W, NV, NT, SY>(gslots + (size_t)bk * kPartBucket * kPartStride * W, bsz, sm, red);
     if (threadIdx.x < W) {
         double* bs = gslots + ((size_t)nrb + bk) * kPartStride * W;
 #pragma unroll
         for (int q = 0; q < NV; ++q) bs[(size_t)q * W + threadIdx.x] = red[threadIdx.x * kPartStride + q];
     }
     if (threadIdx.x == 0) bk_count[bk] = 0u;
-    if (!arrive_count(grp_count, nbk, flag_sm)) return false;
-    sum_slots<W, NV>(gslots + (size_t)nrb * kPartStride * W, nbk, sm, red);
+    if (!arrive_count<SY>(grp_count, nbk, flag_sm)) return false;
+    sum_slots<W, NV, NT, SY>(gslots + (size_t)nrb * kPartStride * W, nbk, sm, red);
     if (threadIdx.x == 0) *grp_count = 0u;
     return true;
 }
@@ -954,6 +966,241 @@ __global__ void __launch_bounds__(kThreads, FEAST_AW_MINB) cocg_step_aw(FilterAr
     }
 }
 
+// ---------------------------------------------------------------- warp-specialized staged step A
+// The staged gathering step with the copies taken off the compute warps: one
+// CTA per SM of 16 consumer warps and one producer warp, two stages.  The
+// producer stages each item's windows of r, its own rows of p and q, its
+// entries and its local row pointers (bulk copies onto the stage's "full"
+// mbarrier) as soon as the consumers have released the stage (its "empty"
+// mbarrier, one arrival per consumer warp), so the copies of the next item
+// are in flight while the current one computes; the consumers only wait,
+// compute and store.  Same arithmetic and partial sums as cocg_step_aw.
+static constexpr int kThreadsWS = 512;          // consumer threads
+static constexpr int kMaxGroupsWS = 1024;        // column groups per problem this kernel takes
+
+__device__ __forceinline__ void mbar_arrive(unsigned addr)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+// OR of pred over the kThreadsWS consumer threads (named barrier 1).
+__device__ __forceinline__ bool consumers_or(bool pred)
+{
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.s32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.s32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((int)pred), "n"(kThreadsWS)
+        : "memory");
+    return r != 0;
+}
+
+template <typename T, int W, int BM, int RBW>
+__global__ void __launch_bounds__(kThreadsWS + 32, 1) cocg_step_ws(FilterArgs a, int kk)
+{
+    const int k = a.kdev ? *a.kdev : kk;
+    using V = c2_t<T>;
+    using SY = NamedSync<1, kThreadsWS>;
+    constexpr int NT = kThreadsWS;
+    constexpr int RPP = NT / W;    // rows per pass of the consumers
+    constexpr int RPT = RBW / RPP;  // rows per consumer thread per item
+    static_assert(RBW % RPP == 0, "row block must be a whole number of passes");
+    constexpr int LPP = RBW + 4;
+    constexpr unsigned ROWB = W * sizeof(V);
+    constexpr unsigned ENTB = sizeof(T) == 4 ? 8u : 16u;
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ double sm[NT * 3];
+    __shared__ double red[W * kPartStride];
+    __shared__ int flag;
+    __shared__ unsigned char s_done[kMaxGroupsWS];
+    __shared__ __align__(8) unsigned long long mbar[4];  // full[0], full[1], empty[0], empty[1]
+    const int tid = threadIdx.x, lane = tid & 31;
+    const bool first = (k == 0);
+    const FiltProb& P = a.probs[0];
+    const int n = P.n, nrb = P.nrb, nitems = (int)a.nitems, G = P.G;
+    const int* __restrict__ app = P.app;
+    const unsigned cap = (unsigned)a.wcapr, cape = (unsigned)a.wcape;
+    // a stage: [windows of r | own rows of p | own rows of q | entries | local row pointers]
+    const unsigned p_off = cap * ROWB, q_off = p_off + RBW * ROWB, ent_off = q_off + RBW * ROWB;
+    const unsigned lpp_off = ent_off + cape * ENTB;
+    const unsigned stage_bytes = (lpp_off + LPP * 4u + 127u) & ~127u;
+    const unsigned dsm_sh = (unsigned)__cvta_generic_to_shared(dsm);
+    const unsigned base_sh = (dsm_sh + 127u) & ~127u;
+    const unsigned char* base = dsm + (base_sh - dsm_sh);
+    const unsigned mb0 = (unsigned)__cvta_generic_to_shared(&mbar[0]);  // full[s] = mb0 + 8s, empty[s] = mb0 + 16 + 8s
+    if (tid == 0) {
+        mbar_init(mb0, 1);
+        mbar_init(mb0 + 8, 1);
+        mbar_init(mb0 + 16, NT / 32);
+        mbar_init(mb0 + 24, NT / 32);
+        mbar_fence_init();
+    }
+    for (int g = tid; g < G; g += blockDim.x) s_done[g] = a.grp_done[P.grp_off + g] ? 1 : 0;
+    __syncthreads();  // the last CTA-wide barrier: producer and consumers part here
+    auto live_item = [&](int it) {
+        while (it < nitems && s_done[it / nrb]) it += gridDim.x;
+        return it;
+    };
+
+    if (tid >= NT) {  // ---- producer warp
+        // table rows of the next item, loaded one item ahead
+        int4 mh = make_int4(0, 0, 0, 0);
+        int2 mwv = make_int2(0, 0);
+        int me0 = 0;
+        auto load_meta = [&](int it) {
+            const int rb = it % nrb;
+            mh = __ldg(a.whdr + rb);
+            mwv = __ldg(a.wwin + (size_t)rb * kWinMax + (lane & (kWinMax - 1)));
+            me0 = __ldg(app + rb * RBW);
+        };
+        int kq = 0;
+        int it = live_item(blockIdx.x);
+        if (it < nitems) load_meta(it);
+        for (; it < nitems; ++kq) {
+            const int st = kq & 1;
+            const int4 h = mh;
+            const int2 wv = lane < h.x ? mwv : make_int2(0, 0);
+            const int e0 = me0;
+            const int nx = live_item(it + gridDim.x);
+            if (nx < nitems) load_meta(nx);
+            if (kq >= 2) {  // the consumers released this stage (item kq - 2)
+                if (!mbar_wait(mb0 + 16 + 8 * st, ((kq >> 1) - 1) & 1, a.wlimit)) {
+                    if (lane == 0) atomicExch(a.werr, 1);
+                    return;
+                }
+            }
+            const int g = it / nrb, rb = it - g * nrb;
+            const int row0 = rb * RBW, rows = min(n, row0 + RBW) - row0;
+            int pos = wv.y;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, pos, o);
+                if (lane >= o) pos += t;
+            }
+            pos -= wv.y;
+            const size_t tile_b = ((size_t)P.vec_off + (size_t)g * n * W) * sizeof(V);
+            const unsigned sb = base_sh + (unsigned)st * stage_bytes, full = mb0 + 8 * st;
+            fence_proxy_async_smem();
+            if (lane == 0)
+                mbar_expect_tx(full, (unsigned)h.y * ROWB + (first ? 0u : 2u * rows * ROWB) + (unsigned)h.w * ENTB +
+                                         LPP * 4u);
+            __syncwarp();
+            if (lane < h.x)
+                bulk_g2s(sb + (unsigned)pos * ROWB, (const char*)a.r + tile_b + (size_t)wv.x * ROWB,
+                         (unsigned)wv.y * ROWB, full);
+            if (!first && lane == 16)
+                bulk_g2s(sb + p_off, (const char*)a.p0 + tile_b + (size_t)row0 * ROWB, (unsigned)rows * ROWB, full);
+            if (!first && lane == 17)
+                bulk_g2s(sb + q_off, (const char*)a.p1 + tile_b + (size_t)row0 * ROWB, (unsigned)rows * ROWB, full);
+            if (lane == 31 && h.w > 0)
+                bulk_g2s(sb + ent_off, (const char*)a.wpk + (size_t)e0 * ENTB, (unsigned)h.w * ENTB, full);
+            if (lane == 30) bulk_g2s(sb + lpp_off, a.wlpp + (size_t)rb * LPP, LPP * 4u, full);
+            it = nx;
+        }
+        return;
+    }
+
+    // ---- consumer warps
+    const int cl = tid % W, rowslot = tid / W;
+    const V zero = cmk<V>(T(0), T(0));
+    int cur = -1;
+    bool use_p = false;
+    V z = zero, beta = zero;
+    V *pl_ = nullptr, *ql_ = nullptr;
+    T accs[3] = {T(0), T(0), T(0)}, accc[3] = {T(0), T(0), T(0)};
+    auto publish = [&](int g) {
+        const int gi = P.grp_off + g;
+        double* gslots = a.part + (size_t)gi * a.nslot * kPartStride * W;
+        double accd[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) accd[q] = (double)accs[q] - (double)accc[q];
+        item_partials<W, 3, double, NT, SY>(accd, sm, gslots + (size_t)blockIdx.x * kPartStride * W);
+        if (tree_arrive<W, 3, NT, SY>(gslots, gridDim.x, blockIdx.x, a.bk_count + (size_t)gi * a.nbk,
+                                      a.grp_count + gi, sm, red, &flag))
+            finish_group_a<W>(a.cs + P.col_off + (size_t)g * W, first, red);
+    };
+    int kq = 0;
+    for (int it = live_item(blockIdx.x); it < nitems; it = live_item(it + gridDim.x), ++kq) {
+        const int g = it / nrb, rb = it - g * nrb;
+        if (g != cur) {
+            if (cur >= 0) publish(cur);
+            cur = g;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) accs[q] = accc[q] = T(0);
+            const ColState* csg = a.cs + P.col_off + (size_t)g * W;
+            const int active = csg[cl].active;
+            const double2 zd = csg[cl].z, bd = csg[cl].beta;
+            z = cmk<V>((T)zd.x, (T)zd.y);
+            beta = cmk<V>((T)bd.x, (T)bd.y);
+            use_p = !first && active;
+            const size_t tile = (size_t)P.vec_off + (size_t)g * n * W;
+            pl_ = (V*)a.p0 + tile + cl;
+            ql_ = (V*)a.p1 + tile + cl;
+        }
+        const int st = kq & 1;
+        const bool ok = mbar_wait(mb0 + 8 * st, (kq >> 1) & 1, a.wlimit);
+        if (consumers_or(!ok)) {  // flag, then leave (all consumers) once the copies in flight have landed
+            if (tid == 0) atomicExch(a.werr, 1);
+            mbar_wait(mb0 + 8 * st, (kq >> 1) & 1, a.wlimit);
+            mbar_wait(mb0 + 8 * (st ^ 1), ((kq + 1) >> 1) & 1, a.wlimit);
+            return;
+        }
+        const unsigned char* sb = base + (unsigned)st * stage_bytes;
+        const V* xs = (const V*)sb;
+        const V* ps = (const V*)(sb + p_off);
+        const V* qs = (const V*)(sb + q_off);
+        const int4* sent = (const int4*)(sb + ent_off);
+        const int* lp = (const int*)(sb + lpp_off);
+        const int row0 = rb * RBW, row1 = min(n, row0 + RBW);
+        const int own0 = lp[RBW + 1];
+        T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            const int i = row0 + rowslot + u * RPP;
+            if (i < row1) {
+                const int c0 = lp[i - row0], c1 = lp[i - row0 + 1];
+                V ar = zero;
+                for (int c = c0; c < c1; c += kChunk) {
+                    int j[kChunk];
+                    T av[kChunk];
+                    load_chunk<T, true>(sent, c, j, av);
+                    V xv[kChunk];
+#pragma unroll
+                    for (int v = 0; v < kChunk; ++v) xv[v] = j[v] >= 0 ? xs[(size_t)j[v] * W + cl] : zero;
+#pragma unroll
+                    for (int v = 0; v < kChunk; ++v) {
+                        ar.x = fma(av[v], xv[v].x, ar.x);
+                        ar.y = fma(av[v], xv[v].y, ar.y);
+                    }
+                }
+                const V ri = xs[(size_t)(own0 + i - row0) * W + cl];
+                V bx = ri;
+                if (BM == 1) {
+                    const T b = ((const T*)P.bd)[i];
+                    bx = cmk<V>(b * ri.x, b * ri.y);
+                }
+                V pi_ = ri, qi = csub(cmul(z, bx), ar);  // (zB - A) r
+                if (use_p) {
+                    pi_ = cfma(beta, ps[(size_t)(i - row0) * W + cl], pi_);
+                    qi = cfma(beta, qs[(size_t)(i - row0) * W + cl], qi);
+                }
+                pl_[(size_t)i * W] = pi_;
+                ql_[(size_t)i * W] = qi;
+                acc[0] = fma(pi_.x, qi.x, fma(-pi_.y, qi.y, acc[0]));
+                acc[1] = fma(pi_.x, qi.y, fma(pi_.y, qi.x, acc[1]));
+                if (first) acc[2] = fma(ri.x, ri.x, fma(ri.y, ri.y, acc[2]));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) kahan_add(accs[q], accc[q], acc[q]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(mb0 + 16 + 8 * st);  // this warp is done with the stage
+    }
+    if (cur >= 0) publish(cur);
+}
+
 // ---------------------------------------------------------------- init
 // Column states for one node batch: node e = node0 + (lane % nbp) of the
 // problem's Ne nodes, subspace column m; coefficient c = w_e (first pass) or
@@ -1312,6 +1559,64 @@ cudaError_t launch_cocg_step_aw(const FilterArgs& a, bool fp64, int rbw, int k, 
     if (!fp64 && a.W == 32) return aw_launch_tw<float, 32>(a, rbw, k, grid, smem, s);
     if (fp64 && a.W == 16) return aw_launch_tw<double, 16>(a, rbw, k, grid, smem, s);
     return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------- warp-specialized step A launchers
+size_t ws_smem_bytes(int W, int rbw, int capr, int cape)
+{
+    const size_t rowb = (size_t)W * 8;  // complex FP32 tiles
+    const size_t stage = ((size_t)capr * rowb + 2 * (size_t)rbw * rowb + (size_t)cape * 8 + (size_t)(rbw + 4) * 4 + 127) &
+                         ~(size_t)127;
+    return 128 + 2 * stage;
+}
+
+template <int BM, int RBW>
+static int ws_occupancy_one(size_t smem)
+{
+    auto kern = cocg_step_ws<float, 32, BM, RBW>;
+    cudaFuncAttributes fa;
+    int dev = 0, optin = 0;
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const long long room = (long long)optin - (long long)fa.sharedSizeBytes;
+    if (room <= 0 || (long long)smem > room) return 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)room) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, kThreadsWS + 32, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return o;
+}
+
+// Variants built: complex FP32, 32 lanes, B the identity or diagonal, 48 or 32
+// rows per item; at most kMaxGroupsWS column groups.
+int ws_occupancy(bool fp64, int W, int bmode, int rbw, int groups, size_t smem)
+{
+    if (fp64 || W != 32 || groups > kMaxGroupsWS) return 0;
+    if (bmode == 0 && rbw == 48) return ws_occupancy_one<0, 48>(smem);
+    if (bmode == 0 && rbw == 32) return ws_occupancy_one<0, 32>(smem);
+    if (bmode == 1 && rbw == 48) return ws_occupancy_one<1, 48>(smem);
+    if (bmode == 1 && rbw == 32) return ws_occupancy_one<1, 32>(smem);
+    return 0;
+}
+
+cudaError_t launch_cocg_step_ws(const FilterArgs& a, int rbw, int k, int grid, size_t smem, cudaStream_t s)
+{
+    if (a.W != 32) return cudaErrorInvalidValue;
+    if (a.bmode == 0 && rbw == 48) cocg_step_ws<float, 32, 0, 48><<<grid, kThreadsWS + 32, smem, s>>>(a, k);
+    else if (a.bmode == 0 && rbw == 32) cocg_step_ws<float, 32, 0, 32><<<grid, kThreadsWS + 32, smem, s>>>(a, k);
+    else if (a.bmode == 1 && rbw == 48) cocg_step_ws<float, 32, 1, 48><<<grid, kThreadsWS + 32, smem, s>>>(a, k);
+    else if (a.bmode == 1 && rbw == 32) cocg_step_ws<float, 32, 1, 32><<<grid, kThreadsWS + 32, smem, s>>>(a, k);
+    else return cudaErrorInvalidValue;
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_filter_init(const FilterArgs& a, bool fp64, const double* R, const double* X, int rii,
