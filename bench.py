@@ -36,8 +36,8 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per group-iteration of each COCG step from one ncu
 # capture (profiles/cocg_steps_laplace3d_64cube.md), valid only for the kernel
 # source they were measured on.
-NCU_TRAFFIC = {"source_sha1": "89a43ee85654717cd2c6a26edead138abfd4dff7",
-               "cocg_step_a": (1.108600e9 + 0.627256e9) / 5, "cocg_step_b": (1.182058e9 + 0.467139e9) / 5}
+NCU_TRAFFIC = {"source_sha1": "d111b7a42e3d2659aeb3f935d8e05e73d221142c",
+               "cocg_step_a": (1.108692e9 + 0.626872e9) / 5, "cocg_step_b": (1.181998e9 + 0.467095e9) / 5}
 
 
 def parse():

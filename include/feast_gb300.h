@@ -444,9 +444,13 @@ int feast_eig_grad_dev(int n, const int* ia, const int* ja, int m, const double*
  * a CTA that spins there for more than `cycles` SM clock cycles sets an error
  * flag that makes every CTA of the launch return, and the call reports the
  * failure (-3 from the solvers and the reduced-eigensolver entry points) with the
- * context still usable.  Default 4e9 cycles (about two seconds at 2 GHz);
- * cycles < 1 restores the default.  Applies to launches issued after the
- * call, process-wide.  Returns the previous limit. */
+ * context still usable.  The COCG gathering step waits on an mbarrier for the
+ * bulk copies that stage its rows; a CTA whose wait exceeds the limit sets an
+ * error flag, lets its copies in flight land (waiting up to about a second
+ * more) and returns, and the solver reports -4 (message in feast_last_error).
+ * Default 4e9 cycles (about two seconds at 2 GHz); cycles < 1 restores the
+ * default.  Applies to launches issued after the call, process-wide.  Returns
+ * the previous limit. */
 long long feast_set_wait_limit(long long cycles);
 
 /* Gradient of an eigenvalue loss over the stored entries of A and B, host

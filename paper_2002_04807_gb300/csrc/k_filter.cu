@@ -642,6 +642,11 @@ __device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity, long l
         if (clock64() - t0 > limit) return false;
     return true;
 }
+// Limit of the wait for copies still in flight after a timed-out wait, before a
+// CTA leaves: at least about a second, whatever the caller's limit, so that no
+// copy lands in shared memory after its CTA has exited.
+__device__ __forceinline__ long long settle_limit(long long limit) { return limit > 2000000000LL ? limit : 2000000000LL; }
+
 // Bulk copy global -> shared (TMA engine), completion counted on the mbarrier.
 __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned mbar)
 {
@@ -917,7 +922,7 @@ __global__ void __launch_bounds__(kThreads, FEAST_AW_MINB) cocg_step_aw(FilterAr
         const bool ok = mbar_wait(mb, parity, a.wlimit);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(a.werr, 1);
-            mbar_wait(mb, parity, a.wlimit);  // let copies still in flight land before the CTA exits
+            mbar_wait(mb, parity, settle_limit(a.wlimit));  // let copies still in flight land before the CTA exits
             return;
         }
         parity ^= 1u;
@@ -1143,8 +1148,8 @@ __global__ void __launch_bounds__(kThreadsWS + 32, 1) cocg_step_ws(FilterArgs a,
         const bool ok = mbar_wait(mb0 + 8 * st, (kq >> 1) & 1, a.wlimit);
         if (consumers_or(!ok)) {  // flag, then leave (all consumers) once the copies in flight have landed
             if (tid == 0) atomicExch(a.werr, 1);
-            mbar_wait(mb0 + 8 * st, (kq >> 1) & 1, a.wlimit);
-            mbar_wait(mb0 + 8 * (st ^ 1), ((kq + 1) >> 1) & 1, a.wlimit);
+            mbar_wait(mb0 + 8 * st, (kq >> 1) & 1, settle_limit(a.wlimit));
+            mbar_wait(mb0 + 8 * (st ^ 1), ((kq + 1) >> 1) & 1, settle_limit(a.wlimit));
             return;
         }
         const unsigned char* sb = base + (unsigned)st * stage_bytes;
