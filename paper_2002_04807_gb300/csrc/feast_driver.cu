@@ -845,10 +845,11 @@ int choose_step_a(const Plan& P, Bufs& B, cudaStream_t s)
         B.nitems = (long long)P.G * nrbw;
         return 0;
     }
-#ifndef FEAST_WIN_RB_FIRST
-#define FEAST_WIN_RB_FIRST 64  // rows per staged item tried first (then the other of 64, 32)
+#ifndef FEAST_WIN_RB_MAX
+#define FEAST_WIN_RB_MAX 80  // largest rows per staged item tried (80 complex FP32 only, 64, 32)
 #endif
-    for (const int rbw : {FEAST_WIN_RB_FIRST, 96 - FEAST_WIN_RB_FIRST}) {
+    for (const int rbw : {80, 64, 32}) {
+        if (rbw > FEAST_WIN_RB_MAX || (rbw == 80 && P.fp64)) continue;
         int st4[4] = {0, 0, 0, 0};
         CK(cudaMemsetAsync(B.wstat, 0, sizeof(st4), s));
         CK(launch_win_build(P.n, rbw, B.app, B.apk, P.fp64, B.wpk, B.whdr, B.wwin, B.wlpp, B.wstat, s));

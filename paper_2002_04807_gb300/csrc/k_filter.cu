@@ -1530,6 +1530,8 @@ static int aw_occupancy(size_t smem)
 template <typename T, int W>
 static int aw_occupancy_tw(int bmode, int rbw, size_t smem)
 {
+    if (sizeof(T) == 4 && bmode == 0 && rbw == 80) return aw_occupancy<T, W, 0, 80>(smem);
+    if (sizeof(T) == 4 && bmode == 1 && rbw == 80) return aw_occupancy<T, W, 1, 80>(smem);
     if (bmode == 0 && rbw == 64) return aw_occupancy<T, W, 0, 64>(smem);
     if (bmode == 0 && rbw == 32) return aw_occupancy<T, W, 0, 32>(smem);
     if (bmode == 1 && rbw == 64) return aw_occupancy<T, W, 1, 64>(smem);
@@ -1538,7 +1540,8 @@ static int aw_occupancy_tw(int bmode, int rbw, size_t smem)
 }
 
 // Variants built: complex FP32 with 32 lanes, complex FP64 with 16 lanes (a
-// 256-byte tile row each); B the identity or diagonal; 32 or 64 rows per item.
+// 256-byte tile row each); B the identity or diagonal; 32 or 64 rows per item,
+// and 80 for complex FP32.
 int win_occupancy(bool fp64, int W, int bmode, int rbw, size_t smem)
 {
     if (!fp64 && W == 32) return aw_occupancy_tw<float, 32>(bmode, rbw, smem);
@@ -1549,7 +1552,9 @@ int win_occupancy(bool fp64, int W, int bmode, int rbw, size_t smem)
 template <typename T, int W>
 static cudaError_t aw_launch_tw(const FilterArgs& a, int rbw, int k, int grid, size_t smem, cudaStream_t s)
 {
-    if (a.bmode == 0 && rbw == 64) cocg_step_aw<T, W, 0, 64><<<grid, kThreads, smem, s>>>(a, k);
+    if (sizeof(T) == 4 && a.bmode == 0 && rbw == 80) cocg_step_aw<T, W, 0, 80><<<grid, kThreads, smem, s>>>(a, k);
+    else if (sizeof(T) == 4 && a.bmode == 1 && rbw == 80) cocg_step_aw<T, W, 1, 80><<<grid, kThreads, smem, s>>>(a, k);
+    else if (a.bmode == 0 && rbw == 64) cocg_step_aw<T, W, 0, 64><<<grid, kThreads, smem, s>>>(a, k);
     else if (a.bmode == 0 && rbw == 32) cocg_step_aw<T, W, 0, 32><<<grid, kThreads, smem, s>>>(a, k);
     else if (a.bmode == 1 && rbw == 64) cocg_step_aw<T, W, 1, 64><<<grid, kThreads, smem, s>>>(a, k);
     else if (a.bmode == 1 && rbw == 32) cocg_step_aw<T, W, 1, 32><<<grid, kThreads, smem, s>>>(a, k);

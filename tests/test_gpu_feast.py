@@ -441,7 +441,7 @@ def test_step_a_staged_and_cached_gathers_agree(pkg, name, mixed):
         else:
             assert form == 0, prof
         if form:
-            assert int(prof["step_a_rows_per_item"]) in (32, 48, 64)
+            assert int(prof["step_a_rows_per_item"]) in (32, 48, 64, 80)
             assert 1 <= int(prof["step_a_grid"]) <= -(-p.n // int(prof["step_a_rows_per_item"]))
         else:
             assert int(prof["step_a_rows_per_item"]) == 256
