@@ -31,16 +31,25 @@
 // a gather of a wide 3D stencil moves data at roughly half the rate of a
 // plain stream (far neighbours come through L2), so trading a second gather
 // for two extra streams is faster even though it moves more bytes.
+// Step A comes in three forms: the gather through the caches (cocg_step_a,
+// any matrix, several problems), and for single problems whose row blocks
+// read a few contiguous column ranges the staged forms, which copy those
+// ranges of r into shared memory with bulk asynchronous copies first: two
+// CTAs per SM each loading then computing one item (cocg_step_aw), or one
+// CTA per SM with a producer warp filling two stages while 16 warps compute
+// (cocg_step_ws, for blocks that stage many rows per row).
 // Rows of a CSR matrix are stored as packed (column, value) entries, the
 // diagonal entry first, padded to chunks of 8 with column -1 entries that
 // issue no load, so a row is gathered with fully unrolled loads and its own
 // value comes out of its first load.
 // Reductions are deterministic: fixed per-thread order, fixed block order;
-// every work item writes its own partial-sum slot, the CTA that completes a
-// bucket of 32 consecutive items sums them into a bucket slot, and the CTA
-// that completes a group's last bucket sums the bucket slots, each in item
-// order.  No CTA has to read more than 64 slots, so no single CTA carries a
-// long reduction at the end of a launch.
+// every work item (staged forms: every CTA, once per group) writes its own
+// partial-sum slot, the CTA that completes a bucket of 32 consecutive slots
+// sums them into a bucket slot, and the CTA that completes a group's last
+// bucket sums the bucket slots, each in slot order.  No CTA has to read more
+// than 64 slots, so no single CTA carries a long reduction at the end of a
+// launch.  Per-thread and per-item sums run in the filter precision: GB300's
+// FP64 rate is a small fraction of its FP32 rate.
 #include "feast_internal.cuh"
 #include <climits>
 #include <algorithm>
