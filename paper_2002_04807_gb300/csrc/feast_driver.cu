@@ -357,7 +357,6 @@ struct Bufs {
     size_t wsmem = 0;
     int4* whdr = nullptr;  // staged-window tables (k_filter.cu win_build)
     int2* wwin = nullptr;
-    int* wlpp = nullptr;
     void* wpk = nullptr;
     int wcape = 0;
     bool wws = false;  // staged step A in its warp-specialized form (cocg_step_ws)
@@ -455,11 +454,11 @@ size_t carve(const Plan& P, void* base, Bufs& B, bool filter_only = false)
     }
     if (P.win) {
         const size_t nrb32 = ((size_t)P.n + 31) / 32;
-        B.wpk = c.take<char>(((size_t)P.nnzA + 7 * (size_t)P.n) * pk);
+        // per row block its local row pointers ((rows + 4) ints: at most 36 per 32 rows
+        // for 32- to 80-row blocks, plus one block) and its packed entries
+        B.wpk = c.take<char>(((size_t)P.nnzA + 7 * (size_t)P.n) * pk + (nrb32 * 36 + 84) * 4);
         B.whdr = c.take<int4>(nrb32);
         B.wwin = c.take<int2>(nrb32 * kWinMax);
-        // (rows per item + 4) ints per row block: 32-row (36 ints) and 64-row (68 ints) blocks
-        B.wlpp = c.take<int>(nrb32 * 36 + 68);
         B.wstat = c.take<int>(4);
     }
     B.dQ = c.take<char>((size_t)P.G * P.mt * P.n * (P.fp64 ? 8 : 4));
@@ -701,7 +700,6 @@ int filter_pass(const Plan& P, Bufs& B, int rii, const double* R, const double* 
     fa.wpk = B.wpk;
     fa.wcapr = B.wcapr;
     fa.wcape = B.wcape;
-    fa.wlpp = B.wlpp;
     fa.werr = B.groups_left + 1;
     fa.wlimit = wait_limit_cycles();
     int grid_a = 1, grid_b = 1;
@@ -824,7 +822,7 @@ int choose_step_a(const Plan& P, Bufs& B, cudaStream_t s)
         if (!FEAST_STEP_A_WS || P.fp64 || P.W != 32) break;
         int st4[4] = {0, 0, 0, 0};
         CK(cudaMemsetAsync(B.wstat, 0, sizeof(st4), s));
-        CK(launch_win_build(P.n, rbw, B.app, B.apk, P.fp64, B.wpk, B.whdr, B.wwin, B.wlpp, B.wstat, s));
+        CK(launch_win_build(P.n, rbw, B.app, B.apk, P.fp64, B.wpk, B.whdr, B.wwin, B.wstat, s));
         CK(cudaMemcpyAsync(st4, B.wstat, sizeof(st4), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (st4[3]) return 0;  // column indices outside [0, n): leave the matrix to the general path
@@ -852,7 +850,7 @@ int choose_step_a(const Plan& P, Bufs& B, cudaStream_t s)
         if (rbw > FEAST_WIN_RB_MAX || (rbw == 80 && P.fp64)) continue;
         int st4[4] = {0, 0, 0, 0};
         CK(cudaMemsetAsync(B.wstat, 0, sizeof(st4), s));
-        CK(launch_win_build(P.n, rbw, B.app, B.apk, P.fp64, B.wpk, B.whdr, B.wwin, B.wlpp, B.wstat, s));
+        CK(launch_win_build(P.n, rbw, B.app, B.apk, P.fp64, B.wpk, B.whdr, B.wwin, B.wstat, s));
         CK(cudaMemcpyAsync(st4, B.wstat, sizeof(st4), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (st4[3]) return 0;  // column indices outside [0, n): leave the matrix to the general path

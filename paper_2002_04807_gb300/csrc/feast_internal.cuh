@@ -113,10 +113,9 @@ struct FilterArgs {
     // staged-window gather of step A (single problem; see win_build in k_filter.cu)
     const int4* whdr;   // per row block: (windows, staged rows, staged position of its first row, entries)
     const int2* wwin;   // per row block: kWinMax windows (first row, rows)
-    const void* wpk;    // packed entries with staged positions instead of columns
+    const void* wpk;    // per row block, one region: local row pointers, then its packed entries with staged positions
     int wcapr;          // staged rows per CTA (largest over the row blocks)
     int wcape;          // staged entries per CTA (largest over the row blocks)
-    const int* wlpp;    // per row block: local row pointers and own position (rows per item + 4 ints)
     int* werr;          // set to 1 when a CTA gave up waiting for its staged rows
     long long wlimit;   // that wait's limit in SM clock cycles
 };
@@ -138,15 +137,17 @@ cudaError_t launch_pack_csr(int n, const int* ia, const int* ja, const double* a
                             cudaStream_t s);
 cudaError_t launch_cast_diag(int n, const int* ia, const double* av, bool fp64, void* out, cudaStream_t s);
 // Staged-window gather (k_filter.cu).  win_build: for every row block of rbw
-// rows of the packed matrix (pp, pk), its windows (hdr, win) and its entries
-// rewritten with staged positions (lpk, same layout as pk); stat[0] largest
+// rows of the packed matrix (pp, pk), its windows (hdr, win) and, in one
+// region of meta, its local row pointers and its entries rewritten with
+// staged positions (bytes: rows of blocks x (rbw + 4) x 4 + the packed
+// entries); stat[0] largest
 // staged rows, stat[1] largest entry count of a row block, stat[2] row blocks
 // that do not fit, stat[3] entries with a column outside [0, n) (stat zeroed
 // by the caller).  win_smem_bytes: dynamic shared memory of step A for capr
 // staged rows and cape entries; win_occupancy: resident CTAs per SM of that
 // step A variant (0 when it does not exist or does not fit).
-cudaError_t launch_win_build(int n, int rbw, const int* pp, const void* pk, bool fp64, void* lpk, int4* hdr,
-                             int2* win, int* lpp, int* stat, cudaStream_t s);
+cudaError_t launch_win_build(int n, int rbw, const int* pp, const void* pk, bool fp64, void* meta, int4* hdr,
+                             int2* win, int* stat, cudaStream_t s);
 size_t win_smem_bytes(bool fp64, int W, int rbw, int capr, int cape);
 int win_occupancy(bool fp64, int W, int bmode, int rbw, size_t smem);
 cudaError_t launch_cocg_step_aw(const FilterArgs& a, bool fp64, int rbw, int k, int grid, size_t smem,

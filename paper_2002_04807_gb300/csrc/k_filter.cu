@@ -688,14 +688,16 @@ __device__ void block_bitonic(int* key, int P2)
 // One CTA per row block (grid-stride): the distinct columns of its entries
 // and its own rows, sorted and merged into windows; entries rewritten with
 // staged positions (window base + column - window start).
-// lpp[rb * (rbw + 4) + t]: the row block's row pointers relative to its first
-// entry (t = 0..rbw; rows past the end repeat the last), then its own rows'
-// staged position at t = rbw + 1: staged with the block's windows.
+// Each row block's staged metadata is one contiguous region of `meta`, at
+// byte offset rb * (rbw + 4) * 4 + e0 * sizeof(PK) (e0: the block's first
+// packed entry), so one bulk copy stages it: (rbw + 4) ints -- the row
+// pointers relative to e0 (t = 0..rbw; rows past the end repeat the last), the
+// own rows' staged position at t = rbw + 1 -- then the block's entries with
+// staged positions for columns.
 template <typename PK>
 __global__ void __launch_bounds__(256) win_build(int n, int rbw, int nrbw, const int* __restrict__ pp,
-                                                 const PK* __restrict__ pk, PK* __restrict__ lpk,
-                                                 int4* __restrict__ hdr, int2* __restrict__ win, int* __restrict__ lpp,
-                                                 int* stat)
+                                                 const PK* __restrict__ pk, char* __restrict__ meta,
+                                                 int4* __restrict__ hdr, int2* __restrict__ win, int* stat)
 {
     __shared__ int key[kWinKeys];
     __shared__ int ws[kWinMax], we[kWinMax], wb[kWinMax];
@@ -762,9 +764,10 @@ __global__ void __launch_bounds__(256) win_build(int n, int rbw, int nrbw, const
                         total += we[w] - ws[w];
                     }
                     hdr[rb] = make_int4(nw, total, own, cnt);
-                    lpp[(size_t)rb * (rbw + 4) + rbw + 1] = own;
-                    lpp[(size_t)rb * (rbw + 4) + rbw + 2] = 0;
-                    lpp[(size_t)rb * (rbw + 4) + rbw + 3] = 0;
+                    int* lpp = (int*)(meta + (size_t)rb * (rbw + 4) * 4 + (size_t)e0 * sizeof(PK));
+                    lpp[rbw + 1] = own;
+                    lpp[rbw + 2] = 0;
+                    lpp[rbw + 3] = 0;
                     atomicMax(stat + 0, total);
                     atomicMax(stat + 1, cnt);
                 } else {
@@ -777,7 +780,10 @@ __global__ void __launch_bounds__(256) win_build(int n, int rbw, int nrbw, const
         __syncthreads();
         if (s_ok) {
             const int nw = s_nw;
-            for (int t = tid; t <= rbw; t += blockDim.x) lpp[(size_t)rb * (rbw + 4) + t] = pp[min(row0 + t, row1)] - e0;
+            char* region = meta + (size_t)rb * (rbw + 4) * 4 + (size_t)e0 * sizeof(PK);
+            int* lpp = (int*)region;
+            PK* lpk = (PK*)(region + (size_t)(rbw + 4) * 4);
+            for (int t = tid; t <= rbw; t += blockDim.x) lpp[t] = pp[min(row0 + t, row1)] - e0;
             for (int t = tid; t < cnt; t += blockDim.x) {
                 PK e = pk[e0 + t];
                 if (e.x >= 0) {
@@ -785,7 +791,7 @@ __global__ void __launch_bounds__(256) win_build(int n, int rbw, int nrbw, const
                     while (w + 1 < nw && e.x >= ws[w + 1]) ++w;
                     e.x = wb[w] + e.x - ws[w];
                 }
-                lpk[e0 + t] = e;
+                lpk[t] = e;
             }
         }
         __syncthreads();  // shared tables are rewritten by the next row block
@@ -823,8 +829,8 @@ __global__ void __launch_bounds__(kThreads, FEAST_AW_MINB) cocg_step_aw(FilterAr
     // row block's entries, its local row pointers
     const unsigned dsm_sh = (unsigned)__cvta_generic_to_shared(dsm);
     const unsigned xs_sh = (dsm_sh + 127u) & ~127u;
-    const unsigned ent_sh = xs_sh + (unsigned)a.wcapr * ROWB;
-    const unsigned lpp_sh = ent_sh + (unsigned)a.wcape * ENTB;
+    const unsigned lpp_sh = xs_sh + (unsigned)a.wcapr * ROWB;  // staged metadata: row pointers, then entries
+    const unsigned ent_sh = lpp_sh + LPP * 4u;
     const V* xs = (const V*)(dsm + (xs_sh - dsm_sh));
     const int4* sent = (const int4*)(dsm + (ent_sh - dsm_sh));
     const int* lp = (const int*)(dsm + (lpp_sh - dsm_sh));
@@ -903,9 +909,9 @@ __global__ void __launch_bounds__(kThreads, FEAST_AW_MINB) cocg_step_aw(FilterAr
             __syncwarp();
             if (lane < h.x)
                 bulk_g2s(xs_sh + (unsigned)pos * ROWB, rtile + (size_t)wv.x * ROWB, (unsigned)wv.y * ROWB, mb);
-            if (lane == 31 && h.w > 0)
-                bulk_g2s(ent_sh, (const char*)a.wpk + (size_t)me0 * ENTB, (unsigned)h.w * ENTB, mb);
-            if (lane == 30) bulk_g2s(lpp_sh, a.wlpp + (size_t)rb * LPP, LPP * 4u, mb);
+            if (lane == 31)
+                bulk_g2s(lpp_sh, (const char*)a.wpk + (size_t)rb * LPP * 4 + (size_t)me0 * ENTB,
+                         LPP * 4u + (unsigned)h.w * ENTB, mb);
             // the next item's table rows load while this item computes
             const int nx = item + gridDim.x;
             mrb = -1;
@@ -1037,9 +1043,9 @@ __global__ void __launch_bounds__(kThreadsWS + 32, 1) cocg_step_ws(FilterArgs a,
     const int* __restrict__ app = P.app;
     const unsigned cap = (unsigned)a.wcapr, cape = (unsigned)a.wcape;
     // a stage: [windows of r | own rows of p | own rows of q | entries | local row pointers]
-    const unsigned p_off = cap * ROWB, q_off = p_off + RBW * ROWB, ent_off = q_off + RBW * ROWB;
-    const unsigned lpp_off = ent_off + cape * ENTB;
-    const unsigned stage_bytes = (lpp_off + LPP * 4u + 127u) & ~127u;
+    const unsigned p_off = cap * ROWB, q_off = p_off + RBW * ROWB, lpp_off = q_off + RBW * ROWB;
+    const unsigned ent_off = lpp_off + LPP * 4u;  // staged metadata: row pointers, then entries
+    const unsigned stage_bytes = (ent_off + cape * ENTB + 127u) & ~127u;
     const unsigned dsm_sh = (unsigned)__cvta_generic_to_shared(dsm);
     const unsigned base_sh = (dsm_sh + 127u) & ~127u;
     const unsigned char* base = dsm + (base_sh - dsm_sh);
@@ -1108,9 +1114,9 @@ __global__ void __launch_bounds__(kThreadsWS + 32, 1) cocg_step_ws(FilterArgs a,
                 bulk_g2s(sb + p_off, (const char*)a.p0 + tile_b + (size_t)row0 * ROWB, (unsigned)rows * ROWB, full);
             if (!first && lane == 17)
                 bulk_g2s(sb + q_off, (const char*)a.p1 + tile_b + (size_t)row0 * ROWB, (unsigned)rows * ROWB, full);
-            if (lane == 31 && h.w > 0)
-                bulk_g2s(sb + ent_off, (const char*)a.wpk + (size_t)e0 * ENTB, (unsigned)h.w * ENTB, full);
-            if (lane == 30) bulk_g2s(sb + lpp_off, a.wlpp + (size_t)rb * LPP, LPP * 4u, full);
+            if (lane == 31)
+                bulk_g2s(sb + lpp_off, (const char*)a.wpk + (size_t)rb * LPP * 4 + (size_t)e0 * ENTB,
+                         LPP * 4u + (unsigned)h.w * ENTB, full);
             it = nx;
         }
         return;
@@ -1488,16 +1494,16 @@ cudaError_t launch_cocg_step_b(const FilterArgs& a, bool fp64, int k, int grid, 
 }
 
 // ---------------------------------------------------------------- staged-window launchers
-cudaError_t launch_win_build(int n, int rbw, const int* pp, const void* pk, bool fp64, void* lpk, int4* hdr,
-                             int2* win, int* lpp, int* stat, cudaStream_t s)
+cudaError_t launch_win_build(int n, int rbw, const int* pp, const void* pk, bool fp64, void* meta, int4* hdr,
+                             int2* win, int* stat, cudaStream_t s)
 {
     if (n <= 0 || rbw <= 0) return cudaSuccess;
     const int nrbw = (n + rbw - 1) / rbw;
     const int grid = std::min(nrbw, num_sms() * 8);
     if (fp64)
-        win_build<int4><<<grid, 256, 0, s>>>(n, rbw, nrbw, pp, (const int4*)pk, (int4*)lpk, hdr, win, lpp, stat);
+        win_build<int4><<<grid, 256, 0, s>>>(n, rbw, nrbw, pp, (const int4*)pk, (char*)meta, hdr, win, stat);
     else
-        win_build<int2><<<grid, 256, 0, s>>>(n, rbw, nrbw, pp, (const int2*)pk, (int2*)lpk, hdr, win, lpp, stat);
+        win_build<int2><<<grid, 256, 0, s>>>(n, rbw, nrbw, pp, (const int2*)pk, (char*)meta, hdr, win, stat);
     count_launches(1);
     return cudaGetLastError();
 }
